@@ -1,0 +1,98 @@
+"""Geometric nested dissection of a box grid into the DBBD form of §2.3, eq. (perm_A).
+
+The paper obtains the doubly bordered block diagonal form with a graph partitioner
+(METIS); for structured grids a geometric recursive coordinate bisection gives the same
+kind of partition: split the longest axis (ties to the lowest axis) of the current box at
+m = floor((lo + hi) / 2); the plane coordinate == m joins the separator (interface)
+Gamma; recurse depth-first on the two halves; the boxes left after log2(nsub) levels are
+the interior subdomains, numbered in depth-first order.
+
+``interior_nd_order`` gives a fill-reducing elimination order for each interior block by
+the same bisection continued inside the subdomain box (children first, separator last),
+which is the ordering a caller would normally hand to a sparse direct solver.
+"""
+
+import numpy as np
+
+from .grids import grid_coords
+
+
+def _split_axis(lo, hi):
+    ext = [h - l + 1 for l, h in zip(lo, hi)]
+    return int(np.argmax(ext))  # argmax returns the lowest axis on ties
+
+
+def _box_mask(coords, lo, hi):
+    m = np.ones(coords.shape[0], dtype=bool)
+    for t in range(coords.shape[1]):
+        m &= (coords[:, t] >= lo[t]) & (coords[:, t] <= hi[t])
+    return m
+
+
+def nd_partition(shape, nsub):
+    """part[i] in [0, nsub) for interior nodes, -1 for the separator Gamma.
+
+    Returns (part, boxes) where boxes[b] = (lo, hi) inclusive bounds of subdomain b.
+    """
+    levels = int(round(np.log2(nsub)))
+    if 1 << levels != nsub:
+        raise ValueError("nsub must be a power of two")
+    shape = tuple(int(s) for s in shape)
+    coords = grid_coords(shape)
+    n = coords.shape[0]
+    part = np.full(n, -1, dtype=np.int32)
+    boxes = []
+
+    def rec(lo, hi, depth):
+        if any(h < l for l, h in zip(lo, hi)):
+            raise ValueError("grid too small for the requested number of subdomains")
+        if depth == levels:
+            b = len(boxes)
+            boxes.append((tuple(lo), tuple(hi)))
+            part[_box_mask(coords, lo, hi)] = b
+            return
+        ax = _split_axis(lo, hi)
+        m = (lo[ax] + hi[ax]) // 2
+        left_hi = list(hi)
+        left_hi[ax] = m - 1
+        right_lo = list(lo)
+        right_lo[ax] = m + 1
+        rec(list(lo), left_hi, depth + 1)
+        rec(right_lo, list(hi), depth + 1)
+
+    rec([0] * len(shape), [s - 1 for s in shape], 0)
+    return part, boxes
+
+
+def _box_nd_order(lo, hi, shape, leaf):
+    """Global node ids of the box in nested-dissection order (halves first, plane last)."""
+    ext = [h - l + 1 for l, h in zip(lo, hi)]
+    if any(e <= 0 for e in ext):
+        return np.zeros(0, dtype=np.int64)
+    if int(np.prod(ext)) <= leaf:
+        rng = [np.arange(l, h + 1) for l, h in zip(lo, hi)]
+        grid = np.meshgrid(*rng, indexing="ij")
+        # x fastest inside the leaf box
+        pts = np.stack([g.ravel(order="F") for g in grid], axis=1)
+        strides = np.cumprod([1] + list(shape[:-1]))
+        return (pts * strides).sum(axis=1).astype(np.int64)
+    ax = _split_axis(lo, hi)
+    m = (lo[ax] + hi[ax]) // 2
+    left_hi = list(hi)
+    left_hi[ax] = m - 1
+    right_lo = list(lo)
+    right_lo[ax] = m + 1
+    sep_lo = list(lo)
+    sep_hi = list(hi)
+    sep_lo[ax] = sep_hi[ax] = m
+    return np.concatenate([
+        _box_nd_order(list(lo), left_hi, shape, leaf),
+        _box_nd_order(right_lo, list(hi), shape, leaf),
+        _box_nd_order(sep_lo, sep_hi, shape, 1 << 62),  # separator: one dense block
+    ])
+
+
+def interior_nd_order(shape, boxes, leaf=16):
+    """Concatenated nested-dissection orders of all subdomain boxes (block by block)."""
+    shape = tuple(int(s) for s in shape)
+    return np.concatenate([_box_nd_order(list(lo), list(hi), shape, leaf) for lo, hi in boxes])

@@ -1,0 +1,283 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these checks re-types the oracle's own formula: each compares the oracle with an
+independent characterisation (closed forms, block inverses of A, textbook identities,
+finite termination, the Nyström definition, spectral inclusions stated in the paper).
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import fixtures as F
+import oracle as O
+
+
+def tiny(shape=(8, 8), nsub=2, lognormal=None, seed=0):
+    coef = None
+    if lognormal is not None:
+        rng = np.random.default_rng(seed)
+        coef = F.lognormal_field(F.grid_coords(shape), lognormal[0], lognormal[1], rng)
+    A = F.diffusion_matrix(shape, coef)
+    part, _ = F.nd_partition(shape, nsub)
+    return A, part
+
+
+# ---------------------------------------------------------------- fixtures
+@pytest.mark.parametrize("N", [5, 9, 12])
+def test_poisson2d_closed_form_eigenvalues(N):
+    A = F.diffusion_matrix((N, N)).toarray()
+    i = np.arange(1, N + 1)
+    lam = (4 - 2 * np.cos(i[:, None] * np.pi / (N + 1))
+           - 2 * np.cos(i[None, :] * np.pi / (N + 1))).ravel()
+    assert np.allclose(np.sort(np.linalg.eigvalsh(A)), np.sort(lam), atol=1e-12)
+
+
+def test_poisson3d_closed_form_eigenvalues():
+    N = 5
+    A = F.diffusion_matrix((N, N, N)).toarray()
+    c = 2 - 2 * np.cos(np.arange(1, N + 1) * np.pi / (N + 1))
+    lam = (c[:, None, None] + c[None, :, None] + c[None, None, :]).ravel()
+    assert np.allclose(np.sort(np.linalg.eigvalsh(A)), np.sort(lam), atol=1e-12)
+
+
+def test_diffusion_is_spd_and_symmetric():
+    A, _ = tiny((7, 6, 5), 2, lognormal=(2.0, 2.0))
+    D = A.toarray()
+    assert np.allclose(D, D.T)
+    assert np.linalg.eigvalsh(D).min() > 0
+    assert A.has_sorted_indices
+
+
+def test_partition_is_dbbd_and_config0_sizes():
+    P = F.make_problem(0)
+    assert P.n == 4096 and P.n_gamma == 127
+    assert sorted(int((P.part == b).sum()) for b in range(4)) == [961, 992, 992, 1024]
+    coo = P.A.tocoo()
+    pr, pc = P.part[coo.row], P.part[coo.col]
+    both = (pr >= 0) & (pc >= 0)
+    assert np.all(pr[both] == pc[both])          # no coupling between subdomains
+    # the interior order lists every interior node once, block by block
+    assert np.array_equal(np.sort(P.perm), np.nonzero(P.part >= 0)[0])
+    assert np.all(np.diff(P.part[P.perm]) >= 0)
+
+
+def test_dbbd_rejects_coupled_blocks():
+    A, part = tiny((6, 6), 2)
+    part = part.copy()
+    part[part < 0] = 0      # separator merged into block 0 -> blocks 0 and 1 couple
+    with pytest.raises(O.NotDBBD):
+        O.DBBD(A, part, 2)
+
+
+# ---------------------------------------------------------------- Schur complements
+def test_schur_gamma_is_inverse_of_gamma_block_of_Ainv():
+    A, part = tiny((9, 8), 4, lognormal=(3.0, 1.5))
+    D = O.DBBD(A, part)
+    Ainv = np.linalg.inv(A.toarray())
+    S = D.dense_S_gamma()
+    assert np.allclose(S @ Ainv[np.ix_(D.gamma, D.gamma)], np.eye(D.n_G), atol=1e-10)
+    # block elimination (eq. A_LDLT): A [x_I; x_G] = [0; f]  =>  S_Gamma x_G = f
+    f = np.random.default_rng(1).standard_normal(D.n_G)
+    rhs = np.zeros(D.n)
+    rhs[D.gamma] = f
+    x = np.linalg.solve(A.toarray(), rhs)
+    assert np.allclose(D.apply_S_gamma(x[D.gamma]), f, atol=1e-10)
+
+
+def test_schur_interior_is_inverse_of_interior_block_of_Ainv():
+    A, part = tiny((8, 7), 2, lognormal=(3.0, 1.0))
+    D = O.DBBD(A, part)
+    Ainv = np.linalg.inv(A.toarray())
+    SI = D.dense_S_I()
+    assert np.allclose(SI @ Ainv[np.ix_(D.interior, D.interior)], np.eye(D.n_I), atol=1e-10)
+
+
+def test_smw_identity():
+    A, part = tiny((8, 8), 2, lognormal=(2.0, 1.0))
+    D = O.DBBD(A, part)
+    AGinv = np.linalg.inv(D.A_G.toarray())
+    lhs = np.linalg.inv(D.dense_S_gamma())
+    rhs = AGinv + AGinv @ D.A_GI.toarray() @ np.linalg.inv(D.dense_S_I()) @ D.A_IG.toarray() @ AGinv
+    assert np.allclose(lhs, rhs, rtol=1e-9, atol=1e-12)
+
+
+def test_first_level_spectrum_and_eigen_map():
+    # lambda(A_G^{-1} S_G) in (0, 1] (§2.3) and the map lambda -> 1/lambda - 1 (§4.1)
+    A, part = tiny((9, 9), 4, lognormal=(3.0, 1.0))
+    D = O.DBBD(A, part)
+    S = D.dense_S_gamma()
+    AG = D.A_G.toarray()
+    lam = sla.eigh(S, AG, eigvals_only=True)
+    assert lam.min() > 0 and lam.max() <= 1 + 1e-12
+    B = D.A_GI.toarray() @ np.linalg.inv(D.dense_S_I()) @ D.A_IG.toarray()
+    mu = np.sort(sla.eigh(B, AG, eigvals_only=True))
+    assert np.allclose(mu, np.sort(1.0 / lam - 1.0), rtol=1e-8, atol=1e-8)
+
+
+# ---------------------------------------------------------------- (block) CG
+def _spd(n, seed, cond=1e3):
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.geomspace(1.0, cond, n)
+    return (Q * ev) @ Q.T
+
+
+def test_pcg_finite_termination_and_error_bound():
+    # in exact arithmetic CG ends after (number of distinct eigenvalues) steps; with 6
+    # well separated eigenvalues this survives rounding
+    n = 30
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A6 = (Q * np.repeat([1.0, 2.0, 5.0, 9.0, 20.0, 50.0], 5)) @ Q.T
+    xs = rng.standard_normal(n)
+    x, it, hist = O.pcg(lambda v: A6 @ v, lambda v: v, A6 @ xs, rtol=1e-11, maxit=200)
+    assert it <= 7
+    assert np.allclose(x, xs, atol=1e-8)
+    # CG error bound of the introduction (eq. k-th_error_cg) at every step
+    A = _spd(n, 3, cond=50.0)
+    b = A @ xs
+    lam = np.linalg.eigvalsh(A)
+    kappa = lam.max() / lam.min()
+    rate = (np.sqrt(kappa) - 1) / (np.sqrt(kappa) + 1)
+    e0 = np.sqrt(xs @ A @ xs)
+    for k in range(1, 15):
+        xk, _, _ = O.pcg(lambda v: A @ v, lambda v: v, b, rtol=0.0, maxit=k)
+        ek = np.sqrt((xs - xk) @ A @ (xs - xk))
+        assert ek <= 2 * e0 * rate ** k * (1 + 1e-10)
+
+
+def test_block_pcg_finite_termination():
+    n, s = 24, 4
+    A = _spd(n, 5, cond=1e2)
+    B = np.random.default_rng(6).standard_normal((n, s))
+    X, it, hist = O.block_pcg(lambda V: A @ V, lambda V: V, B, tol=1e-10, maxit=100)
+    assert it <= int(np.ceil(n / s)) + 2
+    assert np.linalg.norm(A @ X - B) / np.linalg.norm(B) < 1e-9
+
+
+def test_block_pcg_single_column_is_pcg():
+    n = 40
+    A = _spd(n, 7, cond=1e3)
+    Minv = np.diag(1.0 / np.diag(A))
+    b = np.random.default_rng(8).standard_normal(n)
+    for k in (1, 3, 7, 12):
+        xb, itb, _ = O.block_pcg(lambda V: A @ V, lambda V: Minv @ V, b[:, None], tol=0.0,
+                                 maxit=k)
+        x, it, _ = O.pcg(lambda v: A @ v, lambda v: Minv @ v, b, rtol=0.0, maxit=k)
+        assert itb == it == k
+        assert np.allclose(xb[:, 0], x, rtol=1e-9, atol=1e-12)
+
+
+def test_block_pcg_breakdown_free_on_duplicate_columns():
+    n = 30
+    A = _spd(n, 9, cond=1e2)
+    b = np.random.default_rng(10).standard_normal((n, 2))
+    B = np.concatenate([b, b, 2 * b[:, :1]], axis=1)      # rank 2, 5 columns
+    X, it, _ = O.block_pcg(lambda V: A @ V, lambda V: V, B, tol=1e-10, maxit=100)
+    assert np.all(np.isfinite(X))
+    assert np.linalg.norm(A @ X - B) / np.linalg.norm(B) < 1e-9
+    assert O.orth(B).shape[1] == 2
+
+
+def test_pcg_matches_scipy_cg():
+    A, part = tiny((10, 10), 2, lognormal=(3.0, 1.0))
+    b = np.random.default_rng(11).standard_normal(A.shape[0])
+    x, it, _ = O.pcg(lambda v: A @ v, lambda v: v, b, rtol=1e-12, maxit=1000)
+    xr = spla.spsolve(sp.csc_matrix(A), b)
+    assert np.allclose(x, xr, rtol=1e-8, atol=1e-10)
+
+
+# ---------------------------------------------------------------- Nyström (§2.1, Alg. 1)
+def test_nystrom_core_matches_definition():
+    # Nystrom approximation of eq. (NystromApprox): B G (G^T B G)^+ (B G)^T
+    rng = np.random.default_rng(12)
+    n, s = 40, 10
+    Bm = _spd(n, 13, cond=1e6)
+    G = rng.standard_normal((n, s))
+    Y = Bm @ G
+    U, Sig, info = O.nystrom_core(G, Y, k=s, eps_rel=1e-14)
+    ref = Y @ np.linalg.pinv(G.T @ Y) @ Y.T
+    assert np.allclose((U * Sig) @ U.T, ref, rtol=1e-7, atol=1e-8 * np.abs(ref).max())
+    assert np.allclose(U.T @ U, np.eye(U.shape[1]), atol=1e-10)
+    assert np.all(np.diff(Sig) <= 0)
+
+
+def test_nystrom_exact_for_low_rank():
+    rng = np.random.default_rng(14)
+    n, r, s = 50, 6, 10
+    V = np.linalg.qr(rng.standard_normal((n, r)))[0]
+    ev = np.array([50.0, 20.0, 9.0, 4.0, 2.0, 1.0])
+    Bm = (V * ev) @ V.T
+    G = rng.standard_normal((n, s))
+    U, Sig, info = O.nystrom_core(G, Bm @ G, k=8)
+    assert U.shape[1] == r                      # rank min(r, k) (§2.1)
+    assert np.allclose(Sig, ev, rtol=1e-9)
+    assert np.allclose((U * Sig) @ U.T, Bm, atol=1e-9)
+    # k < r: exact top-k eigenvectors
+    U3, S3, _ = O.nystrom_core(G, Bm @ G, k=3)
+    assert np.allclose(np.abs(U3.T @ V[:, :3]), np.eye(3), atol=1e-9)
+
+
+# ---------------------------------------------------------------- M2 (§4.3, Alg. 2)
+def _small_problem():
+    A, part = tiny((12, 12), 2, lognormal=(4.0, 1.0), seed=3)
+    return A, part, O.DBBD(A, part)
+
+
+@pytest.mark.parametrize("form", ["S_gamma", "S_I"])
+def test_m2_exact_when_rank_captured(form):
+    # n_Gamma = 12, s = 14 >= rank(A_GI S_I^{-1} A_IG): M2 = S_Gamma^{-1}, PCG in 1 step
+    A, part, D = _small_problem()
+    s = D.n_G + 2
+    G = np.random.default_rng(15).standard_normal((D.n_G, s))
+    M, info = O.build_m2(D, G, k=s, eps_inner=1e-14, form=form, eps_rel=1e-13)
+    Sinv = np.linalg.inv(D.dense_S_gamma())
+    assert np.allclose(M.dense(), Sinv, rtol=1e-7, atol=1e-9 * np.abs(Sinv).max())
+    b = np.random.default_rng(16).standard_normal(D.n)
+    x, it, _ = O.solve(D, M.apply, b, rtol=1e-10)
+    assert it <= 2
+    assert O.relative_residual(A, x, b) < 1e-9
+
+
+def test_m2_spectral_inclusion_and_monotone_in_k():
+    # 0 <= B_k <= B  =>  A_G^{-1} <= M2 <= S_G^{-1}: Lambda(M2 S) in [lambda_min(A_G^{-1}S), 1]
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=4)
+    D = O.DBBD(A, part)
+    S = D.dense_S_gamma()
+    lam1 = sla.eigh(S, D.A_G.toarray(), eigvals_only=True).min()
+    G = np.random.default_rng(17).standard_normal((D.n_G, D.n_G))
+    prev = lam1 * (1 - 1e-9)
+    for k in (2, 5, 10, 20):
+        M, _ = O.build_m2(D, G[:, :k + 4], k=k, eps_inner=1e-14)
+        mu = np.linalg.eigvals(M.dense() @ S).real
+        assert mu.min() >= lam1 * (1 - 1e-7) and mu.max() <= 1 + 1e-7
+        assert mu.min() >= prev * (1 - 1e-7)
+        prev = mu.min()
+
+
+def test_forms_agree_for_exact_inner_solves():
+    A, part, D = _small_problem()
+    G = np.random.default_rng(18).standard_normal((D.n_G, 6))
+    _, a = O.build_m2(D, G, k=4, eps_inner=1e-14, form="S_gamma")
+    _, b = O.build_m2(D, G, k=4, eps_inner=1e-14, form="S_I")
+    _, c = O.build_m2(D, G, k=4, eps_inner=1e-14, form="S_gamma_naive")
+    assert np.allclose(a["Y"], b["Y"], rtol=1e-8, atol=1e-10)
+    assert np.allclose(c["Y"], b["Y"], rtol=1e-6, atol=1e-8)
+
+
+def test_solve_and_full_space_form_on_config0():
+    P = F.make_problem(0)
+    D = O.DBBD(P.A, P.part, P.nsub)
+    G = F.make_sketch(D.n_G, P.s, 0)
+    _, b = F.make_rhs(P, 0)
+    M, info = O.build_m2(D, G, P.k, P.eps_inner)
+    x, it, _ = O.solve(D, M.apply, b, rtol=1e-8)
+    x2, it2, _ = O.solve_full_space(D, M.apply, b, rtol=1e-8)
+    x1, it1, _ = O.solve(D, D.solve_G, b, rtol=1e-8)
+    assert O.relative_residual(P.A, x, b) < 1e-7
+    assert abs(it - it2) <= 1
+    assert it < it1                                       # two-level beats S1
+    assert np.allclose(x, spla.spsolve(sp.csc_matrix(P.A), b), rtol=1e-6, atol=1e-7)
