@@ -1,0 +1,202 @@
+/*
+ * nsp.h — C ABI of a GB300 (sm_103a) implementation of the two-level Nyström–Schur
+ * preconditioner M2 for sparse SPD systems in doubly bordered block diagonal (DBBD)
+ * form (Al Daas, Rees & Scott, "Two-level Nyström–Schur preconditioner for sparse
+ * symmetric positive definite matrices").
+ *
+ * Problem statement (§2.3, eq. (perm_A)): A is SPD and, after a symmetric permutation
+ * given by a partition of its unknowns, has the form
+ *
+ *        [ A_I    A_IG ]      A_I = diag(A_1, ..., A_N) block diagonal (one block per
+ *        [ A_GI   A_G  ]      subdomain), G = the interface (separator) Gamma.
+ *
+ * The library builds M2 = A_G^{-1} + Z Sigma Z^T (§4.3 eq. (left_prec_mat), Algorithm 2)
+ * and solves S_Gamma w = f (§2.3 eq. (Sx=b)) with PCG preconditioned by M2, where
+ * S_Gamma = A_G - A_GI A_I^{-1} A_IG (§2.3 eq. (schur_complement)).
+ *
+ * Conventions used by every entry point:
+ *  - Orderings seen by callers. "Gamma order": interface unknowns (part[i] < 0) sorted by
+ *    their index i in A. "Interior order": interior unknowns block by block (block 0
+ *    first), each block sorted by index in A. Full-length vectors use A's own order.
+ *  - Blocks of vectors are row-major: a block of s columns over m unknowns is m*s
+ *    contiguous values, entry (i, j) at [i*s + j].
+ *  - Device pointers are CUDA global-memory pointers on the current device; all device
+ *    work is ordered on the handle's stream (nsp_params.stream, 0 = legacy default).
+ *  - Entry points never abort. They return an nsp_status; after NSP_ERR_CUDA the handle
+ *    should be destroyed. A NULL handle or pointer argument gives NSP_ERR_INVALID_ARG.
+ *  - One handle must not be used concurrently from several host threads.
+ */
+#ifndef NSP_H
+#define NSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  NSP_OK = 0,
+  NSP_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, malformed CSR, bad parameter      */
+  NSP_ERR_NOT_DBBD = 2,      /* two different interior blocks are coupled in A           */
+  NSP_ERR_NOT_SPD = 3,       /* non-positive pivot in a Cholesky factor (see failed_block) */
+  NSP_ERR_BREAKDOWN = 4,     /* block CG lost every search direction / PCG p^T S p <= 0   */
+  NSP_ERR_NOT_CONVERGED = 5, /* iteration cap reached; outputs still hold the last iterate */
+  NSP_ERR_TIMEOUT = 6,       /* a bounded device wait gave up (scheduler dependency)      */
+  NSP_ERR_CUDA = 7,          /* a CUDA runtime error                                      */
+  NSP_ERR_OOM = 8,           /* device allocation failed                                  */
+  NSP_ERR_UNSUPPORTED = 9    /* valid request this build does not handle                  */
+} nsp_status;
+
+typedef enum { NSP_FP64 = 0, NSP_FP32 = 1 } nsp_precision;
+
+/* Outer solve forms, both PCG preconditioned by M2 (§2.3, §4.3):
+ *  NSP_OUTER_SCHUR : PCG on S_Gamma w = f, f = b_G - A_GI A_I^{-1} b_I, then
+ *                    x_I = A_I^{-1}(b_I - A_IG w)  (block elimination, eq. (A_LDLT)).
+ *  NSP_OUTER_FULL  : PCG on A x = b with the block-factorization preconditioner of §2.3
+ *                    whose Schur-complement block is M2, from x0 = (A_I^{-1} b_I, 0). With
+ *                    exact A_I^{-1} its iterates equal those of NSP_OUTER_SCHUR; with an
+ *                    FP32 factor the operator A stays FP64, so the residual is exact.
+ *  NSP_OUTER_AUTO  : FULL when the factor precision is FP32, SCHUR when it is FP64. */
+typedef enum { NSP_OUTER_AUTO = 0, NSP_OUTER_SCHUR = 1, NSP_OUTER_FULL = 2 } nsp_outer_form;
+
+/* Inner system of Algorithm 2 step 3:
+ *  NSP_FORM_SGAMMA : block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G preconditioned by A_G
+ *                    (first level S1, §2.3 eq. (S1)), then Y = A_G E. By the SMW identity
+ *                    (§4.1 eq. (S-1)) Y = A_GI S_I^{-1} A_IG G, the Y of Algorithm 2. */
+typedef enum { NSP_FORM_SGAMMA = 0 } nsp_inner_form;
+
+/* Sparse matrix in CSR. Full symmetric pattern (both triangles) with sorted column
+ * indices and no duplicates. rowptr has n+1 entries. Host pointers unless on_device. */
+typedef struct {
+  int64_t n;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const double *val;
+  int32_t on_device;         /* 1: rowptr/col/val are device pointers (values read only) */
+} nsp_csr;
+
+/* DBBD partition (§2.3 eq. (perm_A)). part[i] in [0, nblocks) puts unknown i in interior
+ * block part[i]; part[i] = -1 puts it on the interface Gamma. perm (optional, may be NULL)
+ * lists interior unknowns in a fill-reducing elimination order: for each block, the
+ * relative order of its unknowns in perm is the order in which the block is factorized.
+ * perm has n_interior entries (every interior unknown once). Without perm, and always for
+ * A_G, the library computes a nested-dissection order of the block's graph. Host memory. */
+typedef struct {
+  int32_t nblocks;
+  const int32_t *part;
+  const int64_t *perm;
+} nsp_partition;
+
+typedef struct {
+  int32_t k;                 /* Nyström rank k > 0 (Algorithm 2 input)                    */
+  int32_t p;                 /* oversampling p >= 0; sketch width s = k + p               */
+  double eps_inner;          /* relative tolerance of the inner block PCG (paper: 0.1)    */
+  double eps_trunc_rel;      /* Algorithm 2 step 7 threshold, relative to max eig(C)      */
+  double drop_tol;           /* block-PCG column drop threshold (relative pivot)          */
+  int32_t max_inner_it;      /* inner block-PCG iteration cap (e.g. 500)                  */
+  uint64_t seed;             /* Gaussian sketch seed (Philox4x32-10 + Box-Muller)          */
+  const double *sketch;      /* optional caller sketch G: n_Gamma x s row-major, Gamma
+                                order, host memory; NULL = draw from seed                 */
+  int32_t precision;         /* nsp_precision of the factors and the inner block PCG      */
+  int32_t outer_form;        /* nsp_outer_form                                            */
+  int32_t inner_form;        /* nsp_inner_form                                            */
+  int32_t keep_intermediates;/* 1: keep E, Y, U of Algorithm 2 for nsp_get_intermediate  */
+  void *stream;              /* cudaStream_t for all device work (NULL = default stream)  */
+} nsp_params;
+
+typedef struct {
+  int64_t n, n_interior, n_gamma;
+  int32_t nblocks;
+  int64_t nnz_L_interior;    /* structural nonzeros of the interior Cholesky factors      */
+  int64_t nnz_L_gamma;       /* structural nonzeros of the A_G Cholesky factor            */
+  int64_t n_supernodes;
+  int32_t it_inner;          /* block-PCG iterations (it_{S_I} of §5)                     */
+  int32_t inner_active_cols; /* search-direction columns left at the last iteration      */
+  int32_t rank;              /* Nyström rank min(r, k) (§2.1)                             */
+  int32_t it_pcg;            /* outer PCG iterations of the last nsp_solve (it_PCG)      */
+  double inner_residual;     /* max relative column residual at exit of the block PCG     */
+  double final_residual;     /* ||b - A x|| / ||b|| of the last nsp_solve (FP64)          */
+  double pcg_residual;       /* updated-residual ratio ||r|| / ||f|| at exit              */
+  int32_t failed_block;      /* block id for NSP_ERR_NOT_SPD (nblocks = the A_G factor)   */
+  double ms_analyze, ms_factor, ms_inner, ms_core, ms_solve;   /* host wall times (ms)     */
+} nsp_info;
+
+typedef struct nsp_handle nsp_handle;
+
+/* Defaults: k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=1e-12 (FP64) /
+ * 1e-6 (FP32), max_inner_it=500, precision=NSP_FP32, AUTO outer form, seed=210112164. */
+void nsp_default_params(nsp_params *prm);
+
+/* Algorithm 2 end to end: analysis of A's pattern and the partition (host), numeric
+ * Cholesky factorization of every A_i and of A_G on the device, sketch G (step 1), inner
+ * block PCG (steps 2-4), Nyström core (steps 5-10), Z = A_G^{-1} U (step 11).
+ * A is copied; the caller keeps ownership of all inputs. On success *out owns all device
+ * memory of the preconditioner. Errors: INVALID_ARG, NOT_DBBD, NOT_SPD, BREAKDOWN, CUDA,
+ * OOM; *out is NULL on error. */
+nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params *prm,
+                     nsp_handle **out);
+
+/* Repeat the numeric part of nsp_build (factorization + Algorithm 2) for new values of A
+ * with the same pattern (val has nnz entries in the CSR order given to nsp_build; device
+ * memory if on_device). prm may change k, p, tolerances, seed, sketch (not precision). */
+nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device,
+                       const nsp_params *prm);
+
+/* z = M2 r = A_G^{-1} r + Z Sigma Z^T r (Algorithm 2 step 12). r, z: n_Gamma doubles in
+ * Gamma order, device pointers, may not alias. */
+nsp_status nsp_apply(const nsp_handle *h, const double *r_gamma, double *z_gamma);
+
+/* Solve A x = b (n doubles, A's order) to ||r|| / ||f|| <= rtol with the outer form of
+ * the handle (see nsp_outer_form). b and x may be host or device pointers (detected);
+ * host buffers are staged through device memory inside the call. info may be NULL.
+ * NOT_CONVERGED after maxit iterations (x holds the last iterate). */
+nsp_status nsp_solve(const nsp_handle *h, const double *b, double *x, double rtol,
+                     int32_t maxit, nsp_info *info);
+
+/* Y = S_Gamma X = A_G X - A_GI A_I^{-1} A_IG X (§2.3 eq. (schur_complement)) for an
+ * n_Gamma x s block (Gamma order, row-major, 1 <= s <= 256), in the handle's precision:
+ * X, Y are float* for NSP_FP32 handles and double* for NSP_FP64 handles. Device pointers,
+ * may not alias. This is the operator applied inside the inner block PCG. */
+nsp_status nsp_schur_apply(const nsp_handle *h, const void *X, void *Y, int32_t s);
+
+/* X = A_I^{-1} B (interior order, n_interior x s) or X = A_G^{-1} B (Gamma order,
+ * n_Gamma x s) with the device Cholesky factors, in the handle's precision (see
+ * nsp_schur_apply). which: 0 = interior blocks, 1 = A_G. Device pointers. */
+nsp_status nsp_factor_solve(const nsp_handle *h, int32_t which, const void *B, void *X,
+                            int32_t s);
+
+/* Copy Sigma (rank doubles, descending) and Z (n_Gamma x rank row-major, Gamma order) of
+ * M2 to host memory; either pointer may be NULL. *rank receives the rank. */
+nsp_status nsp_get_basis(const nsp_handle *h, double *Z, double *Sigma, int32_t *rank);
+
+/* Copy an intermediate of the last build to host (needs keep_intermediates=1), all
+ * n_Gamma x s row-major in Gamma order as doubles: which = 0: G (the sketch, step 1),
+ * 1: E (block-PCG solution), 2: Y (= A_G E, step 4), 3: U (step 10, n_Gamma x rank). */
+nsp_status nsp_get_intermediate(const nsp_handle *h, int32_t which, double *out);
+
+/* Dense lower Cholesky factor entries of one factor, for tests: block in [0, nblocks]
+ * (nblocks = A_G). Writes the block's elimination order (n_b global indices of A) to
+ * order and the factor L (n_b x n_b column-major, zeros above the diagonal and outside
+ * the structure) to L, host memory. The library stores inv(L_JJ) and L_J2 inv(L_JJ) per
+ * supernode; this call reconstructs L from them on the host. Use only for small blocks. */
+nsp_status nsp_get_factor(const nsp_handle *h, int32_t block, int64_t *order, double *L,
+                          int64_t n_b);
+
+/* Host-only validation, DBBD check, orderings and symbolic analysis of A's pattern (no CUDA
+ * call; A must be host memory). Fills n, n_interior, n_gamma, nblocks, nnz_L_interior,
+ * nnz_L_gamma, n_supernodes and ms_analyze of info. Errors as nsp_build's analysis part. */
+nsp_status nsp_analyze(const nsp_csr *A, const nsp_partition *P, nsp_info *info);
+
+nsp_status nsp_get_info(const nsp_handle *h, nsp_info *info);
+nsp_status nsp_destroy(nsp_handle *h);
+const char *nsp_status_string(nsp_status s);
+
+/* Philox4x32-10 (Salmon et al., SC'11) + Box-Muller normals, as used for the sketch:
+ * out[i] for i in [0, count), stream defined by seed; out is a device pointer. */
+nsp_status nsp_gaussian(uint64_t seed, int64_t count, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NSP_H */

@@ -1,0 +1,293 @@
+"""Python binding of the nsp C ABI (include/nsp.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library ``libnsp.so`` built in-tree by
+``paper_2101_12164_gb300.build``; there is no CPU fallback. Loading fails loudly when the
+library is missing. PyTorch is used only for device memory and the current CUDA stream.
+
+Function names follow the C ABI (``nsp_build``, ``nsp_apply``, ``nsp_solve`` ...); the
+``Handle`` class wraps a built preconditioner.
+"""
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnsp.so")
+
+NSP_FP64, NSP_FP32 = 0, 1
+NSP_OUTER_AUTO, NSP_OUTER_SCHUR, NSP_OUTER_FULL = 0, 1, 2
+STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_ERR_NOT_SPD",
+          4: "NSP_ERR_BREAKDOWN", 5: "NSP_ERR_NOT_CONVERGED", 6: "NSP_ERR_TIMEOUT",
+          7: "NSP_ERR_CUDA", 8: "NSP_ERR_OOM", 9: "NSP_ERR_UNSUPPORTED"}
+EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_solve",
+           "nsp_schur_apply", "nsp_factor_solve", "nsp_get_basis", "nsp_get_intermediate",
+           "nsp_get_factor", "nsp_get_info", "nsp_destroy", "nsp_status_string", "nsp_gaussian",
+           "nsp_analyze"]
+
+
+class NspError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s failed: %s" % (where, STATUS.get(status, status)))
+
+
+class nsp_csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("on_device", C.c_int32)]
+
+
+class nsp_partition(C.Structure):
+    _fields_ = [("nblocks", C.c_int32), ("part", C.c_void_p), ("perm", C.c_void_p)]
+
+
+class nsp_params(C.Structure):
+    _fields_ = [("k", C.c_int32), ("p", C.c_int32), ("eps_inner", C.c_double),
+                ("eps_trunc_rel", C.c_double), ("drop_tol", C.c_double),
+                ("max_inner_it", C.c_int32), ("seed", C.c_uint64), ("sketch", C.c_void_p),
+                ("precision", C.c_int32), ("outer_form", C.c_int32), ("inner_form", C.c_int32),
+                ("keep_intermediates", C.c_int32), ("stream", C.c_void_p)]
+
+
+class nsp_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("n_interior", C.c_int64), ("n_gamma", C.c_int64),
+                ("nblocks", C.c_int32), ("nnz_L_interior", C.c_int64),
+                ("nnz_L_gamma", C.c_int64), ("n_supernodes", C.c_int64),
+                ("it_inner", C.c_int32), ("inner_active_cols", C.c_int32), ("rank", C.c_int32),
+                ("it_pcg", C.c_int32), ("inner_residual", C.c_double),
+                ("final_residual", C.c_double), ("pcg_residual", C.c_double),
+                ("failed_block", C.c_int32), ("ms_analyze", C.c_double),
+                ("ms_factor", C.c_double), ("ms_inner", C.c_double), ("ms_core", C.c_double),
+                ("ms_solve", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libnsp.so is not built: run paper_2101_12164_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        sig = {
+            "nsp_default_params": (None, [C.POINTER(nsp_params)]),
+            "nsp_build": (C.c_int, [C.POINTER(nsp_csr), C.POINTER(nsp_partition),
+                                    C.POINTER(nsp_params), C.POINTER(P)]),
+            "nsp_rebuild": (C.c_int, [P, P, C.c_int32, C.POINTER(nsp_params)]),
+            "nsp_apply": (C.c_int, [P, P, P]),
+            "nsp_solve": (C.c_int, [P, P, P, C.c_double, C.c_int32, C.POINTER(nsp_info)]),
+            "nsp_schur_apply": (C.c_int, [P, P, P, C.c_int32]),
+            "nsp_factor_solve": (C.c_int, [P, C.c_int32, P, P, C.c_int32]),
+            "nsp_get_basis": (C.c_int, [P, P, P, C.POINTER(C.c_int32)]),
+            "nsp_get_intermediate": (C.c_int, [P, C.c_int32, P]),
+            "nsp_get_factor": (C.c_int, [P, C.c_int32, P, P, C.c_int64]),
+            "nsp_get_info": (C.c_int, [P, C.POINTER(nsp_info)]),
+            "nsp_destroy": (C.c_int, [P]),
+            "nsp_status_string": (C.c_char_p, [C.c_int]),
+            "nsp_gaussian": (C.c_int, [C.c_uint64, C.c_int64, P, P]),
+            "nsp_analyze": (C.c_int, [C.POINTER(nsp_csr), C.POINTER(nsp_partition),
+                                      C.POINTER(nsp_info)]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, where):
+    if status != 0:
+        raise NspError(status, where)
+
+
+def _ptr(x):
+    """Raw pointer of a torch tensor or numpy array (must be contiguous)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    assert x.flags["C_CONTIGUOUS"]
+    return x.ctypes.data
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _csr_struct(A, keep):
+    """nsp_csr from a scipy CSR matrix (host) or a (rowptr, col, val) triple of CUDA tensors."""
+    if isinstance(A, tuple):
+        rowptr, col, val = A
+        keep += [rowptr, col, val]
+        return nsp_csr(int(rowptr.numel() - 1), _ptr(rowptr), _ptr(col), _ptr(val), 1)
+    rowptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    keep += [rowptr, col, val]
+    return nsp_csr(A.shape[0], _ptr(rowptr), _ptr(col), _ptr(val), 0)
+
+
+def _part_struct(part, nblocks, perm, keep):
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    keep.append(part)
+    pp = None
+    if perm is not None:
+        perm = np.ascontiguousarray(perm, dtype=np.int64)
+        keep.append(perm)
+        pp = _ptr(perm)
+    return nsp_partition(int(nblocks), _ptr(part), pp)
+
+
+def nsp_default_params():
+    p = nsp_params()
+    lib().nsp_default_params(C.byref(p))
+    return p
+
+
+def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
+                max_inner_it=500, seed=210112164, sketch=None, precision="fp32",
+                outer_form="auto", keep_intermediates=False, stream=None, keep=None):
+    prm = nsp_default_params()
+    prm.k, prm.p = int(k), int(p)
+    prm.eps_inner, prm.eps_trunc_rel = float(eps_inner), float(eps_trunc_rel)
+    prm.precision = {"fp64": NSP_FP64, "fp32": NSP_FP32}[precision]
+    prm.drop_tol = float(drop_tol if drop_tol is not None else
+                         (1e-12 if precision == "fp64" else 1e-6))
+    prm.max_inner_it = int(max_inner_it)
+    prm.seed = int(seed)
+    prm.outer_form = {"auto": NSP_OUTER_AUTO, "schur": NSP_OUTER_SCHUR,
+                      "full": NSP_OUTER_FULL}[outer_form]
+    prm.keep_intermediates = 1 if keep_intermediates else 0
+    if sketch is not None:
+        sk = np.ascontiguousarray(sketch, dtype=np.float64)
+        if keep is not None:
+            keep.append(sk)
+        prm.sketch = _ptr(sk)
+    prm.stream = _stream() if stream is None else stream
+    return prm
+
+
+def nsp_build(A, part, nblocks, perm=None, **kw):
+    """Build M2 (Algorithm 2) for A; returns a Handle. See make_params for keywords."""
+    keep = []
+    csr = _csr_struct(A, keep)
+    ps = _part_struct(part, nblocks, perm, keep)
+    prm = make_params(keep=keep, **kw)
+    h = C.c_void_p()
+    _check(lib().nsp_build(C.byref(csr), C.byref(ps), C.byref(prm), C.byref(h)), "nsp_build")
+    return Handle(h, prm, keep)
+
+
+def nsp_analyze(A, part, nblocks, perm=None):
+    """Host-only validation and symbolic analysis; returns nsp_info as a dict."""
+    keep = []
+    csr = _csr_struct(A, keep)
+    ps = _part_struct(part, nblocks, perm, keep)
+    info = nsp_info()
+    _check(lib().nsp_analyze(C.byref(csr), C.byref(ps), C.byref(info)), "nsp_analyze")
+    return info.as_dict()
+
+
+def nsp_gaussian(seed, count, out):
+    _check(lib().nsp_gaussian(int(seed), int(count), _ptr(out), _stream()), "nsp_gaussian")
+    return out
+
+
+class Handle:
+    """A built Nyström–Schur preconditioner (owns device memory until destroyed)."""
+
+    def __init__(self, h, prm, keep):
+        self._h = h
+        self.prm = prm
+        self._keep = keep
+        self.dtype_name = "float64" if prm.precision == NSP_FP64 else "float32"
+
+    def _handle(self):
+        if self._h is None or not self._h.value:
+            raise RuntimeError("handle destroyed")
+        return self._h
+
+    def info(self):
+        inf = nsp_info()
+        _check(lib().nsp_get_info(self._handle(), C.byref(inf)), "nsp_get_info")
+        return inf.as_dict()
+
+    def rebuild(self, val, on_device=True, **kw):
+        keep = []
+        prm = make_params(keep=keep, **kw) if kw else None
+        if prm is not None:
+            prm.stream = self.prm.stream
+        st = lib().nsp_rebuild(self._handle(), _ptr(val), 1 if on_device else 0,
+                               C.byref(prm) if prm is not None else None)
+        _check(st, "nsp_rebuild")
+
+    def apply(self, r, z):
+        _check(lib().nsp_apply(self._handle(), _ptr(r), _ptr(z)), "nsp_apply")
+        return z
+
+    def solve(self, b, x, rtol=1e-8, maxit=500, allow_not_converged=False):
+        inf = nsp_info()
+        st = lib().nsp_solve(self._handle(), _ptr(b), _ptr(x), float(rtol), int(maxit),
+                             C.byref(inf))
+        if not (st == 0 or (allow_not_converged and st == 5)):
+            _check(st, "nsp_solve")
+        return inf.as_dict()
+
+    def schur_apply(self, X, Y):
+        s = 1 if X.dim() == 1 else X.shape[1]
+        _check(lib().nsp_schur_apply(self._handle(), _ptr(X), _ptr(Y), int(s)), "nsp_schur_apply")
+        return Y
+
+    def factor_solve(self, which, B, X):
+        s = 1 if B.dim() == 1 else B.shape[1]
+        _check(lib().nsp_factor_solve(self._handle(), int(which), _ptr(B), _ptr(X), int(s)),
+               "nsp_factor_solve")
+        return X
+
+    def get_basis(self):
+        inf = self.info()
+        nG, k = inf["n_gamma"], self.prm.k
+        Z = np.zeros((nG, k))
+        S = np.zeros(k)
+        r = C.c_int32()
+        _check(lib().nsp_get_basis(self._handle(), _ptr(Z), _ptr(S), C.byref(r)), "nsp_get_basis")
+        r = r.value
+        return np.ascontiguousarray(Z.ravel()[: nG * r].reshape(nG, r)), S[:r]
+
+    def get_intermediate(self, which):
+        inf = self.info()
+        nG = inf["n_gamma"]
+        cols = inf["rank"] if which == 3 else self.prm.k + self.prm.p
+        out = np.zeros((nG, max(cols, 1)))
+        _check(lib().nsp_get_intermediate(self._handle(), int(which), _ptr(out)),
+               "nsp_get_intermediate")
+        return out[:, :cols]
+
+    def get_factor(self, block, n_b):
+        """(order, L): elimination order (indices in A) and dense lower factor of a block."""
+        order = np.zeros(n_b, dtype=np.int64)
+        Lf = np.zeros(n_b * n_b)
+        _check(lib().nsp_get_factor(self._handle(), int(block), _ptr(order), _ptr(Lf),
+                                    int(n_b)), "nsp_get_factor")
+        return order, Lf.reshape(n_b, n_b).T.copy()   # column-major -> [row, col]
+
+    def destroy(self):
+        if self._h is not None and self._h.value:
+            lib().nsp_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

@@ -1,0 +1,1114 @@
+// Host runtime of the Nyström–Schur preconditioner and the C ABI of include/nsp.h.
+//
+// nsp_build = validation + DBBD extraction (§2.3 eq. (perm_A)) + symbolic analysis (host)
+//           + numeric factorization of A_1..A_N and A_G (device)
+//           + Algorithm 2: sketch G (step 1), inner block PCG (steps 2-4), Nyström core
+//             (steps 5-10), Z = A_G^{-1} U (step 11)             (device)
+// nsp_solve = outer PCG preconditioned by M2 (§2.3 eq. (Sx=b), §4.3 eq. (left_prec_mat)).
+//
+// Device vectors use the factor ("internal") orderings: interior unknowns by block, each
+// block in its postordered elimination order; interface unknowns in A_G's elimination order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "symbolic.h"
+
+namespace nsp {
+
+using Clock = std::chrono::steady_clock;
+static double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+// ------------------------------------------------------------------ host analysis
+struct HostSub {                     // a sub-matrix of A in internal numbering
+  int32_t nrows = 0, ncols = 0;
+  std::vector<int32_t> rowptr, col;
+  std::vector<int64_t> src;          // index into A's values
+};
+
+struct Analysis {
+  int64_t n = 0, nnz = 0, nI = 0, nG = 0;
+  int32_t nblocks = 0;
+  std::vector<int64_t> rowptr;       // copy of A's pattern
+  std::vector<int32_t> col;
+  Forest FI, FG;
+  std::vector<int64_t> i2g_I, i2g_G; // internal -> index in A
+  std::vector<int64_t> i2u_I, i2u_G; // internal -> caller interior / Gamma order
+  HostSub A_I, A_IG, A_GI, A_G;
+  double ms = 0;
+};
+
+static void validate_csr(const nsp_csr *A) {
+  require(A && A->n > 0 && A->rowptr && A->col && A->val, NSP_ERR_INVALID_ARG, "CSR: null or empty");
+  require(A->n < (int64_t(1) << 31) - 1, NSP_ERR_UNSUPPORTED, "CSR: n too large");
+}
+
+static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
+                    const nsp_partition *P, Analysis &an) {
+  auto t0 = Clock::now();
+  const int64_t n = A->n;
+  an.n = n;
+  require(rowptr[0] == 0, NSP_ERR_INVALID_ARG, "CSR: rowptr[0] != 0");
+  for (int64_t i = 0; i < n; ++i) require(rowptr[i + 1] >= rowptr[i], NSP_ERR_INVALID_ARG, "CSR: rowptr not monotone");
+  an.nnz = rowptr[n];
+  require(an.nnz < (int64_t(1) << 31) - 1, NSP_ERR_UNSUPPORTED, "CSR: too many nonzeros");
+  an.rowptr.assign(rowptr, rowptr + n + 1);
+  an.col.assign(col, col + an.nnz);
+  for (int64_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      require(col[e] >= 0 && col[e] < n, NSP_ERR_INVALID_ARG, "CSR: column out of range");
+      if (e > rowptr[i]) require(col[e] > col[e - 1], NSP_ERR_INVALID_ARG, "CSR: columns not sorted/unique");
+      diag |= col[e] == i;
+    }
+    require(diag, NSP_ERR_INVALID_ARG, "CSR: missing diagonal entry");
+  }
+  // symmetric pattern
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int32_t j = col[e];
+      const int32_t *b = col + rowptr[j], *en = col + rowptr[j + 1];
+      require(std::binary_search(b, en, (int32_t)i), NSP_ERR_INVALID_ARG, "CSR: pattern not symmetric");
+    }
+  // partition
+  require(P && P->part && P->nblocks >= 1, NSP_ERR_INVALID_ARG, "partition: null");
+  const int32_t nb = P->nblocks;
+  an.nblocks = nb;
+  const int32_t *part = P->part;
+  std::vector<std::vector<int64_t>> nodes(nb);
+  std::vector<int64_t> gam;
+  for (int64_t i = 0; i < n; ++i) {
+    require(part[i] >= -1 && part[i] < nb, NSP_ERR_INVALID_ARG, "partition: part out of range");
+    if (part[i] < 0) gam.push_back(i);
+    else nodes[part[i]].push_back(i);
+  }
+  for (int64_t i = 0; i < n; ++i)
+    if (part[i] >= 0)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int32_t pj = part[col[e]];
+        require(pj < 0 || pj == part[i], NSP_ERR_NOT_DBBD, "interior blocks are coupled");
+      }
+  an.nG = (int64_t)gam.size();
+  an.nI = n - an.nG;
+  require(an.nG > 0, NSP_ERR_INVALID_ARG, "partition: empty interface");
+  require(an.nI > 0, NSP_ERR_INVALID_ARG, "partition: no interior unknowns");
+  // caller order of interior / interface unknowns
+  std::vector<int64_t> g2u(n, -1);
+  {
+    int64_t u = 0;
+    for (int32_t b = 0; b < nb; ++b) for (int64_t g : nodes[b]) g2u[g] = u++;
+    for (int64_t t = 0; t < an.nG; ++t) g2u[gam[t]] = t;
+  }
+  // initial (elimination) order of each block
+  std::vector<std::vector<int64_t>> init(nb);
+  if (P->perm) {
+    std::vector<char> seen(n, 0);
+    for (int64_t q = 0; q < an.nI; ++q) {
+      const int64_t g = P->perm[q];
+      require(g >= 0 && g < n && part[g] >= 0 && !seen[g], NSP_ERR_INVALID_ARG, "partition: perm is not a permutation of the interior unknowns");
+      seen[g] = 1;
+      init[part[g]].push_back(g);
+    }
+  }
+  std::vector<int64_t> g2l(n, -1);
+  auto graph_of = [&](const std::vector<int64_t> &vs, int32_t label) {
+    Graph gr;
+    gr.n = (int32_t)vs.size();
+    gr.ptr.assign(gr.n + 1, 0);
+    for (int32_t l = 0; l < gr.n; ++l) g2l[vs[l]] = l;
+    for (int32_t l = 0; l < gr.n; ++l) {
+      const int64_t g = vs[l];
+      for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e)
+        if (col[e] != g && part[col[e]] == label) gr.adj.push_back((int32_t)g2l[col[e]]);
+      gr.ptr[l + 1] = (int64_t)gr.adj.size();
+    }
+    return gr;
+  };
+  for (int32_t b = 0; b < nb; ++b) {
+    if (!P->perm && !nodes[b].empty()) {
+      Graph gr = graph_of(nodes[b], b);
+      std::vector<int32_t> ord = nested_dissection(gr, 64);
+      init[b].resize(ord.size());
+      for (size_t q = 0; q < ord.size(); ++q) init[b][q] = nodes[b][ord[q]];
+    }
+  }
+  std::vector<int64_t> ginit;
+  {
+    Graph gr = graph_of(gam, -1);
+    std::vector<int32_t> ord = nested_dissection(gr, 64);
+    ginit.resize(ord.size());
+    for (size_t q = 0; q < ord.size(); ++q) ginit[q] = gam[ord[q]];
+  }
+  // lower-triangle patterns in the initial orders
+  auto pattern = [&](const std::vector<int64_t> &ord, int32_t label) {
+    BlockPattern bp;
+    bp.n = (int32_t)ord.size();
+    for (int32_t l = 0; l < bp.n; ++l) g2l[ord[l]] = l;
+    bp.colptr.assign(bp.n + 1, 0);
+    for (int32_t j = 0; j < bp.n; ++j) {
+      const int64_t g = ord[j];
+      for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+        const int32_t c = col[e];
+        if (part[c] != label) continue;
+        const int64_t i = g2l[c];
+        if (i >= j) { bp.rowidx.push_back((int32_t)i); bp.src.push_back(e); }
+      }
+      bp.colptr[j + 1] = (int64_t)bp.rowidx.size();
+    }
+    return bp;
+  };
+  {
+    std::vector<BlockPattern> pats(nb);
+    for (int32_t b = 0; b < nb; ++b) pats[b] = pattern(init[b], b);
+    analyze_forest(pats, 1, an.FI);
+  }
+  {
+    std::vector<BlockPattern> pats(1);
+    pats[0] = pattern(ginit, -1);
+    analyze_forest(pats, 1, an.FG);
+  }
+  // internal numbering
+  an.i2g_I.resize(an.nI);
+  an.i2u_I.resize(an.nI);
+  std::vector<int64_t> g2int(n, -1);
+  for (int32_t b = 0; b < nb; ++b) {
+    const int64_t off = an.FI.block_off[b];
+    for (int64_t t = off; t < an.FI.block_off[b + 1]; ++t) {
+      const int64_t g = init[b][an.FI.order[t]];
+      an.i2g_I[t] = g;
+      an.i2u_I[t] = g2u[g];
+      g2int[g] = t;
+    }
+  }
+  an.i2g_G.resize(an.nG);
+  an.i2u_G.resize(an.nG);
+  for (int64_t t = 0; t < an.nG; ++t) {
+    const int64_t g = ginit[an.FG.order[t]];
+    an.i2g_G[t] = g;
+    an.i2u_G[t] = g2u[g];
+    g2int[g] = t;
+  }
+  auto sub = [&](const std::vector<int64_t> &rows_g, bool cols_gamma, int32_t ncols) {
+    HostSub h;
+    h.nrows = (int32_t)rows_g.size();
+    h.ncols = ncols;
+    h.rowptr.assign(h.nrows + 1, 0);
+    for (int32_t r = 0; r < h.nrows; ++r) {
+      const int64_t g = rows_g[r];
+      for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+        const bool cg = part[col[e]] < 0;
+        if (cg != cols_gamma) continue;
+        h.col.push_back((int32_t)g2int[col[e]]);
+        h.src.push_back(e);
+      }
+      h.rowptr[r + 1] = (int32_t)h.col.size();
+    }
+    return h;
+  };
+  an.A_I = sub(an.i2g_I, false, (int32_t)an.nI);
+  an.A_IG = sub(an.i2g_I, true, (int32_t)an.nG);
+  an.A_GI = sub(an.i2g_G, false, (int32_t)an.nI);
+  an.A_G = sub(an.i2g_G, true, (int32_t)an.nG);
+  an.ms = ms_since(t0);
+}
+
+// ------------------------------------------------------------------ device containers
+template <typename T>
+struct DevCsr {
+  int32_t nrows = 0, ncols = 0;
+  int64_t nnz = 0;
+  DBuf<int32_t> rowptr, col;
+  DBuf<int64_t> src;
+  DBuf<double> v64;
+  DBuf<T> vT;
+  void upload(const HostSub &h, cudaStream_t st) {
+    nrows = h.nrows;
+    ncols = h.ncols;
+    nnz = (int64_t)h.col.size();
+    rowptr.upload(h.rowptr, st);
+    col.upload(h.col, st);
+    src.upload(h.src, st);
+    v64.alloc(nnz);
+    vT.alloc(nnz);
+  }
+  void refresh(const double *Aval, cudaStream_t st) {
+    launch_gather_values<double>(src.p, nnz, Aval, v64.p, st);
+    launch_gather_values<T>(src.p, nnz, Aval, vT.p, st);
+  }
+  CsrDev<double> d64() const { return CsrDev<double>{nrows, ncols, nnz, rowptr.p, col.p, v64.p}; }
+  CsrDev<T> dT() const { return CsrDev<T>{nrows, ncols, nnz, rowptr.p, col.p, vT.p}; }
+};
+
+struct ForestData {
+  Forest h;
+  DBuf<int32_t> sn_first, sn_w, sn_m, sn_block, rows, relmap, ch_ptr, ch_list, level_sn;
+  DBuf<int64_t> sn_rowptr, sn_panel, sn_front, sn_upd, gptr, gsrc, asm_ptr, asm_dst, asm_src;
+  ForestDev dev;
+  struct Tiles {
+    std::vector<int> fptr, bptr;
+    DBuf<TileItem> fwd, bwd;
+  };
+  std::map<int, std::unique_ptr<Tiles>> tiles;
+
+  void upload(cudaStream_t st) {
+    sn_first.upload(h.sn_first, st);
+    sn_w.upload(h.sn_w, st);
+    sn_m.upload(h.sn_m, st);
+    sn_block.upload(h.sn_block, st);
+    rows.upload(h.rows, st);
+    relmap.upload(h.relmap, st);
+    ch_ptr.upload(h.ch_ptr, st);
+    ch_list.upload(h.ch_list, st);
+    level_sn.upload(h.level_sn, st);
+    sn_rowptr.upload(h.sn_rowptr, st);
+    sn_panel.upload(h.sn_panel, st);
+    sn_front.upload(h.sn_front, st);
+    sn_upd.upload(h.sn_upd, st);
+    gptr.upload(h.gptr, st);
+    gsrc.upload(h.gsrc, st);
+    asm_ptr.upload(h.asm_ptr, st);
+    asm_dst.upload(h.asm_dst, st);
+    asm_src.upload(h.asm_src, st);
+    dev.nsn = h.nsn;
+    dev.n = h.n;
+    dev.sn_first = sn_first.p;
+    dev.sn_w = sn_w.p;
+    dev.sn_m = sn_m.p;
+    dev.sn_block = sn_block.p;
+    dev.sn_rowptr = sn_rowptr.p;
+    dev.sn_panel = sn_panel.p;
+    dev.sn_front = sn_front.p;
+    dev.sn_upd = sn_upd.p;
+    dev.rows = rows.p;
+    dev.relmap = relmap.p;
+    dev.ch_ptr = ch_ptr.p;
+    dev.ch_list = ch_list.p;
+    dev.gptr = gptr.p;
+    dev.gsrc = gsrc.p;
+    dev.asm_ptr = asm_ptr.p;
+    dev.asm_dst = asm_dst.p;
+    dev.asm_src = asm_src.p;
+  }
+
+  const Tiles &get_tiles(int tm, cudaStream_t st) {
+    auto it = tiles.find(tm);
+    if (it != tiles.end()) return *it->second;
+    auto t = std::make_unique<Tiles>();
+    std::vector<TileItem> f, b;
+    t->fptr.push_back(0);
+    t->bptr.push_back(0);
+    for (int l = 0; l < h.nlevels; ++l) {
+      for (int q = h.level_ptr[l]; q < h.level_ptr[l + 1]; ++q) {
+        const int J = h.level_sn[q];
+        for (int r0 = 0; r0 < h.sn_m[J]; r0 += tm) f.push_back(TileItem{J, r0});
+        for (int r0 = 0; r0 < h.sn_w[J]; r0 += tm) b.push_back(TileItem{J, r0});
+      }
+      t->fptr.push_back((int)f.size());
+      t->bptr.push_back((int)b.size());
+    }
+    t->fwd.upload(f, st);
+    t->bwd.upload(b, st);
+    auto &ref = *t;
+    tiles[tm] = std::move(t);
+    return ref;
+  }
+};
+
+// ------------------------------------------------------------------ engine
+struct EngineBase {
+  virtual ~EngineBase() = default;
+  virtual void factorize(const double *val, bool on_device) = 0;
+  virtual void construct(const nsp_params &prm) = 0;
+  virtual void apply_m2(const double *r, double *z) = 0;
+  virtual void solve(const double *b, double *x, double rtol, int maxit, int form) = 0;
+  virtual void schur_apply_user(const void *X, void *Y, int s) = 0;
+  virtual void factor_solve_user(int which, const void *B, void *X, int s) = 0;
+  virtual void get_basis(double *Z, double *Sigma, int32_t *rank) = 0;
+  virtual void get_intermediate(int which, double *out) = 0;
+  virtual void get_factor(int block, int64_t *order, double *L, int64_t nb) = 0;
+  nsp_info info{};
+  cudaStream_t st = nullptr;
+  int precision = NSP_FP32;
+};
+
+template <typename T>
+struct Engine : EngineBase {
+  Analysis an;
+  ForestData FI, FG;
+  DevCsr<T> A_I, A_IG, A_GI, A_G;
+  DBuf<int32_t> full_rowptr, full_col;   // A in caller order (FP64 residual)
+  DBuf<int64_t> i2g_I, i2g_G, i2u_I, i2u_G;
+  DBuf<double> Aval;
+  DBuf<T> panelI, panelG, front;
+  DBuf<DevStatus> dstat;
+  DevStatus *hstat = nullptr;            // pinned
+  double *hscal = nullptr;               // pinned scalars
+  int32_t *hint = nullptr;               // pinned ints
+  // solve workspaces (sized for s_ws columns)
+  int s_ws = 0;
+  DBuf<T> Bv, Yw, Xw, Uw, YwG, UwG;
+  // Algorithm 2 state
+  int s = 0, k = 0, rank = 0;
+  DBuf<T> G, Fh, E, R, P, Q, Z, W, Y, U, Zt;
+  DBuf<double> gram_work, PtQ, PtR, QtZ, Cg, alpha, beta, Rinv, Lwork, colsq, bnorm, ratio;
+  DBuf<double> K, Cn, Mix, Sigma, nys_work, Zs;
+  DBuf<int32_t> mask, nkept, drank;
+  bool keep = false;
+  // outer PCG vectors (FP64)
+  DBuf<double> vb, vx, vr, vz, vp, vq, vt, vu, vf, dwork, dscal;
+  DBuf<T> sT, sT2;
+
+  Engine(const nsp_csr *A, const int64_t *rowptr, const int32_t *col, const nsp_partition *P,
+         cudaStream_t stream) {
+    st = stream;
+    precision = std::is_same<T, double>::value ? NSP_FP64 : NSP_FP32;
+    analyze(A, rowptr, col, P, an);
+    FI.h = std::move(an.FI);
+    FG.h = std::move(an.FG);
+    FI.upload(st);
+    FG.upload(st);
+    A_I.upload(an.A_I, st);
+    A_IG.upload(an.A_IG, st);
+    A_GI.upload(an.A_GI, st);
+    A_G.upload(an.A_G, st);
+    {
+      std::vector<int32_t> rp(an.n + 1);
+      for (int64_t i = 0; i <= an.n; ++i) rp[i] = (int32_t)an.rowptr[i];
+      full_rowptr.upload(rp, st);
+      full_col.upload(an.col, st);
+    }
+    i2g_I.upload(an.i2g_I, st);
+    i2g_G.upload(an.i2g_G, st);
+    i2u_I.upload(an.i2u_I, st);
+    i2u_G.upload(an.i2u_G, st);
+    Aval.alloc(an.nnz);
+    panelI.alloc(FI.h.panel_size);
+    panelG.alloc(FG.h.panel_size);
+    front.alloc(std::max(FI.h.front_size, FG.h.front_size));
+    dstat.alloc(1);
+    NSP_CUDA(cudaMallocHost(&hstat, sizeof(DevStatus)));
+    NSP_CUDA(cudaMallocHost(&hscal, 16 * sizeof(double)));
+    NSP_CUDA(cudaMallocHost(&hint, 16 * sizeof(int32_t)));
+    dscal.alloc(16);
+    info.n = an.n;
+    info.n_interior = an.nI;
+    info.n_gamma = an.nG;
+    info.nblocks = an.nblocks;
+    info.nnz_L_interior = FI.h.nnz_L;
+    info.nnz_L_gamma = FG.h.nnz_L;
+    info.n_supernodes = FI.h.nsn + FG.h.nsn;
+    info.ms_analyze = an.ms;
+    info.failed_block = -1;
+  }
+  ~Engine() override {
+    if (hstat) cudaFreeHost(hstat);
+    if (hscal) cudaFreeHost(hscal);
+    if (hint) cudaFreeHost(hint);
+  }
+
+  void sync() { NSP_CUDA(cudaStreamSynchronize(st)); }
+
+  void check_status() {
+    NSP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    sync();
+    if (hstat->code == DEV_NOT_SPD) {
+      info.failed_block = hstat->aux < 0 ? an.nblocks : hstat->aux;
+      throw Error(NSP_ERR_NOT_SPD, "non-positive pivot in a Cholesky factor");
+    }
+    if (hstat->code == DEV_BREAKDOWN) throw Error(NSP_ERR_BREAKDOWN, "block PCG breakdown");
+    if (hstat->code != DEV_OK) throw Error(NSP_ERR_CUDA, "device error");
+  }
+
+  void ensure_ws(int sc) {
+    if (sc <= s_ws) return;
+    s_ws = sc;
+    Bv.alloc((size_t)an.nI * sc);
+    Yw.alloc((size_t)an.nI * sc);
+    Xw.alloc((size_t)an.nI * sc);
+    Uw.alloc((size_t)std::max<int64_t>(FI.h.upd_rows, 1) * sc);
+    YwG.alloc((size_t)an.nG * sc);
+    UwG.alloc((size_t)std::max<int64_t>(FG.h.upd_rows, 1) * sc);
+  }
+
+  // ---- numeric factorization of every A_b and of A_G (§2.3)
+  void factorize(const double *val, bool on_device) override {
+    auto t0 = Clock::now();
+    NSP_CUDA(cudaMemcpyAsync(Aval.p, val, an.nnz * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    A_I.refresh(Aval.p, st);
+    A_IG.refresh(Aval.p, st);
+    A_GI.refresh(Aval.p, st);
+    A_G.refresh(Aval.p, st);
+    NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
+    for (int l = 0; l < FI.h.nlevels; ++l) {
+      const int c0 = FI.h.level_ptr[l], c1 = FI.h.level_ptr[l + 1];
+      launch_factor_level<T>(FI.dev, FI.level_sn.p + c0, c1 - c0, Aval.p, front.p, panelI.p,
+                             dstat.p, st);
+    }
+    check_factor_status(-1);
+    for (int l = 0; l < FG.h.nlevels; ++l) {
+      const int c0 = FG.h.level_ptr[l], c1 = FG.h.level_ptr[l + 1];
+      launch_factor_level<T>(FG.dev, FG.level_sn.p + c0, c1 - c0, Aval.p, front.p, panelG.p,
+                             dstat.p, st);
+    }
+    check_factor_status(an.nblocks);  // a failure in the A_G factor reports block nblocks
+    info.ms_factor = ms_since(t0);
+  }
+
+  void check_factor_status(int block_override) {
+    NSP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    sync();
+    if (hstat->code == DEV_NOT_SPD) {
+      info.failed_block = block_override >= 0 ? block_override : hstat->aux;
+      throw Error(NSP_ERR_NOT_SPD, "non-positive pivot in a Cholesky factor");
+    }
+    if (hstat->code != DEV_OK) throw Error(NSP_ERR_CUDA, "device error in factorization");
+  }
+
+  // ---- X = A_b^{-1} B over a forest (internal order, s columns)
+  void solve_forest(ForestData &F, const T *panel, const T *B, T *Ywk, T *Uwk, T *X, int sc) {
+    const int tm = solve_tile_rows(sc);
+    const auto &tl = F.get_tiles(tm, st);
+    for (int l = 0; l < F.h.nlevels; ++l) {
+      const int a = tl.fptr[l], b = tl.fptr[l + 1];
+      launch_solve_fwd<T>(F.dev, tl.fwd.p + a, b - a, tm, panel, B, Ywk, Uwk, sc, st);
+    }
+    for (int l = F.h.nlevels - 1; l >= 0; --l) {
+      const int a = tl.bptr[l], b = tl.bptr[l + 1];
+      launch_solve_bwd<T>(F.dev, tl.bwd.p + a, b - a, tm, panel, Ywk, X, sc, st);
+    }
+  }
+  void solve_I(const T *B, T *X, int sc) {
+    ensure_ws(sc);
+    solve_forest(FI, panelI.p, B, Yw.p, Uw.p, X, sc);
+  }
+  void solve_G(const T *B, T *X, int sc) {
+    ensure_ws(sc);
+    solve_forest(FG, panelG.p, B, YwG.p, UwG.p, X, sc);
+  }
+
+  // ---- S_Gamma X (with_AG) or A_GI A_I^{-1} A_IG X (internal Gamma order)
+  void schur_apply(const T *X, T *Yo, int sc, bool with_AG) {
+    ensure_ws(sc);
+    launch_spmm<T>(A_IG.dT(), X, Bv.p, sc, T(1), nullptr, T(0), st);
+    solve_forest(FI, panelI.p, Bv.p, Yw.p, Uw.p, Xw.p, sc);
+    if (with_AG) {
+      launch_spmm<T>(A_G.dT(), X, Yo, sc, T(1), nullptr, T(0), st);
+      launch_spmm<T>(A_GI.dT(), Xw.p, Yo, sc, T(-1), Yo, T(1), st);
+    } else {
+      launch_spmm<T>(A_GI.dT(), Xw.p, Yo, sc, T(1), nullptr, T(0), st);
+    }
+  }
+
+  void gram(const T *X, const T *Yv, int s1, int s2, double *C) {
+    launch_gram<T, T>(X, Yv, an.nG, s1, s2, C, gram_work.p, st);
+  }
+  void gram_acc64(const T *X, const T *Yv, int s1, int s2, double *C) {
+    launch_gram<T, double>(X, Yv, an.nG, s1, s2, C, gram_work.p, st);
+  }
+
+  // ---- Algorithm 2
+  void construct(const nsp_params &prm) override {
+    auto t0 = Clock::now();
+    require(prm.k > 0 && prm.p >= 0, NSP_ERR_INVALID_ARG, "k > 0 and p >= 0 required");
+    s = prm.k + prm.p;
+    k = prm.k;
+    require(s <= 256, NSP_ERR_UNSUPPORTED, "k + p > 256");
+    require(s <= an.nG, NSP_ERR_INVALID_ARG, "k + p exceeds the interface size");
+    require(prm.inner_form == NSP_FORM_SGAMMA, NSP_ERR_UNSUPPORTED, "inner form");
+    keep = prm.keep_intermediates != 0;
+    ensure_ws(s);
+    const size_t ns = (size_t)an.nG * s;
+    for (DBuf<T> *b : {&G, &Fh, &E, &R, &P, &Q, &Z, &W, &Y}) b->ensure(ns);
+    gram_work.ensure(std::max(gram_work_size(an.nG, s, s), gram_work_size(an.nG, s, 1)));
+    for (DBuf<double> *b : {&PtQ, &PtR, &QtZ, &Cg, &alpha, &beta, &Lwork, &K, &Cn})
+      b->ensure((size_t)s * s);
+    Rinv.ensure(3 * (size_t)s * s + s + 64);
+    colsq.ensure(s);
+    bnorm.ensure(s);
+    ratio.ensure(1);
+    Mix.ensure((size_t)s * k);
+    Sigma.ensure(k);
+    nys_work.ensure(nystrom_work_size(s));
+    mask.ensure(s);
+    nkept.ensure(1);
+    drank.ensure(1);
+    NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
+
+    // step 1: sketch G (caller order), moved to the internal order
+    {
+      DBuf<double> g64(ns);
+      if (prm.sketch) {
+        NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+      } else {
+        launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
+      }
+      launch_gather_rows<double, T>(i2u_G.p, an.nG, g64.p, G.p, s, st);
+      sync();
+    }
+    // steps 2-3: block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G, preconditioner A_G^{-1}
+    schur_apply(G.p, Fh.p, s, false);
+    launch_col_sumsq<T>(Fh.p, an.nG, s, colsq.p, gram_work.p, st);
+    launch_sqrt_vec(colsq.p, s, bnorm.p, st);
+    NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
+    NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    solve_G(R.p, Z.p, s);
+    gram(Z.p, Z.p, s, s, Cg.p);
+    launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, st);
+    launch_block_update<T>(Z.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
+    int it = 0;
+    double rat = 1.0;
+    int active = s;
+    while (it < prm.max_inner_it) {
+      schur_apply(P.p, Q.p, s, true);
+      gram(P.p, Q.p, s, s, PtQ.p);
+      gram(P.p, R.p, s, s, PtR.p);
+      launch_spd_solve_masked(PtQ.p, PtR.p, s, s, mask.p, 1.0, alpha.p, Lwork.p, dstat.p, st);
+      launch_block_update<T>(P.p, alpha.p, an.nG, s, s, T(1), E.p, T(1), E.p, st);
+      launch_block_update<T>(Q.p, alpha.p, an.nG, s, s, T(-1), R.p, T(1), R.p, st);
+      ++it;
+      launch_col_sumsq<T>(R.p, an.nG, s, colsq.p, gram_work.p, st);
+      launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st);
+      NSP_CUDA(cudaMemcpyAsync(hscal, ratio.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      rat = hscal[0];
+      if (!(rat > prm.eps_inner)) break;
+      solve_G(R.p, Z.p, s);
+      gram(Q.p, Z.p, s, s, QtZ.p);
+      launch_spd_solve_masked(PtQ.p, QtZ.p, s, s, mask.p, -1.0, beta.p, Lwork.p, dstat.p, st);
+      launch_block_update<T>(P.p, beta.p, an.nG, s, s, T(1), Z.p, T(1), W.p, st);
+      gram(W.p, W.p, s, s, Cg.p);
+      launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, st);
+      launch_block_update<T>(W.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
+      NSP_CUDA(cudaMemcpyAsync(hint, nkept.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      sync();
+      active = hint[0];
+      if (active == 0) break;
+    }
+    check_status();
+    info.it_inner = it;
+    info.inner_residual = rat;
+    info.inner_active_cols = active;
+    info.ms_inner = ms_since(t0);
+    auto t1 = Clock::now();
+    // step 4: Y = A_G E (= A_GI S_I^{-1} A_IG G)
+    launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
+    // steps 5-10
+    gram_acc64(Y.p, Y.p, s, s, K.p);
+    gram_acc64(G.p, Y.p, s, s, Cn.p);
+    launch_nystrom_core(K.p, Cn.p, s, k, prm.eps_trunc_rel, 1e-14, Mix.p, Sigma.p, drank.p,
+                        nys_work.p, st);
+    NSP_CUDA(cudaMemcpyAsync(hint, drank.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    sync();
+    rank = hint[0];
+    info.rank = rank;
+    U.ensure((size_t)an.nG * k);
+    Zt.ensure((size_t)an.nG * k);
+    Zs.ensure((size_t)an.nG * k);
+    if (rank > 0) {
+      // U = Y Mix (columns beyond the rank are zero, Sigma there is zero)
+      launch_block_update<T>(Y.p, Mix.p, an.nG, s, k, T(1), nullptr, T(0), U.p, st);
+      // step 11: Z = A_G^{-1} U; M2's low-rank term kept as Zs = Z Sigma^{1/2} in FP64
+      solve_G(U.p, Zt.p, k);
+      launch_gather_rows<T, double>(nullptr, an.nG, Zt.p, Zs.p, k, st);
+      launch_scale_cols(Zs.p, an.nG, k, Sigma.p, true, st);
+      sync();
+    }
+    info.ms_core = ms_since(t1);
+  }
+
+  // ---- M2 r = A_G^{-1} r + Z Sigma Z^T r (internal order, FP64 in/out)
+  DBuf<double> zt_vec;
+  void m2_apply_internal(const double *r, double *z) {
+    if (std::is_same<T, double>::value) {
+      solve_G(reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), 1);
+    } else {
+      sT.ensure(an.nG);
+      sT2.ensure(an.nG);
+      launch_gather_rows<double, T>(nullptr, an.nG, r, sT.p, 1, st);
+      solve_G(sT.p, sT2.p, 1);
+      launch_gather_rows<T, double>(nullptr, an.nG, sT2.p, z, 1, st);
+    }
+    if (rank > 0) {
+      zt_vec.ensure(k);
+      launch_gram<double, double>(Zs.p, r, an.nG, k, 1, zt_vec.p, dwork.p, st);
+      launch_block_update<double>(Zs.p, zt_vec.p, an.nG, k, 1, 1.0, z, 1.0, z, st);
+    }
+  }
+
+  // interior solve on FP64 vectors with the T factor
+  void solve_I64(const double *b, double *x) {
+    if (std::is_same<T, double>::value) {
+      solve_I(reinterpret_cast<const T *>(b), reinterpret_cast<T *>(x), 1);
+    } else {
+      sT.ensure(std::max(an.nI, an.nG));
+      sT2.ensure(std::max(an.nI, an.nG));
+      launch_gather_rows<double, T>(nullptr, an.nI, b, sT.p, 1, st);
+      solve_I(sT.p, sT2.p, 1);
+      launch_gather_rows<T, double>(nullptr, an.nI, sT2.p, x, 1, st);
+    }
+  }
+
+  void schur64(const double *p, double *q) {
+    if (std::is_same<T, double>::value) {
+      schur_apply(reinterpret_cast<const T *>(p), reinterpret_cast<T *>(q), 1, true);
+    } else {
+      sT.ensure(std::max(an.nI, an.nG));
+      sT2.ensure(std::max(an.nI, an.nG));
+      launch_gather_rows<double, T>(nullptr, an.nG, p, sT.p, 1, st);
+      schur_apply(sT.p, sT2.p, 1, true);
+      launch_gather_rows<T, double>(nullptr, an.nG, sT2.p, q, 1, st);
+    }
+  }
+
+  void apply_m2(const double *r, double *z) override {
+    dwork.ensure(gram_work_size(std::max(an.n, an.nG), 256, 1));
+    DBuf<double> ri(an.nG), zi(an.nG);
+    launch_gather_rows<double, double>(i2u_G.p, an.nG, r, ri.p, 1, st);
+    m2_apply_internal(ri.p, zi.p);
+    launch_scatter_rows<double, double>(i2u_G.p, an.nG, zi.p, z, 1, st);
+    sync();
+  }
+
+  // ---- PCG (textbook; FP64 recurrences, scalars kept on the device)
+  template <typename Aop, typename Mop>
+  int pcg(int64_t n, Aop &&A, Mop &&M, const double *f, double *x, double rtol, int maxit,
+          double *rel_out) {
+    vr.ensure(n); vz.ensure(n); vp.ensure(n); vq.ensure(n);
+    dwork.ensure(gram_work_size(std::max(an.n, an.nG), 256, 1));
+    double *d_rz = dscal.p, *d_pq = dscal.p + 1, *d_alpha = dscal.p + 2, *d_beta = dscal.p + 3,
+           *d_rr = dscal.p + 4, *d_rznew = dscal.p + 5, *d_ff = dscal.p + 6;
+    NSP_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), st));
+    NSP_CUDA(cudaMemcpyAsync(vr.p, f, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_dot(f, f, n, d_ff, dwork.p, st);
+    NSP_CUDA(cudaMemcpyAsync(hscal, d_ff, sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    const double fn = std::sqrt(hscal[0]);
+    *rel_out = 0.0;
+    if (fn == 0.0) return 0;
+    M(vr.p, vz.p);
+    NSP_CUDA(cudaMemcpyAsync(vp.p, vz.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_dot(vr.p, vz.p, n, d_rz, dwork.p, st);
+    int it = 0;
+    double rel = 1.0;
+    while (it < maxit) {
+      A(vp.p, vq.p);
+      launch_dot(vp.p, vq.p, n, d_pq, dwork.p, st);
+      launch_pcg_scalars(d_rz, nullptr, d_pq, d_alpha, nullptr, st);
+      launch_axpby(n, d_alpha, 1.0, vp.p, 1.0, x, st);
+      launch_axpby(n, d_alpha, -1.0, vq.p, 1.0, vr.p, st);
+      ++it;
+      launch_dot(vr.p, vr.p, n, d_rr, dwork.p, st);
+      NSP_CUDA(cudaMemcpyAsync(hscal, d_rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      rel = std::sqrt(std::max(hscal[0], 0.0)) / fn;
+      if (!(rel > rtol)) break;
+      M(vr.p, vz.p);
+      launch_dot(vr.p, vz.p, n, d_rznew, dwork.p, st);
+      launch_pcg_scalars(d_rznew, d_rz, nullptr, nullptr, d_beta, st);
+      launch_axpby(n, d_beta, 1.0, vp.p, 0.0, vp.p, st);         // p = beta p
+      launch_axpby(n, nullptr, 1.0, vz.p, 1.0, vp.p, st);        // p += z
+      NSP_CUDA(cudaMemcpyAsync(d_rz, d_rznew, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    *rel_out = rel;
+    return it;
+  }
+
+  void solve(const double *b_user, double *x_user, double rtol, int maxit, int form) override {
+    auto t0 = Clock::now();
+    const int64_t n = an.n, nI = an.nI, nG = an.nG;
+    vb.ensure(n); vx.ensure(n); vt.ensure(n); vu.ensure(n); vf.ensure(n);
+    dwork.ensure(gram_work_size(std::max(an.n, an.nG), 256, 1));
+    ensure_ws(1);
+    if (form == NSP_OUTER_AUTO) form = std::is_same<T, double>::value ? NSP_OUTER_SCHUR : NSP_OUTER_FULL;
+    // internal layout of full vectors: [interior (FI order); interface (FG order)]
+    double *bI = vb.p, *bG = vb.p + nI;
+    launch_gather_rows<double, double>(i2g_I.p, nI, b_user, bI, 1, st);
+    launch_gather_rows<double, double>(i2g_G.p, nG, b_user, bG, 1, st);
+    double rel = 0.0;
+    int it = 0;
+    if (form == NSP_OUTER_SCHUR) {
+      // f = b_G - A_GI A_I^{-1} b_I
+      solve_I64(bI, vt.p);
+      launch_spmm<double>(A_GI.d64(), vt.p, vf.p, 1, -1.0, bG, 1.0, st);
+      double *w = vx.p + nI;
+      it = pcg(nG, [&](const double *p, double *q) { schur64(p, q); },
+               [&](const double *r, double *z) { m2_apply_internal(r, z); }, vf.p, w, rtol,
+               maxit, &rel);
+      // x_I = A_I^{-1}(b_I - A_IG w)
+      launch_spmm<double>(A_IG.d64(), w, vt.p, 1, -1.0, bI, 1.0, st);
+      solve_I64(vt.p, vx.p);
+    } else {
+      // x0 = (A_I^{-1} b_I, 0); r0 = b - A x0; PCG on A d = r0 with the block preconditioner
+      double *x0 = vu.p;
+      solve_I64(bI, x0);
+      NSP_CUDA(cudaMemsetAsync(x0 + nI, 0, nG * sizeof(double), st));
+      auto Aop = [&](const double *v, double *o) {
+        launch_spmm<double>(A_I.d64(), v, o, 1, 1.0, nullptr, 0.0, st);
+        launch_spmm<double>(A_IG.d64(), v + nI, o, 1, 1.0, o, 1.0, st);
+        launch_spmm<double>(A_GI.d64(), v, o + nI, 1, 1.0, nullptr, 0.0, st);
+        launch_spmm<double>(A_G.d64(), v + nI, o + nI, 1, 1.0, o + nI, 1.0, st);
+      };
+      Aop(x0, vf.p);
+      launch_axpby(n, nullptr, 1.0, vb.p, -1.0, vf.p, st);   // r0 = b - A x0
+      pfull_t.ensure(n);
+      auto Mop = [&](const double *r, double *z) {
+        double *t = pfull_t.p;            // t_I = A_I^{-1} r_I, t_G = r_G - A_GI t_I
+        solve_I64(r, t);
+        launch_spmm<double>(A_GI.d64(), t, t + nI, 1, -1.0, r + nI, 1.0, st);
+        m2_apply_internal(t + nI, z + nI);
+        launch_spmm<double>(A_IG.d64(), z + nI, t, 1, -1.0, r, 1.0, st);   // r_I - A_IG z_G
+        solve_I64(t, z);
+      };
+      it = pcg(n, Aop, Mop, vf.p, vx.p, rtol, maxit, &rel);
+      launch_axpby(n, nullptr, 1.0, x0, 1.0, vx.p, st);     // x = x0 + d
+    }
+    // back to the caller's order; true residual ||b - A x|| / ||b|| in FP64
+    launch_scatter_rows<double, double>(i2g_I.p, nI, vx.p, x_user, 1, st);
+    launch_scatter_rows<double, double>(i2g_G.p, nG, vx.p + nI, x_user, 1, st);
+    CsrDev<double> Af{(int32_t)n, (int32_t)n, an.nnz, full_rowptr.p, full_col.p, Aval.p};
+    launch_spmm<double>(Af, x_user, vt.p, 1, -1.0, b_user, 1.0, st);
+    launch_dot(vt.p, vt.p, n, dscal.p + 8, dwork.p, st);
+    launch_dot(b_user, b_user, n, dscal.p + 9, dwork.p, st);
+    NSP_CUDA(cudaMemcpyAsync(hscal + 8, dscal.p + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    info.it_pcg = it;
+    info.pcg_residual = rel;
+    info.final_residual = hscal[9] > 0 ? std::sqrt(hscal[8] / hscal[9]) : 0.0;
+    info.ms_solve = ms_since(t0);
+    if (rel > rtol) throw Error(NSP_ERR_NOT_CONVERGED, "outer PCG did not converge");
+  }
+  DBuf<double> pfull_t;
+
+  // ---- caller-order wrappers used by tests
+  void schur_apply_user(const void *X, void *Yv, int sc) override {
+    ensure_ws(sc);
+    DBuf<T> xi((size_t)an.nG * sc), yi((size_t)an.nG * sc);
+    launch_gather_rows<T, T>(i2u_G.p, an.nG, (const T *)X, xi.p, sc, st);
+    schur_apply(xi.p, yi.p, sc, true);
+    launch_scatter_rows<T, T>(i2u_G.p, an.nG, yi.p, (T *)Yv, sc, st);
+    sync();
+  }
+  void factor_solve_user(int which, const void *B, void *X, int sc) override {
+    ensure_ws(sc);
+    const int64_t nn = which == 0 ? an.nI : an.nG;
+    const int64_t *perm = which == 0 ? i2u_I.p : i2u_G.p;
+    DBuf<T> bi((size_t)nn * sc), xi((size_t)nn * sc);
+    launch_gather_rows<T, T>(perm, nn, (const T *)B, bi.p, sc, st);
+    if (which == 0) solve_I(bi.p, xi.p, sc);
+    else solve_G(bi.p, xi.p, sc);
+    launch_scatter_rows<T, T>(perm, nn, xi.p, (T *)X, sc, st);
+    sync();
+  }
+  void get_basis(double *Zh, double *Sh, int32_t *rk) override {
+    if (rk) *rk = rank;
+    if (rank <= 0) return;
+    if (Sh) {
+      NSP_CUDA(cudaMemcpyAsync(Sh, Sigma.p, rank * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    if (Zh) {
+      DBuf<double> zu((size_t)an.nG * k);
+      launch_scatter_rows<T, double>(i2u_G.p, an.nG, Zt.p, zu.p, k, st);
+      std::vector<double> hz((size_t)an.nG * k);
+      NSP_CUDA(cudaMemcpyAsync(hz.data(), zu.p, hz.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      for (int64_t i = 0; i < an.nG; ++i)
+        for (int j = 0; j < rank; ++j) Zh[i * rank + j] = hz[(size_t)i * k + j];
+    }
+    sync();
+  }
+  void get_intermediate(int which, double *out) override {
+    require(keep, NSP_ERR_INVALID_ARG, "build without keep_intermediates");
+    require(which >= 0 && which <= 3, NSP_ERR_INVALID_ARG, "intermediate id");
+    const T *src = which == 0 ? G.p : which == 1 ? E.p : which == 2 ? Y.p : U.p;
+    const int cols = which == 3 ? k : s;
+    DBuf<double> o((size_t)an.nG * std::max(cols, 1));
+    launch_scatter_rows<T, double>(i2u_G.p, an.nG, src, o.p, cols, st);
+    std::vector<double> h((size_t)an.nG * cols);
+    NSP_CUDA(cudaMemcpyAsync(h.data(), o.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    const int oc = which == 3 ? rank : s;
+    for (int64_t i = 0; i < an.nG; ++i)
+      for (int j = 0; j < oc; ++j) out[i * oc + j] = h[(size_t)i * cols + j];
+  }
+  void get_factor(int block, int64_t *order, double *L, int64_t nb) override {
+    require(block >= 0 && block <= an.nblocks, NSP_ERR_INVALID_ARG, "block id");
+    const bool g = block == an.nblocks;
+    const Forest &F = g ? FG.h : FI.h;
+    const int b = g ? 0 : block;
+    const int64_t off = F.block_off[b], n_b = F.block_off[b + 1] - off;
+    require(nb == n_b, NSP_ERR_INVALID_ARG, "n_b does not match the block size");
+    std::vector<T> pan(F.panel_size);
+    NSP_CUDA(cudaMemcpyAsync(pan.data(), g ? panelG.p : panelI.p, F.panel_size * sizeof(T),
+                             cudaMemcpyDeviceToHost, st));
+    sync();
+    for (int64_t t = 0; t < n_b; ++t) order[t] = g ? an.i2g_G[off + t] : an.i2g_I[off + t];
+    std::fill(L, L + n_b * n_b, 0.0);
+    for (int J = 0; J < F.nsn; ++J) {
+      if (F.sn_block[J] != b) continue;
+      const int w = F.sn_w[J], m = F.sn_m[J];
+      const T *Pj = pan.data() + F.sn_panel[J];
+      // L11 = inv(Pj_top) by forward substitution; L21 = Pj_bot L11
+      std::vector<double> Li((size_t)w * w, 0.0), L11((size_t)w * w, 0.0);
+      for (int r = 0; r < w; ++r)
+        for (int c = 0; c <= r; ++c) Li[r + (size_t)c * w] = (double)Pj[r + (size_t)c * m];
+      for (int c = 0; c < w; ++c)
+        for (int r = c; r < w; ++r) {
+          double v = (r == c) ? 1.0 : 0.0;
+          for (int t = c; t < r; ++t) v -= Li[r + (size_t)t * w] * L11[t + (size_t)c * w];
+          L11[r + (size_t)c * w] = v / Li[r + (size_t)r * w];
+        }
+      const int64_t first = F.sn_first[J] - off;
+      for (int c = 0; c < w; ++c) {
+        for (int r = c; r < w; ++r)
+          L[(first + r) + (first + c) * n_b] = L11[r + (size_t)c * w];
+        for (int r = w; r < m; ++r) {
+          double v = 0.0;
+          for (int t = c; t < w; ++t) v += (double)Pj[r + (size_t)t * m] * L11[t + (size_t)c * w];
+          const int64_t row = F.rows[F.sn_rowptr[J] + r] - off;
+          L[row + (first + c) * n_b] = v;
+        }
+      }
+    }
+  }
+};
+
+}  // namespace nsp
+
+// ------------------------------------------------------------------ C ABI
+struct nsp_handle {
+  std::unique_ptr<nsp::EngineBase> eng;
+  nsp_params prm{};
+};
+
+static nsp_status guard(const std::function<void()> &f) {
+  try {
+    f();
+    return NSP_OK;
+  } catch (const nsp::Error &e) {
+    return e.status;
+  } catch (const std::bad_alloc &) {
+    return NSP_ERR_OOM;
+  } catch (...) {
+    return NSP_ERR_INVALID_ARG;
+  }
+}
+
+extern "C" {
+
+void nsp_default_params(nsp_params *prm) {
+  if (!prm) return;
+  std::memset(prm, 0, sizeof(*prm));
+  prm->k = 16;
+  prm->p = 10;
+  prm->eps_inner = 0.1;
+  prm->eps_trunc_rel = 1e-10;
+  prm->drop_tol = 1e-6;
+  prm->max_inner_it = 500;
+  prm->seed = 210112164ull;
+  prm->sketch = nullptr;
+  prm->precision = NSP_FP32;
+  prm->outer_form = NSP_OUTER_AUTO;
+  prm->inner_form = NSP_FORM_SGAMMA;
+  prm->keep_intermediates = 0;
+  prm->stream = nullptr;
+}
+
+const char *nsp_status_string(nsp_status s) {
+  switch (s) {
+    case NSP_OK: return "ok";
+    case NSP_ERR_INVALID_ARG: return "invalid argument";
+    case NSP_ERR_NOT_DBBD: return "partition is not doubly bordered block diagonal";
+    case NSP_ERR_NOT_SPD: return "matrix block is not positive definite";
+    case NSP_ERR_BREAKDOWN: return "block PCG breakdown";
+    case NSP_ERR_NOT_CONVERGED: return "iteration did not converge";
+    case NSP_ERR_TIMEOUT: return "device wait timed out";
+    case NSP_ERR_CUDA: return "CUDA error";
+    case NSP_ERR_OOM: return "out of device memory";
+    case NSP_ERR_UNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+static nsp::EngineBase *make_engine(const nsp_csr *A, const int64_t *rp, const int32_t *ci,
+                                    const nsp_partition *P, const nsp_params *prm) {
+  cudaStream_t st = (cudaStream_t)prm->stream;
+  if (prm->precision == NSP_FP64) return new nsp::Engine<double>(A, rp, ci, P, st);
+  if (prm->precision == NSP_FP32) return new nsp::Engine<float>(A, rp, ci, P, st);
+  throw nsp::Error(NSP_ERR_INVALID_ARG, "precision");
+}
+
+nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params *prm,
+                     nsp_handle **out) {
+  if (!out) return NSP_ERR_INVALID_ARG;
+  *out = nullptr;
+  auto h = std::make_unique<nsp_handle>();
+  nsp_status s = guard([&] {
+    nsp::validate_csr(A);
+    nsp::require(prm != nullptr, NSP_ERR_INVALID_ARG, "params");
+    h->prm = *prm;
+    std::vector<int64_t> rp;
+    std::vector<int32_t> ci;
+    const int64_t *rpp = A->rowptr;
+    const int32_t *cip = A->col;
+    if (A->on_device) {  // pattern is analysed on the host
+      rp.resize(A->n + 1);
+      NSP_CUDA(cudaMemcpy(rp.data(), A->rowptr, (A->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+      ci.resize(rp[A->n]);
+      NSP_CUDA(cudaMemcpy(ci.data(), A->col, ci.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+      rpp = rp.data();
+      cip = ci.data();
+    }
+    h->eng.reset(make_engine(A, rpp, cip, P, prm));
+    h->eng->factorize(A->val, A->on_device != 0);
+    h->eng->construct(h->prm);
+  });
+  if (s == NSP_OK) *out = h.release();
+  return s;
+}
+
+nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device, const nsp_params *prm) {
+  if (!h || !h->eng || !val) return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    if (prm) {
+      nsp::require(prm->precision == h->prm.precision, NSP_ERR_INVALID_ARG, "precision change");
+      void *stream = h->prm.stream;
+      h->prm = *prm;
+      h->prm.stream = stream;
+    }
+    h->eng->factorize(val, on_device != 0);
+    h->eng->construct(h->prm);
+  });
+}
+
+nsp_status nsp_apply(const nsp_handle *h, const double *r, double *z) {
+  if (!h || !h->eng || !r || !z) return NSP_ERR_INVALID_ARG;
+  return guard([&] { h->eng->apply_m2(r, z); });
+}
+
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+nsp_status nsp_solve(const nsp_handle *h, const double *b, double *x, double rtol, int32_t maxit,
+                     nsp_info *info) {
+  if (!h || !h->eng || !b || !x || !(rtol > 0) || maxit < 1) return NSP_ERR_INVALID_ARG;
+  nsp_status s = guard([&] {
+    const int64_t n = h->eng->info.n;
+    cudaStream_t st = h->eng->st;
+    const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
+    nsp::DBuf<double> db, dx;
+    const double *bp = b;
+    double *xp = x;
+    if (!bd) {
+      db.alloc(n);
+      NSP_CUDA(cudaMemcpyAsync(db.p, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      bp = db.p;
+    }
+    if (!xd) {
+      dx.alloc(n);
+      xp = dx.p;
+    }
+    nsp_status inner = NSP_OK;
+    try {
+      h->eng->solve(bp, xp, rtol, maxit, h->prm.outer_form);
+    } catch (const nsp::Error &e) {
+      if (e.status != NSP_ERR_NOT_CONVERGED) throw;
+      inner = e.status;
+    }
+    if (!xd) {
+      NSP_CUDA(cudaMemcpyAsync(x, xp, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      NSP_CUDA(cudaStreamSynchronize(st));
+    }
+    if (inner != NSP_OK) throw nsp::Error(inner, "not converged");
+  });
+  if (info) *info = h->eng->info;
+  return s;
+}
+
+nsp_status nsp_schur_apply(const nsp_handle *h, const void *X, void *Y, int32_t s) {
+  if (!h || !h->eng || !X || !Y || s < 1 || s > 256) return NSP_ERR_INVALID_ARG;
+  return guard([&] { h->eng->schur_apply_user(X, Y, s); });
+}
+
+nsp_status nsp_factor_solve(const nsp_handle *h, int32_t which, const void *B, void *X, int32_t s) {
+  if (!h || !h->eng || !B || !X || s < 1 || s > 256 || (which != 0 && which != 1))
+    return NSP_ERR_INVALID_ARG;
+  return guard([&] { h->eng->factor_solve_user(which, B, X, s); });
+}
+
+nsp_status nsp_get_basis(const nsp_handle *h, double *Z, double *Sigma, int32_t *rank) {
+  if (!h || !h->eng) return NSP_ERR_INVALID_ARG;
+  return guard([&] { h->eng->get_basis(Z, Sigma, rank); });
+}
+
+nsp_status nsp_get_intermediate(const nsp_handle *h, int32_t which, double *out) {
+  if (!h || !h->eng || !out) return NSP_ERR_INVALID_ARG;
+  return guard([&] { h->eng->get_intermediate(which, out); });
+}
+
+nsp_status nsp_get_factor(const nsp_handle *h, int32_t block, int64_t *order, double *L, int64_t n_b) {
+  if (!h || !h->eng || !order || !L) return NSP_ERR_INVALID_ARG;
+  return guard([&] { h->eng->get_factor(block, order, L, n_b); });
+}
+
+nsp_status nsp_get_info(const nsp_handle *h, nsp_info *info) {
+  if (!h || !h->eng || !info) return NSP_ERR_INVALID_ARG;
+  *info = h->eng->info;
+  return NSP_OK;
+}
+
+nsp_status nsp_destroy(nsp_handle *h) {
+  if (!h) return NSP_ERR_INVALID_ARG;
+  delete h;
+  return NSP_OK;
+}
+
+nsp_status nsp_gaussian(uint64_t seed, int64_t count, double *out, void *stream) {
+  if (!out || count < 0) return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    nsp::launch_gaussian<double>(seed, count, out, (cudaStream_t)stream);
+    NSP_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+// Host-only analysis (no CUDA call): validation, DBBD check, orderings and symbolic
+// factorization statistics.
+nsp_status nsp_analyze(const nsp_csr *A, const nsp_partition *P, nsp_info *info) {
+  if (!info) return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    nsp::validate_csr(A);
+    nsp::require(!A->on_device, NSP_ERR_INVALID_ARG, "nsp_analyze needs host CSR");
+    nsp::Analysis an;
+    nsp::analyze(A, A->rowptr, A->col, P, an);
+    std::memset(info, 0, sizeof(*info));
+    info->n = an.n;
+    info->n_interior = an.nI;
+    info->n_gamma = an.nG;
+    info->nblocks = an.nblocks;
+    info->nnz_L_interior = an.FI.nnz_L;
+    info->nnz_L_gamma = an.FG.nnz_L;
+    info->n_supernodes = an.FI.nsn + an.FG.nsn;
+    info->ms_analyze = an.ms;
+    info->failed_block = -1;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,470 @@
+// BLAS-like kernels of the hot path: CSR x dense-block SpMM (A_IG, A_GI, A_G), row
+// gathers/scatters between the caller's and the factor's orderings, block-CG Gram products
+// X^T Y, tall-skinny block updates, column norms, the Philox sketch generator and the FP64
+// vector kernels of the outer PCG.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace nsp {
+namespace {
+
+constexpr int BT = 256;
+
+// ---------------------------------------------------------------- SpMM
+// Y[i, :] = alpha * sum_e val[e] X[col[e], :] + beta * C[i, :]. A group of L lanes per row
+// (L = power of two >= s, at most 32) walks the row's entries; lanes cover the s columns.
+template <typename T>
+__global__ void __launch_bounds__(BT) k_spmm(CsrDev<T> A, const T *__restrict__ X,
+                                             T *Y, int s, int lanes, T alpha, const T *C,
+                                             T beta) {
+  const int rows_per_block = BT / lanes;
+  const int lane = threadIdx.x % lanes;
+  const int64_t i = (int64_t)blockIdx.x * rows_per_block + threadIdx.x / lanes;
+  if (i >= A.nrows) return;
+  const int e0 = A.rowptr[i], e1 = A.rowptr[i + 1];
+  for (int c = lane; c < s; c += lanes) {
+    T acc = T(0);
+    for (int e = e0; e < e1; ++e) acc += A.val[e] * X[(size_t)A.col[e] * s + c];
+    T out = alpha * acc;
+    if (C) out += beta * C[(size_t)i * s + c];
+    Y[(size_t)i * s + c] = out;
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_gather_rows(const int64_t *perm, int64_t nrows, const Ti *in, To *out, int s) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nrows * s) return;
+  const int64_t i = idx / s;
+  const int c = (int)(idx % s);
+  const int64_t src = perm ? perm[i] : i;
+  out[idx] = (To)in[(size_t)src * s + c];
+}
+
+template <typename Ti, typename To>
+__global__ void k_scatter_rows(const int64_t *perm, int64_t nrows, const Ti *in, To *out, int s) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nrows * s) return;
+  const int64_t i = idx / s;
+  const int c = (int)(idx % s);
+  const int64_t dst = perm ? perm[i] : i;
+  out[(size_t)dst * s + c] = (To)in[idx];
+}
+
+template <typename T>
+__global__ void k_gather_values(const int64_t *src, int64_t count, const double *Aval, T *out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) out[e] = (T)Aval[src[e]];
+}
+
+// ---------------------------------------------------------------- Gram X^T Y
+// Stage 1: CTA (chunk, ta, tb) sums rows [chunk*rpc, ...) for the 64 x 64 output tile
+// (ta, tb); stage 2 adds the chunk partials in chunk order (deterministic).
+constexpr int GT = 64, GR = 32;
+
+template <typename T, typename AccT>
+__global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
+                                                     const T *__restrict__ Y, int64_t n,
+                                                     int s1, int s2, int64_t rpc,
+                                                     double *work) {
+  __shared__ T Xs[GR][GT + 1];
+  __shared__ T Ys[GR][GT + 1];
+  const int chunk = blockIdx.x;
+  const int a0 = blockIdx.y * GT, b0 = blockIdx.z * GT;
+  const int64_t i0 = (int64_t)chunk * rpc;
+  const int64_t i1 = min(n, i0 + rpc);
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  AccT acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = AccT(0);
+  for (int64_t ib = i0; ib < i1; ib += GR) {
+    for (int q = tid; q < GR * GT; q += BT) {
+      const int r = q / GT, c = q % GT;
+      const int64_t row = ib + r;
+      Xs[r][c] = (row < i1 && a0 + c < s1) ? X[(size_t)row * s1 + a0 + c] : T(0);
+      Ys[r][c] = (row < i1 && b0 + c < s2) ? Y[(size_t)row * s2 + b0 + c] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int r = 0; r < GR; ++r) {
+      AccT xa[4], yb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xa[i] = (AccT)Xs[r][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) yb[j] = (AccT)Ys[r][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += xa[i] * yb[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < s1 && b < s2) work[((size_t)chunk * s1 + a) * s2 + b] = (double)acc[i][j];
+    }
+}
+
+__global__ void k_gram_reduce(const double *work, int nchunks, int64_t entries, double *C) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= entries) return;
+  double acc = 0.0;
+  for (int c = 0; c < nchunks; ++c) acc += work[(size_t)c * entries + e];
+  C[e] = acc;
+}
+
+int gram_chunks(int64_t n, int s1, int s2) {
+  const int tiles = ceil_div(s1, GT) * ceil_div(s2, GT);
+  int target = std::max(1, 2 * 152 / tiles);
+  int maxc = std::max<int64_t>(1, (n + GR - 1) / GR);
+  return std::max(1, std::min(target, maxc));
+}
+
+// ---------------------------------------------------------------- block update
+// Out = A M + beta C, A n x s1 (T), M s1 x s2 (FP64), 32 rows per CTA, s1 in chunks of 32.
+constexpr int UR = 32, UK = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(BT) k_block_update(const T *__restrict__ A,
+                                                     const double *__restrict__ M, int64_t n,
+                                                     int s1, int s2, T scale, const T *C,
+                                                     T beta, T *Out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *As = reinterpret_cast<T *>(smem_raw);  // [UR][UK + 1]
+  T *Ms = As + UR * (UK + 1);               // [UK][s2]
+  const int64_t i0 = (int64_t)blockIdx.x * UR;
+  const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;  // 8 row groups x 32 lanes
+  constexpr int MAXJ = 8;                                     // s2 <= 256
+  T acc[4][MAXJ];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) acc[i][j] = T(0);
+  for (int kc = 0; kc < s1; kc += UK) {
+    for (int q = tid; q < UR * UK; q += BT) {
+      const int r = q / UK, k = q % UK;
+      As[r * (UK + 1) + k] = (i0 + r < n && kc + k < s1) ? A[(size_t)(i0 + r) * s1 + kc + k] : T(0);
+    }
+    for (int q = tid; q < UK * s2; q += BT) {
+      const int k = q / s2, c = q % s2;
+      Ms[q] = (kc + k < s1) ? (T)M[(size_t)(kc + k) * s2 + c] : T(0);
+    }
+    __syncthreads();
+    for (int k = 0; k < UK; ++k) {
+      T a[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[(ty + 8 * i) * (UK + 1) + k];
+#pragma unroll
+      for (int j = 0; j < MAXJ; ++j) {
+        const int c = tx + 32 * j;
+        if (c < s2) {
+          const T mv = Ms[k * s2 + c];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) acc[i][j] += a[i] * mv;
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t row = i0 + ty + 8 * i;
+    if (row >= n) continue;
+#pragma unroll
+    for (int j = 0; j < MAXJ; ++j) {
+      const int c = tx + 32 * j;
+      if (c < s2) {
+        T v = scale * acc[i][j];
+        if (C) v += beta * C[(size_t)row * s2 + c];
+        Out[(size_t)row * s2 + c] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- column sums of squares
+template <typename T>
+__global__ void __launch_bounds__(BT) k_colsq_partial(const T *X, int64_t n, int s, int64_t rpc,
+                                                      double *work) {
+  __shared__ double red[8][33];
+  const int64_t i0 = (int64_t)blockIdx.x * rpc, i1 = min(n, i0 + rpc);
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int c0 = 0; c0 < s; c0 += 32) {
+    const int c = c0 + tx;
+    double acc = 0.0;
+    if (c < s)
+      for (int64_t i = i0 + ty; i < i1; i += 8) {
+        const double v = (double)X[(size_t)i * s + c];
+        acc += v * v;
+      }
+    red[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && c < s) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += red[q][tx];
+      work[(size_t)blockIdx.x * s + c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC'11):
+// 10 rounds of (two 32x32->64 multiplies, xor with key and swapped halves), Weyl key bumps.
+__device__ __forceinline__ void philox_round(uint32_t &c0, uint32_t &c1, uint32_t &c2,
+                                             uint32_t &c3, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+  const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+  const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+  const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+  c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+}
+
+__device__ void philox4x32_10(uint32_t ctr[4], uint32_t k0, uint32_t k1) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    philox_round(c0, c1, c2, c3, k0, k1);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  ctr[0] = c0; ctr[1] = c1; ctr[2] = c2; ctr[3] = c3;
+}
+
+// Element i: counter (i/2 low word, i/2 high word, 0, 0), key = seed; uniforms
+// u1 = (x0 + 0.5) 2^-32, u2 = (x1 + 0.5) 2^-32; Box-Muller radius sqrt(-2 ln u1), angle
+// 2 pi u2; even i takes the cosine, odd i the sine.
+template <typename T>
+__global__ void k_gaussian(uint64_t seed, int64_t count, T *out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  const uint64_t q = (uint64_t)i >> 1;
+  uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), 0u, 0u};
+  philox4x32_10(ctr, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u1 = ((double)ctr[0] + 0.5) * 2.3283064365386963e-10;
+  const double u2 = ((double)ctr[1] + 0.5) * 2.3283064365386963e-10;
+  const double rad = sqrt(-2.0 * log(u1));
+  const double ang = 6.283185307179586 * u2;
+  out[i] = (T)((i & 1) ? rad * sin(ang) : rad * cos(ang));
+}
+
+// ---------------------------------------------------------------- FP64 vectors
+__global__ void __launch_bounds__(BT) k_dot_partial(const double *x, const double *y, int64_t n,
+                                                    int64_t rpc, double *work) {
+  __shared__ double red[BT];
+  const int64_t i0 = (int64_t)blockIdx.x * rpc, i1 = min(n, i0 + rpc);
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) acc += x[i] * y[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = BT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) work[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum(const double *work, int count, double *out) {
+  __shared__ double red[BT];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < count; i += BT) acc += work[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = BT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_axpby(int64_t n, const double *a_ptr, double a_sign, const double *x,
+                        double b, double *y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double a = a_sign * (a_ptr ? *a_ptr : 1.0);
+  y[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_scale_cols(double *X, int64_t n, int s, const double *scale, int take_sqrt) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n * s) return;
+  const double f = scale[idx % s];
+  X[idx] *= take_sqrt ? sqrt(f) : f;
+}
+
+__global__ void k_pcg_scalars(const double *rz_new, const double *rz_old, const double *pq,
+                              double *alpha, double *beta) {
+  if (threadIdx.x != 0) return;
+  if (pq && alpha) *alpha = *rz_new / *pq;
+  if (rz_old && beta) *beta = *rz_new / *rz_old;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename T>
+void launch_spmm(const CsrDev<T> &A, const T *X, T *Y, int s, T alpha, const T *C, T beta,
+                 cudaStream_t stream) {
+  if (A.nrows <= 0 || s <= 0) return;
+  int lanes = 1;
+  while (lanes < s && lanes < 32) lanes <<= 1;
+  const int rpb = BT / lanes;
+  k_spmm<T><<<ceil_div(A.nrows, rpb), BT, 0, stream>>>(A, X, Y, s, lanes, alpha, C, beta);
+  NSP_LAUNCH_CHECK();
+}
+
+template <typename Ti, typename To>
+void launch_gather_rows(const int64_t *perm, int64_t nrows, const Ti *in, To *out, int s,
+                        cudaStream_t stream) {
+  const int64_t tot = nrows * s;
+  if (tot <= 0) return;
+  k_gather_rows<Ti, To><<<ceil_div(tot, BT), BT, 0, stream>>>(perm, nrows, in, out, s);
+  NSP_LAUNCH_CHECK();
+}
+
+template <typename Ti, typename To>
+void launch_scatter_rows(const int64_t *perm, int64_t nrows, const Ti *in, To *out, int s,
+                         cudaStream_t stream) {
+  const int64_t tot = nrows * s;
+  if (tot <= 0) return;
+  k_scatter_rows<Ti, To><<<ceil_div(tot, BT), BT, 0, stream>>>(perm, nrows, in, out, s);
+  NSP_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_gather_values(const int64_t *src, int64_t count, const double *Aval, T *out,
+                          cudaStream_t stream) {
+  if (count <= 0) return;
+  k_gather_values<T><<<ceil_div(count, BT), BT, 0, stream>>>(src, count, Aval, out);
+  NSP_LAUNCH_CHECK();
+}
+
+size_t gram_work_size(int64_t n, int s1, int s2) {
+  const int ch = gram_chunks(n, s1, s2);
+  const size_t g = (size_t)ch * s1 * s2;
+  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256));
+  const size_t c = (size_t)cs * std::max(s1, s2);
+  return std::max<size_t>(std::max(g, c), 4 * 152 + 8);
+}
+
+template <typename T, typename AccT>
+void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C, double *work,
+                 cudaStream_t stream) {
+  if (s1 <= 0 || s2 <= 0) return;
+  const int ch = gram_chunks(n, s1, s2);
+  const int64_t rpc = ((n + ch - 1) / ch + GR - 1) / GR * GR;
+  dim3 grid(ch, ceil_div(s1, GT), ceil_div(s2, GT));
+  k_gram_partial<T, AccT><<<grid, BT, 0, stream>>>(X, Y, n, s1, s2, std::max<int64_t>(rpc, GR), work);
+  NSP_LAUNCH_CHECK();
+  const int64_t ent = (int64_t)s1 * s2;
+  k_gram_reduce<<<ceil_div(ent, BT), BT, 0, stream>>>(work, ch, ent, C);
+  NSP_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_block_update(const T *A, const double *M, int64_t n, int s1, int s2, T scale,
+                         const T *C, T beta, T *Out, cudaStream_t stream) {
+  if (n <= 0 || s2 <= 0) return;
+  require(s2 <= 256, NSP_ERR_UNSUPPORTED, "block update with more than 256 columns");
+  const size_t sm = sizeof(T) * (size_t)(UR * (UK + 1) + UK * s2);
+  static bool attr = false;
+  if (!attr) {
+    NSP_CUDA(cudaFuncSetAttribute(k_block_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(T) * (UR * (UK + 1) + UK * 256))));
+    attr = true;
+  }
+  k_block_update<T><<<ceil_div(n, UR), BT, sm, stream>>>(A, M, n, s1, s2, scale, C, beta, Out);
+  NSP_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_col_sumsq(const T *X, int64_t n, int s, double *colsq, double *work,
+                      cudaStream_t stream) {
+  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256));
+  const int64_t rpc = (n + cs - 1) / cs;
+  k_colsq_partial<T><<<(int)cs, BT, 0, stream>>>(X, n, s, std::max<int64_t>(rpc, 1), work);
+  NSP_LAUNCH_CHECK();
+  k_gram_reduce<<<ceil_div(s, BT), BT, 0, stream>>>(work, (int)cs, s, colsq);
+  NSP_LAUNCH_CHECK();
+}
+
+template <typename T>
+void launch_gaussian(uint64_t seed, int64_t count, T *out, cudaStream_t stream) {
+  if (count <= 0) return;
+  k_gaussian<T><<<ceil_div(count, BT), BT, 0, stream>>>(seed, count, out);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_dot(const double *x, const double *y, int64_t n, double *result, double *work,
+                cudaStream_t stream) {
+  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 1023) / 1024));
+  const int64_t rpc = (n + cs - 1) / cs;
+  k_dot_partial<<<(int)cs, BT, 0, stream>>>(x, y, n, std::max<int64_t>(rpc, 1), work);
+  NSP_LAUNCH_CHECK();
+  k_sum<<<1, BT, 0, stream>>>(work, (int)cs, result);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_axpby(int64_t n, const double *a_ptr, double a_sign, const double *x, double b,
+                  double *y, cudaStream_t stream) {
+  if (n <= 0) return;
+  k_axpby<<<ceil_div(n, BT), BT, 0, stream>>>(n, a_ptr, a_sign, x, b, y);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_scale_cols(double *X, int64_t n, int s, const double *scale, bool take_sqrt,
+                       cudaStream_t stream) {
+  if (n * s <= 0) return;
+  k_scale_cols<<<ceil_div(n * s, BT), BT, 0, stream>>>(X, n, s, scale, take_sqrt ? 1 : 0);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_pcg_scalars(const double *rz_new, const double *rz_old, const double *pq,
+                        double *alpha, double *beta, cudaStream_t stream) {
+  k_pcg_scalars<<<1, 32, 0, stream>>>(rz_new, rz_old, pq, alpha, beta);
+  NSP_LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------- instantiations
+template void launch_spmm<float>(const CsrDev<float> &, const float *, float *, int, float,
+                                 const float *, float, cudaStream_t);
+template void launch_spmm<double>(const CsrDev<double> &, const double *, double *, int, double,
+                                  const double *, double, cudaStream_t);
+#define NSP_GS(Ti, To)                                                                        \
+  template void launch_gather_rows<Ti, To>(const int64_t *, int64_t, const Ti *, To *, int,   \
+                                           cudaStream_t);                                     \
+  template void launch_scatter_rows<Ti, To>(const int64_t *, int64_t, const Ti *, To *, int,  \
+                                            cudaStream_t);
+NSP_GS(float, float)
+NSP_GS(double, double)
+NSP_GS(float, double)
+NSP_GS(double, float)
+template void launch_gather_values<float>(const int64_t *, int64_t, const double *, float *,
+                                          cudaStream_t);
+template void launch_gather_values<double>(const int64_t *, int64_t, const double *, double *,
+                                           cudaStream_t);
+template void launch_gram<float, float>(const float *, const float *, int64_t, int, int, double *,
+                                        double *, cudaStream_t);
+template void launch_gram<float, double>(const float *, const float *, int64_t, int, int, double *,
+                                         double *, cudaStream_t);
+template void launch_gram<double, double>(const double *, const double *, int64_t, int, int,
+                                          double *, double *, cudaStream_t);
+template void launch_block_update<float>(const float *, const double *, int64_t, int, int,
+                                         float, const float *, float, float *, cudaStream_t);
+template void launch_block_update<double>(const double *, const double *, int64_t, int, int,
+                                          double, const double *, double, double *,
+                                          cudaStream_t);
+template void launch_col_sumsq<float>(const float *, int64_t, int, double *, double *, cudaStream_t);
+template void launch_col_sumsq<double>(const double *, int64_t, int, double *, double *,
+                                       cudaStream_t);
+template void launch_gaussian<float>(uint64_t, int64_t, float *, cudaStream_t);
+template void launch_gaussian<double>(uint64_t, int64_t, double *, cudaStream_t);
+
+}  // namespace nsp

@@ -1,0 +1,128 @@
+// Kernel launchers of the hot path. Every launcher enqueues on the given stream and
+// never synchronizes. Blocks of vectors are row-major (entry (i, j) at [i*s + j]).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace nsp {
+
+// Device view of a supernodal forest (see symbolic.h for the meaning of each array).
+struct ForestDev {
+  int32_t nsn = 0;
+  int64_t n = 0;
+  const int32_t *sn_first = nullptr, *sn_w = nullptr, *sn_m = nullptr, *sn_block = nullptr;
+  const int64_t *sn_rowptr = nullptr, *sn_panel = nullptr, *sn_front = nullptr, *sn_upd = nullptr;
+  const int32_t *rows = nullptr, *relmap = nullptr, *ch_ptr = nullptr, *ch_list = nullptr;
+  const int64_t *gptr = nullptr, *gsrc = nullptr;
+  const int64_t *asm_ptr = nullptr, *asm_dst = nullptr, *asm_src = nullptr;
+};
+
+// A (sub)matrix in CSR with int32 indices on the device.
+template <typename T>
+struct CsrDev {
+  int32_t nrows = 0, ncols = 0;
+  int64_t nnz = 0;
+  const int32_t *rowptr = nullptr, *col = nullptr;
+  const T *val = nullptr;
+};
+
+// Work item of a level: one tile of TM rows of supernode sn, starting at row r0.
+struct TileItem {
+  int32_t sn;
+  int32_t r0;
+};
+
+// ---- numeric factorization (k_factor.cu) -----------------------------------------
+// Multifrontal partial Cholesky of the supernodes level_sn[0..count) (one CTA each), then
+// the panel [inv(L_JJ); L_J2 inv(L_JJ)] (m x w, column-major) written to panel.
+// block_of_sn gives the block id reported on a non-positive pivot.
+template <typename T>
+void launch_factor_level(const ForestDev &f, const int32_t *level_sn, int count,
+                         const double *Aval, T *front, T *panel, DevStatus *st,
+                         cudaStream_t stream);
+
+// ---- supernodal multi-RHS solves (k_solve.cu) ------------------------------------
+// Forward sweep over one level: for each item (sn, r0): rows [r0, r0+TM) of
+//   [y_J; u_J] = P_J f_top  (+ f_bot for update rows, minus sign),
+// f_top = B[J's columns] + children's update rows. Y, U outputs.
+// Backward: x_J = P_top^T y_J - P_bot^T x[struct rows] for output rows [r0, r0+TM).
+template <typename T>
+void launch_solve_fwd(const ForestDev &f, const TileItem *items, int nitems, int tm,
+                      const T *panel, const T *B, T *Y, T *U, int s, cudaStream_t stream);
+template <typename T>
+void launch_solve_bwd(const ForestDev &f, const TileItem *items, int nitems, int tm,
+                      const T *panel, const T *Y, T *X, int s, cudaStream_t stream);
+// rows per tile used by the solve kernels for s columns
+int solve_tile_rows(int s);
+
+// ---- BLAS-like kernels (k_blas.cu) ------------------------------------------------
+// Y = alpha * A X + beta * C  (C may be nullptr; Y may alias C)
+template <typename T>
+void launch_spmm(const CsrDev<T> &A, const T *X, T *Y, int s, T alpha, const T *C, T beta,
+                 cudaStream_t stream);
+// out[i*s+j] = (To) in[perm[i]*s + j]   (perm == nullptr: identity)
+template <typename Ti, typename To>
+void launch_gather_rows(const int64_t *perm, int64_t nrows, const Ti *in, To *out, int s,
+                        cudaStream_t stream);
+// out[perm[i]*s+j] = (To) in[i*s + j]
+template <typename Ti, typename To>
+void launch_scatter_rows(const int64_t *perm, int64_t nrows, const Ti *in, To *out, int s,
+                         cudaStream_t stream);
+// out[e] = (T) Aval[src[e]]
+template <typename T>
+void launch_gather_values(const int64_t *src, int64_t count, const double *Aval, T *out,
+                          cudaStream_t stream);
+// C (s1 x s2, FP64, row-major) = X^T Y for X (n x s1), Y (n x s2). work: scratch doubles,
+// at least gram_work_size(n, s1, s2). Deterministic. AccT = accumulation type.
+template <typename T, typename AccT>
+void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C,
+                 double *work, cudaStream_t stream);
+size_t gram_work_size(int64_t n, int s1, int s2);
+// Out (n x s2) = scale * A (n x s1) M (s1 x s2, FP64) + beta * C  (C may alias Out or be
+// nullptr)
+template <typename T>
+void launch_block_update(const T *A, const double *M, int64_t n, int s1, int s2, T scale,
+                         const T *C, T beta, T *Out, cudaStream_t stream);
+// X[i*s + j] *= scale[j]
+void launch_scale_cols(double *X, int64_t n, int s, const double *scale, bool take_sqrt,
+                       cudaStream_t stream);
+// colsq[j] = sum_i X[i*s+j]^2 (FP64), deterministic; work >= gram_work_size(n, s, 1)
+template <typename T>
+void launch_col_sumsq(const T *X, int64_t n, int s, double *colsq, double *work,
+                      cudaStream_t stream);
+// Philox4x32-10 + Box-Muller: out[i] ~ N(0,1), i in [0, count)
+template <typename T>
+void launch_gaussian(uint64_t seed, int64_t count, T *out, cudaStream_t stream);
+// FP64 vector helpers for the outer PCG: out[i] = a*x[i] + b*y[i] etc.
+void launch_dot(const double *x, const double *y, int64_t n, double *result, double *work,
+                cudaStream_t stream);
+void launch_axpby(int64_t n, const double *a_ptr, double a_sign, const double *x, double b,
+                  double *y, cudaStream_t stream);   // y = (a_sign * *a_ptr) x + b y
+void launch_pcg_scalars(const double *rz_new, const double *rz_old, const double *pq,
+                        double *alpha, double *beta, cudaStream_t stream);
+
+// ---- small dense FP64 core on one CTA (k_core.cu) ---------------------------------
+// Cholesky-QR with column drop: C (s x s) = W^T W; writes Rinv (s x s, zero outside the kept
+// columns) such that W Rinv has orthonormal kept columns, mask[j] = kept, *nkept.
+void launch_chol_drop(const double *C, int s, double drop_tol, double *Rinv, int32_t *mask,
+                      int32_t *nkept, cudaStream_t stream);
+// alpha (s x r) = PtQ^{-1} Rhs on the kept rows/cols (mask), zero elsewhere; sign scales.
+// Factor of PtQ kept in Lwork (s x s). Non-SPD PtQ -> DEV_BREAKDOWN.
+void launch_spd_solve_masked(const double *PtQ, const double *Rhs, int s, int r,
+                             const int32_t *mask, double sign, double *out, double *Lwork,
+                             DevStatus *st, cudaStream_t stream);
+// max_j sqrt(colsq[j]) / bnorm[j] -> *ratio
+void launch_max_ratio(const double *colsq, const double *bnorm, int s, double *ratio,
+                      cudaStream_t stream);
+void launch_sqrt_vec(const double *in, int s, double *out, cudaStream_t stream);
+// Nyström core (Algorithm 2 steps 5-10) on K = Y^T Y and C = G^T Y (s x s FP64):
+// writes Mix (s x k, row-major) with U = Y Mix, Sigma (k), *rank. work >= nystrom_work(s).
+void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
+                         double drop_tol, double *Mix, double *Sigma, int32_t *rank,
+                         double *work, cudaStream_t stream);
+size_t nystrom_work_size(int s);
+
+}  // namespace nsp

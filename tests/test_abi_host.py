@@ -1,0 +1,106 @@
+"""C-ABI checks that need no GPU: every declared symbol is exported, and the host-only
+analysis (validation, DBBD check, orderings, symbolic factorization) behaves."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import fixtures as F
+
+from ._util import lib_or_build, tiny_problem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "nsp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nsp_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    N = lib_or_build()
+    names = declared_functions()
+    assert len(names) >= 15
+    L = ctypes.CDLL(N.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(N.EXPORTS) == set(names)
+
+
+def test_status_strings():
+    N = lib_or_build()
+    for code in range(10):
+        assert N.lib().nsp_status_string(code)
+
+
+def _dense_nnz_chol(A, order):
+    M = A[order][:, order].toarray()
+    L = np.linalg.cholesky(M)
+    return int((np.abs(L) > 0).sum())
+
+
+@pytest.mark.parametrize("shape,nsub", [((12, 11), 2), ((9, 8, 7), 4), ((20, 20), 4)])
+def test_symbolic_counts_match_dense_cholesky(shape, nsub):
+    # with the caller's elimination order, nnz(L) of every interior block equals the nonzero
+    # count of the dense Cholesky factor of the permuted block (no cancellation in SPD
+    # diffusion matrices with positive weights)
+    N = lib_or_build()
+    A, part, perm = tiny_problem(shape, nsub)
+    info = N.nsp_analyze(A, part, nsub, perm)
+    ref = 0
+    for b in range(nsub):
+        order = [g for g in perm if part[g] == b]
+        ref += _dense_nnz_chol(A, order)
+    assert info["nnz_L_interior"] == ref
+    assert info["n_gamma"] == int((part < 0).sum())
+    assert info["n_interior"] + info["n_gamma"] == A.shape[0]
+    # nnz(L_G) is at least the lower triangle of A_G and at most dense
+    G = np.nonzero(part < 0)[0]
+    AG = A[G][:, G]
+    assert (AG.nnz + len(G)) // 2 <= info["nnz_L_gamma"] <= len(G) * (len(G) + 1) // 2
+
+
+def test_library_ordering_without_perm_is_valid():
+    N = lib_or_build()
+    A, part, _ = tiny_problem((16, 16), 4)
+    info = N.nsp_analyze(A, part, 4, None)
+    dense = sum(int((part == b).sum()) * (int((part == b).sum()) + 1) // 2 for b in range(4))
+    assert 0 < info["nnz_L_interior"] < dense
+
+
+def _expect(N, code, A, part, nsub, perm=None):
+    with pytest.raises(N.NspError) as e:
+        N.nsp_analyze(A, part, nsub, perm)
+    assert e.value.status == code
+
+
+def test_rejects_malformed_inputs():
+    N = lib_or_build()
+    A, part, perm = tiny_problem((8, 8), 2)
+    # coupled blocks -> NOT_DBBD
+    bad = part.copy()
+    bad[bad < 0] = 0
+    _expect(N, 2, A, bad, 2)
+    # asymmetric pattern
+    B = A.tolil()
+    B[0, 5] = 1.0
+    _expect(N, 1, B.tocsr(), part, 2)
+    # missing diagonal
+    C = A.tolil()
+    C[3, 3] = 0.0
+    C = C.tocsr()
+    C.eliminate_zeros()
+    _expect(N, 1, C, part, 2)
+    # part out of range
+    bad = part.copy()
+    bad[0] = 7
+    _expect(N, 1, A, bad, 2)
+    # perm that is not a permutation of the interior unknowns
+    _expect(N, 1, A, part, 2, perm[:-1].tolist() + [perm[0]])
+    # empty interface
+    _expect(N, 1, A, np.zeros_like(part), 1)

@@ -1,0 +1,187 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step.
+
+Tolerances: FP64 handles are compared at rounding level (the two sides factorize with
+different orderings, so agreement is to a few hundred ulps times the condition number of
+the operation); FP32 handles at the FP32 level, relative error <= c * kappa * 2^-24 with
+the bounds written in each test.
+"""
+
+import numpy as np
+import pytest
+
+import fixtures as F
+import oracle as O
+from oracle import philox
+
+from ._util import lib_or_build, tiny_problem
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "tiny2d": dict(shape=(13, 11), nsub=2, lognormal=(3.0, 1.5)),
+    "tiny3d": dict(shape=(9, 8, 7), nsub=4, lognormal=(2.0, 1.5)),
+    "ragged2d": dict(shape=(37, 29), nsub=4, lognormal=(5.0, 2.0)),
+}
+
+
+@pytest.fixture(scope="module")
+def N():
+    return lib_or_build()
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as T
+    return T
+
+
+def _case(name):
+    c = CASES[name]
+    A, part, perm = tiny_problem(c["shape"], c["nsub"], c["lognormal"], seed=7)
+    return A, part, c["nsub"]
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_factor_entries_match_dense_cholesky(N, name, prec):
+    A, part, nsub = _case(name)
+    h = N.nsp_build(A, part, nsub, k=4, p=2, precision=prec)
+    tol = 1e-11 if prec == "fp64" else 2e-5
+    sizes = [int((part == b).sum()) for b in range(nsub)] + [int((part < 0).sum())]
+    for b, nb in enumerate(sizes):
+        order, L = h.get_factor(b, nb)
+        ref = np.linalg.cholesky(A[order][:, order].toarray())
+        assert _rel(L, ref) < tol, (b, _rel(L, ref))
+    h.destroy()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("s", [1, 3, 16, 26, 80])
+def test_factor_solves_match_oracle(N, torch, name, prec, s):
+    A, part, nsub = _case(name)
+    D = O.DBBD(A, part, nsub)
+    h = N.nsp_build(A, part, nsub, k=4, p=2, precision=prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    rng = np.random.default_rng(s)
+    tol = 1e-11 if prec == "fp64" else 1e-4
+    for which, n, ref_solve in ((0, D.n_I, D.solve_I), (1, D.n_G, D.solve_G)):
+        B = rng.standard_normal((n, s))
+        Bd = torch.tensor(B, dtype=dt, device="cuda")
+        Xd = torch.empty_like(Bd)
+        h.factor_solve(which, Bd, Xd)
+        torch.cuda.synchronize()
+        X = Xd.double().cpu().numpy()
+        ref = ref_solve(B)
+        assert _rel(X, ref) < tol, (which, _rel(X, ref))
+    h.destroy()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("s", [1, 5, 16, 80])
+def test_schur_apply_matches_oracle(N, torch, name, prec, s):
+    A, part, nsub = _case(name)
+    D = O.DBBD(A, part, nsub)
+    h = N.nsp_build(A, part, nsub, k=4, p=2, precision=prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    X = np.random.default_rng(100 + s).standard_normal((D.n_G, s))
+    Xd = torch.tensor(X, dtype=dt, device="cuda")
+    Yd = torch.empty_like(Xd)
+    h.schur_apply(Xd, Yd)
+    torch.cuda.synchronize()
+    ref = D.apply_S_gamma(X)
+    tol = 1e-10 if prec == "fp64" else 2e-4
+    assert _rel(Yd.double().cpu().numpy(), ref) < tol
+    h.destroy()
+
+
+def test_gaussian_sketch_matches_oracle_generator(N, torch):
+    n = 100003
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    N.nsp_gaussian(987654321123, n, out)
+    torch.cuda.synchronize()
+    ref = philox.gaussian(987654321123, n)
+    assert np.allclose(out.cpu().numpy(), ref, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("name", ["tiny3d", "ragged2d"])
+def test_build_parity_fp64(N, name):
+    # same sketch on both sides: block PCG iterations equal, E, Y, Sigma and M2 agree
+    A, part, nsub = _case(name)
+    D = O.DBBD(A, part, nsub)
+    k, p = 6, 4
+    G = np.random.default_rng(3).standard_normal((D.n_G, k + p))
+    h = N.nsp_build(A, part, nsub, k=k, p=p, precision="fp64", sketch=G, drop_tol=1e-12,
+                    keep_intermediates=True)
+    M, info = O.build_m2(D, G, k, 0.1, form="S_gamma", drop_tol=1e-12)
+    gi = h.info()
+    assert gi["it_inner"] == info["it_inner"]
+    assert gi["rank"] == len(info["eig_T"][:k])
+    assert np.allclose(h.get_intermediate(0), G)
+    assert _rel(h.get_intermediate(1), info["X"]) < 1e-8
+    assert _rel(h.get_intermediate(2), info["Y"]) < 1e-8
+    Z, S = h.get_basis()
+    assert np.allclose(S, info["eig_T"][:k], rtol=1e-8)
+    # M2 as an operator: Z Sigma Z^T (signs/rotations of eigenvectors are arbitrary)
+    ref = (M.Z * M.Sigma) @ M.Z.T
+    assert _rel((Z * S) @ Z.T, ref) < 1e-7
+    h.destroy()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_apply_m2_matches_oracle(N, torch, name, prec):
+    A, part, nsub = _case(name)
+    D = O.DBBD(A, part, nsub)
+    k, p = 6, 4
+    G = np.random.default_rng(5).standard_normal((D.n_G, k + p))
+    h = N.nsp_build(A, part, nsub, k=k, p=p, precision=prec, sketch=G,
+                    drop_tol=1e-12 if prec == "fp64" else 1e-6)
+    M, _ = O.build_m2(D, G, k, 0.1, drop_tol=1e-12 if prec == "fp64" else 1e-6)
+    r = np.random.default_rng(6).standard_normal(D.n_G)
+    rd = torch.tensor(r, dtype=torch.float64, device="cuda")
+    zd = torch.empty_like(rd)
+    h.apply(rd, zd)
+    tol = 1e-8 if prec == "fp64" else 2e-3
+    assert _rel(zd.cpu().numpy(), M.apply(r)) < tol
+    h.destroy()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("prec,form", [("fp64", "schur"), ("fp32", "full"), ("fp64", "full")])
+def test_solve_parity(N, torch, name, prec, form):
+    A, part, nsub = _case(name)
+    D = O.DBBD(A, part, nsub)
+    k, p = 6, 4
+    G = np.random.default_rng(8).standard_normal((D.n_G, k + p))
+    x_star = np.random.default_rng(9).standard_normal(A.shape[0])
+    b = A @ x_star
+    h = N.nsp_build(A, part, nsub, k=k, p=p, precision=prec, sketch=G, outer_form=form)
+    M, _ = O.build_m2(D, G, k, 0.1)
+    _, it_ref, _ = O.solve(D, M.apply, b, rtol=1e-8)
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    xd = torch.zeros_like(bd)
+    inf = h.solve(bd, xd, rtol=1e-8, maxit=500)
+    x = xd.cpu().numpy()
+    assert O.relative_residual(A, x, b) < 1e-8 * 10
+    assert abs(inf["it_pcg"] - it_ref) <= 2, (inf["it_pcg"], it_ref)
+    # host buffers go through the same entry point
+    xh = np.zeros_like(b)
+    inf2 = h.solve(np.ascontiguousarray(b), xh, rtol=1e-8, maxit=500)
+    assert np.allclose(xh, x, rtol=1e-12, atol=1e-12)
+    h.destroy()
+
+
+def test_not_spd_block_reported(N):
+    A, part, nsub = _case("tiny2d")
+    B = A.tolil()
+    i = int(np.nonzero(part == 1)[0][3])
+    B[i, i] = -abs(B[i, i])
+    with pytest.raises(N.NspError) as e:
+        N.nsp_build(B.tocsr(), part, nsub, k=4, p=2, precision="fp64")
+    assert e.value.status == 3
