@@ -157,12 +157,15 @@ nsp_status nsp_solve(const nsp_handle *h, const double *b, double *x, double rto
 /* Y = S_Gamma X = A_G X - A_GI A_I^{-1} A_IG X (§2.3 eq. (schur_complement)) for an
  * n_Gamma x s block (Gamma order, row-major, 1 <= s <= 256), in the handle's precision:
  * X, Y are float* for NSP_FP32 handles and double* for NSP_FP64 handles. Device pointers,
- * may not alias. This is the operator applied inside the inner block PCG. */
+ * may not alias. This is the operator applied inside the inner block PCG. The work is
+ * enqueued on the handle's stream and the call returns without waiting: synchronize that
+ * stream before reading Y. Only the first call with a new width s allocates. */
 nsp_status nsp_schur_apply(const nsp_handle *h, const void *X, void *Y, int32_t s);
 
 /* X = A_I^{-1} B (interior order, n_interior x s) or X = A_G^{-1} B (Gamma order,
  * n_Gamma x s) with the device Cholesky factors, in the handle's precision (see
- * nsp_schur_apply). which: 0 = interior blocks, 1 = A_G. Device pointers. */
+ * nsp_schur_apply). which: 0 = interior blocks, 1 = A_G. Device pointers. Asynchronous on
+ * the handle's stream like nsp_schur_apply. */
 nsp_status nsp_factor_solve(const nsp_handle *h, int32_t which, const void *B, void *X,
                             int32_t s);
 
@@ -191,6 +194,10 @@ nsp_status nsp_analyze(const nsp_csr *A, const nsp_partition *P, nsp_info *info)
 nsp_status nsp_get_info(const nsp_handle *h, nsp_info *info);
 nsp_status nsp_destroy(nsp_handle *h);
 const char *nsp_status_string(nsp_status s);
+
+/* Number of CUDA kernels this library has launched in the process so far (all handles).
+ * Used to count the device launches of a timed region. */
+int64_t nsp_kernel_launches(void);
 
 /* Philox4x32-10 (Salmon et al., SC'11) + Box-Muller normals, as used for the sketch:
  * out[i] for i in [0, count), stream defined by seed; out is a device pointer. */

@@ -24,7 +24,7 @@ STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_
 EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_solve",
            "nsp_schur_apply", "nsp_factor_solve", "nsp_get_basis", "nsp_get_intermediate",
            "nsp_get_factor", "nsp_get_info", "nsp_destroy", "nsp_status_string", "nsp_gaussian",
-           "nsp_analyze"]
+           "nsp_analyze", "nsp_kernel_launches"]
 
 
 class NspError(RuntimeError):
@@ -94,6 +94,7 @@ def lib():
             "nsp_gaussian": (C.c_int, [C.c_uint64, C.c_int64, P, P]),
             "nsp_analyze": (C.c_int, [C.POINTER(nsp_csr), C.POINTER(nsp_partition),
                                       C.POINTER(nsp_info)]),
+            "nsp_kernel_launches": (C.c_int64, []),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -196,6 +197,10 @@ def nsp_analyze(A, part, nblocks, perm=None):
     info = nsp_info()
     _check(lib().nsp_analyze(C.byref(csr), C.byref(ps), C.byref(info)), "nsp_analyze")
     return info.as_dict()
+
+
+def nsp_kernel_launches():
+    return int(lib().nsp_kernel_launches())
 
 
 def nsp_gaussian(seed, count, out):

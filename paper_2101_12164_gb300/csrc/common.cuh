@@ -29,7 +29,13 @@ struct Error : std::runtime_error {
     }                                                                                     \
   } while (0)
 
-#define NSP_LAUNCH_CHECK() NSP_CUDA(cudaGetLastError())
+// Every kernel launch of the library passes through this check, which also counts it.
+int64_t count_launch();
+#define NSP_LAUNCH_CHECK()             \
+  do {                                 \
+    ::nsp::count_launch();             \
+    NSP_CUDA(cudaGetLastError());      \
+  } while (0)
 
 inline void require(bool ok, nsp_status s, const char *msg) {
   if (!ok) throw Error(s, msg);

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -25,6 +26,9 @@
 #include "symbolic.h"
 
 namespace nsp {
+
+static std::atomic<int64_t> g_launches{0};
+int64_t count_launch() { return g_launches.fetch_add(1, std::memory_order_relaxed) + 1; }
 
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t0) {
@@ -341,6 +345,7 @@ struct EngineBase {
   nsp_info info{};
   cudaStream_t st = nullptr;
   int precision = NSP_FP32;
+  DBuf<double> stage_b, stage_x;   // device staging of host vectors in nsp_solve
 };
 
 template <typename T>
@@ -365,6 +370,7 @@ struct Engine : EngineBase {
   DBuf<double> gram_work, PtQ, PtR, QtZ, Cg, alpha, beta, Rinv, Lwork, colsq, bnorm, ratio;
   DBuf<double> K, Cn, Mix, Sigma, nys_work, Zs;
   DBuf<int32_t> mask, nkept, drank;
+  DBuf<double> g64, ri_buf, zi_buf;
   bool keep = false;
   // outer PCG vectors (FP64)
   DBuf<double> vb, vx, vr, vz, vp, vq, vt, vu, vf, dwork, dscal;
@@ -549,7 +555,7 @@ struct Engine : EngineBase {
 
     // step 1: sketch G (caller order), moved to the internal order
     {
-      DBuf<double> g64(ns);
+      g64.ensure(ns);
       if (prm.sketch) {
         NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyHostToDevice, st));
       } else {
@@ -675,10 +681,11 @@ struct Engine : EngineBase {
 
   void apply_m2(const double *r, double *z) override {
     dwork.ensure(gram_work_size(std::max(an.n, an.nG), 256, 1));
-    DBuf<double> ri(an.nG), zi(an.nG);
-    launch_gather_rows<double, double>(i2u_G.p, an.nG, r, ri.p, 1, st);
-    m2_apply_internal(ri.p, zi.p);
-    launch_scatter_rows<double, double>(i2u_G.p, an.nG, zi.p, z, 1, st);
+    ri_buf.ensure(an.nG);
+    zi_buf.ensure(an.nG);
+    launch_gather_rows<double, double>(i2u_G.p, an.nG, r, ri_buf.p, 1, st);
+    m2_apply_internal(ri_buf.p, zi_buf.p);
+    launch_scatter_rows<double, double>(i2u_G.p, an.nG, zi_buf.p, z, 1, st);
     sync();
   }
 
@@ -792,25 +799,27 @@ struct Engine : EngineBase {
   }
   DBuf<double> pfull_t;
 
-  // ---- caller-order wrappers used by tests
+  // ---- caller-order wrappers (asynchronous on the handle's stream, no allocation after
+  // the first call with a given width)
+  DBuf<T> io_a, io_b;
   void schur_apply_user(const void *X, void *Yv, int sc) override {
     ensure_ws(sc);
-    DBuf<T> xi((size_t)an.nG * sc), yi((size_t)an.nG * sc);
-    launch_gather_rows<T, T>(i2u_G.p, an.nG, (const T *)X, xi.p, sc, st);
-    schur_apply(xi.p, yi.p, sc, true);
-    launch_scatter_rows<T, T>(i2u_G.p, an.nG, yi.p, (T *)Yv, sc, st);
-    sync();
+    io_a.ensure((size_t)an.nG * sc);
+    io_b.ensure((size_t)an.nG * sc);
+    launch_gather_rows<T, T>(i2u_G.p, an.nG, (const T *)X, io_a.p, sc, st);
+    schur_apply(io_a.p, io_b.p, sc, true);
+    launch_scatter_rows<T, T>(i2u_G.p, an.nG, io_b.p, (T *)Yv, sc, st);
   }
   void factor_solve_user(int which, const void *B, void *X, int sc) override {
     ensure_ws(sc);
     const int64_t nn = which == 0 ? an.nI : an.nG;
     const int64_t *perm = which == 0 ? i2u_I.p : i2u_G.p;
-    DBuf<T> bi((size_t)nn * sc), xi((size_t)nn * sc);
-    launch_gather_rows<T, T>(perm, nn, (const T *)B, bi.p, sc, st);
-    if (which == 0) solve_I(bi.p, xi.p, sc);
-    else solve_G(bi.p, xi.p, sc);
-    launch_scatter_rows<T, T>(perm, nn, xi.p, (T *)X, sc, st);
-    sync();
+    io_a.ensure((size_t)std::max(an.nI, an.nG) * sc);
+    io_b.ensure((size_t)std::max(an.nI, an.nG) * sc);
+    launch_gather_rows<T, T>(perm, nn, (const T *)B, io_a.p, sc, st);
+    if (which == 0) solve_I(io_a.p, io_b.p, sc);
+    else solve_G(io_a.p, io_b.p, sc);
+    launch_scatter_rows<T, T>(perm, nn, io_b.p, (T *)X, sc, st);
   }
   void get_basis(double *Zh, double *Sh, int32_t *rk) override {
     if (rk) *rk = rank;
@@ -1014,17 +1023,16 @@ nsp_status nsp_solve(const nsp_handle *h, const double *b, double *x, double rto
     const int64_t n = h->eng->info.n;
     cudaStream_t st = h->eng->st;
     const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
-    nsp::DBuf<double> db, dx;
     const double *bp = b;
     double *xp = x;
     if (!bd) {
-      db.alloc(n);
-      NSP_CUDA(cudaMemcpyAsync(db.p, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
-      bp = db.p;
+      h->eng->stage_b.ensure(n);
+      NSP_CUDA(cudaMemcpyAsync(h->eng->stage_b.p, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      bp = h->eng->stage_b.p;
     }
     if (!xd) {
-      dx.alloc(n);
-      xp = dx.p;
+      h->eng->stage_x.ensure(n);
+      xp = h->eng->stage_x.p;
     }
     nsp_status inner = NSP_OK;
     try {
@@ -1080,6 +1088,8 @@ nsp_status nsp_destroy(nsp_handle *h) {
   delete h;
   return NSP_OK;
 }
+
+int64_t nsp_kernel_launches(void) { return nsp::g_launches.load(); }
 
 nsp_status nsp_gaussian(uint64_t seed, int64_t count, double *out, void *stream) {
   if (!out || count < 0) return NSP_ERR_INVALID_ARG;
