@@ -14,6 +14,7 @@
 #include <atomic>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -57,6 +58,11 @@ struct Analysis {
 static void validate_csr(const nsp_csr *A) {
   require(A && A->n > 0 && A->rowptr && A->col && A->val, NSP_ERR_INVALID_ARG, "CSR: null or empty");
   require(A->n < (int64_t(1) << 31) - 1, NSP_ERR_UNSUPPORTED, "CSR: n too large");
+}
+
+static int relax_level() {
+  const char *e = std::getenv("NSP_RELAX");
+  return e ? std::atoi(e) : 2;
 }
 
 static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
@@ -176,12 +182,12 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
   {
     std::vector<BlockPattern> pats(nb);
     for (int32_t b = 0; b < nb; ++b) pats[b] = pattern(init[b], b);
-    analyze_forest(pats, 1, an.FI);
+    analyze_forest(pats, relax_level(), an.FI);
   }
   {
     std::vector<BlockPattern> pats(1);
     pats[0] = pattern(ginit, -1);
-    analyze_forest(pats, 1, an.FG);
+    analyze_forest(pats, relax_level(), an.FG);
   }
   // internal numbering
   an.i2g_I.resize(an.nI);
@@ -258,15 +264,96 @@ struct DevCsr {
 struct ForestData {
   Forest h;
   DBuf<int32_t> sn_first, sn_w, sn_m, sn_block, rows, relmap, ch_ptr, ch_list, level_sn;
+  std::vector<int32_t> level_small;   // per level: number of fronts below kBigFront rows
   DBuf<int64_t> sn_rowptr, sn_panel, sn_front, sn_upd, gptr, gsrc, asm_ptr, asm_dst, asm_src;
   ForestDev dev;
-  struct Tiles {
-    std::vector<int> fptr, bptr;
-    DBuf<TileItem> fwd, bwd;
+  struct Plan {
+    SweepPlan d;
+    DBuf<int32_t> item_a, item_b, group_sn, sn_parent, need_f, units_f, units_b;
+    DBuf<int32_t> counters;  // cnt_f, self_f, done_b (nsn each), claim, abort flag
+    int32_t epoch = 0, claim_base = 0, maxneed = 1;
   };
-  std::map<int, std::unique_ptr<Tiles>> tiles;
+  std::unique_ptr<Plan> plans[2];  // 0: block (s > 1), 1: vector (s = 1)
+  int vec_rows = 128;
+
+  Plan &plan(bool vector, cudaStream_t st) {
+    auto &pp = plans[vector ? 1 : 0];
+    if (pp) return *pp;
+    pp = std::make_unique<Plan>();
+    Plan &P = *pp;
+    const int nsn = h.nsn;
+    const int tf = vector ? vec_rows : kSweepBlockRows;
+    const int tb = vector ? kSweepVectorCols : kSweepBlockRows;
+    std::vector<int32_t> ia, ib, gs, uf(nsn, 0), ub(nsn, 0), need(nsn, 0);
+    auto small = [&](int J) { return vector && h.sn_m[J] <= kSmallM && h.sn_w[J] <= kSmallW; };
+    auto emit_level = [&](int l, bool fwd) {
+      std::vector<int32_t> grp;
+      auto flush = [&]() {
+        if (grp.empty()) return;
+        ia.push_back((int32_t)gs.size());
+        ib.push_back(-(int32_t)grp.size());
+        for (int J : grp) { gs.push_back(J); (fwd ? uf : ub)[J] = 1; }
+        grp.clear();
+      };
+      for (int q = h.level_ptr[l]; q < h.level_ptr[l + 1]; ++q) {
+        const int J = h.level_sn[q];
+        if (small(J)) {
+          grp.push_back(J);
+          if ((int)grp.size() == kGroup) flush();
+          continue;
+        }
+        const int extent = fwd ? h.sn_m[J] : h.sn_w[J];
+        const int tile = fwd ? tf : tb;
+        for (int r0 = 0; r0 < extent; r0 += tile) { ia.push_back(J); ib.push_back(r0); }
+        (fwd ? uf : ub)[J] = (extent + tile - 1) / tile;
+      }
+      flush();
+    };
+    for (int l = 0; l < h.nlevels; ++l) emit_level(l, true);
+    const int nfwd = (int)ia.size();
+    for (int l = h.nlevels - 1; l >= 0; --l) emit_level(l, false);
+    for (int J = 0; J < nsn; ++J)
+      if (h.sn_parent[J] >= 0) need[h.sn_parent[J]] += uf[J];
+    for (int J = 0; J < nsn; ++J) P.maxneed = std::max({P.maxneed, need[J], uf[J], ub[J]});
+    if (gs.empty()) gs.push_back(0);
+    P.item_a.upload(ia, st);
+    P.item_b.upload(ib, st);
+    P.group_sn.upload(gs, st);
+    P.sn_parent.upload(h.sn_parent, st);
+    P.need_f.upload(need, st);
+    P.units_f.upload(uf, st);
+    P.units_b.upload(ub, st);
+    P.counters.alloc(3 * (size_t)nsn + 2);
+    NSP_CUDA(cudaMemsetAsync(P.counters.p, 0, P.counters.bytes(), st));
+    int mm = 0;
+    for (int J = 0; J < nsn; ++J) mm = std::max(mm, h.sn_m[J]);
+    P.d.nitems = (int32_t)ia.size();
+    P.d.nfwd = nfwd;
+    P.d.max_m = mm;
+    P.d.vector = vector;
+    P.d.item_a = P.item_a.p;
+    P.d.item_b = P.item_b.p;
+    P.d.group_sn = P.group_sn.p;
+    P.d.sn_parent = P.sn_parent.p;
+    P.d.need_f = P.need_f.p;
+    P.d.units_f = P.units_f.p;
+    P.d.units_b = P.units_b.p;
+    P.d.cnt_f = P.counters.p;
+    P.d.self_f = P.counters.p + nsn;
+    P.d.done_b = P.counters.p + 2 * (size_t)nsn;
+    P.d.claim = P.counters.p + 3 * (size_t)nsn;
+    P.d.abort_flag = P.counters.p + 3 * (size_t)nsn + 1;
+    return P;
+  }
 
   void upload(cudaStream_t st) {
+    // within each level, fronts with m < kBigFront first (one CTA each), then the big ones
+    level_small.assign(h.nlevels, 0);
+    for (int l = 0; l < h.nlevels; ++l) {
+      auto b = h.level_sn.begin() + h.level_ptr[l], e = h.level_sn.begin() + h.level_ptr[l + 1];
+      auto mid = std::stable_partition(b, e, [&](int J) { return h.sn_m[J] < kBigFront; });
+      level_small[l] = (int32_t)(mid - b);
+    }
     sn_first.upload(h.sn_first, st);
     sn_w.upload(h.sn_w, st);
     sn_m.upload(h.sn_m, st);
@@ -306,28 +393,6 @@ struct ForestData {
     dev.asm_src = asm_src.p;
   }
 
-  const Tiles &get_tiles(int tm, cudaStream_t st) {
-    auto it = tiles.find(tm);
-    if (it != tiles.end()) return *it->second;
-    auto t = std::make_unique<Tiles>();
-    std::vector<TileItem> f, b;
-    t->fptr.push_back(0);
-    t->bptr.push_back(0);
-    for (int l = 0; l < h.nlevels; ++l) {
-      for (int q = h.level_ptr[l]; q < h.level_ptr[l + 1]; ++q) {
-        const int J = h.level_sn[q];
-        for (int r0 = 0; r0 < h.sn_m[J]; r0 += tm) f.push_back(TileItem{J, r0});
-        for (int r0 = 0; r0 < h.sn_w[J]; r0 += tm) b.push_back(TileItem{J, r0});
-      }
-      t->fptr.push_back((int)f.size());
-      t->bptr.push_back((int)b.size());
-    }
-    t->fwd.upload(f, st);
-    t->bwd.upload(b, st);
-    auto &ref = *t;
-    tiles[tm] = std::move(t);
-    return ref;
-  }
 };
 
 // ------------------------------------------------------------------ engine
@@ -434,6 +499,7 @@ struct Engine : EngineBase {
       throw Error(NSP_ERR_NOT_SPD, "non-positive pivot in a Cholesky factor");
     }
     if (hstat->code == DEV_BREAKDOWN) throw Error(NSP_ERR_BREAKDOWN, "block PCG breakdown");
+    if (hstat->code == DEV_TIMEOUT) throw Error(NSP_ERR_TIMEOUT, "a device wait timed out");
     if (hstat->code != DEV_OK) throw Error(NSP_ERR_CUDA, "device error");
   }
 
@@ -458,19 +524,21 @@ struct Engine : EngineBase {
     A_GI.refresh(Aval.p, st);
     A_G.refresh(Aval.p, st);
     NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
-    for (int l = 0; l < FI.h.nlevels; ++l) {
-      const int c0 = FI.h.level_ptr[l], c1 = FI.h.level_ptr[l + 1];
-      launch_factor_level<T>(FI.dev, FI.level_sn.p + c0, c1 - c0, Aval.p, front.p, panelI.p,
-                             dstat.p, st);
-    }
+    factor_forest(FI, panelI.p);
     check_factor_status(-1);
-    for (int l = 0; l < FG.h.nlevels; ++l) {
-      const int c0 = FG.h.level_ptr[l], c1 = FG.h.level_ptr[l + 1];
-      launch_factor_level<T>(FG.dev, FG.level_sn.p + c0, c1 - c0, Aval.p, front.p, panelG.p,
-                             dstat.p, st);
-    }
+    factor_forest(FG, panelG.p);
     check_factor_status(an.nblocks);  // a failure in the A_G factor reports block nblocks
     info.ms_factor = ms_since(t0);
+  }
+
+  void factor_forest(ForestData &F, T *panel) {
+    for (int l = 0; l < F.h.nlevels; ++l) {
+      const int c0 = F.h.level_ptr[l], c1 = F.h.level_ptr[l + 1], ns = F.level_small[l];
+      launch_factor_level<T>(F.dev, F.level_sn.p + c0, ns, Aval.p, front.p, panel, dstat.p, st,
+                             false);
+      launch_factor_level<T>(F.dev, F.level_sn.p + c0 + ns, c1 - c0 - ns, Aval.p, front.p,
+                             panel, dstat.p, st, true);
+    }
   }
 
   void check_factor_status(int block_override) {
@@ -483,18 +551,19 @@ struct Engine : EngineBase {
     if (hstat->code != DEV_OK) throw Error(NSP_ERR_CUDA, "device error in factorization");
   }
 
-  // ---- X = A_b^{-1} B over a forest (internal order, s columns)
+  // ---- X = A_b^{-1} B over a forest (internal order, s columns): one persistent launch
   void solve_forest(ForestData &F, const T *panel, const T *B, T *Ywk, T *Uwk, T *X, int sc) {
-    const int tm = solve_tile_rows(sc);
-    const auto &tl = F.get_tiles(tm, st);
-    for (int l = 0; l < F.h.nlevels; ++l) {
-      const int a = tl.fptr[l], b = tl.fptr[l + 1];
-      launch_solve_fwd<T>(F.dev, tl.fwd.p + a, b - a, tm, panel, B, Ywk, Uwk, sc, st);
+    F.vec_rows = sweep_vector_rows((int)sizeof(T));
+    auto &P = F.plan(sc == 1, st);
+    P.epoch += 1;
+    if ((int64_t)P.epoch * P.maxneed > (int64_t(1) << 30) || P.claim_base > (1 << 30)) {
+      NSP_CUDA(cudaMemsetAsync(P.counters.p, 0, P.counters.bytes(), st));
+      P.epoch = 1;
+      P.claim_base = 0;
     }
-    for (int l = F.h.nlevels - 1; l >= 0; --l) {
-      const int a = tl.bptr[l], b = tl.bptr[l + 1];
-      launch_solve_bwd<T>(F.dev, tl.bwd.p + a, b - a, tm, panel, Ywk, X, sc, st);
-    }
+    const int grid = launch_sweep<T>(F.dev, P.d, P.epoch, P.claim_base, panel, B, Ywk, Uwk, X,
+                                     sc, dstat.p, st);
+    P.claim_base += P.d.nitems + grid;
   }
   void solve_I(const T *B, T *X, int sc) {
     ensure_ws(sc);
@@ -539,9 +608,10 @@ struct Engine : EngineBase {
     const size_t ns = (size_t)an.nG * s;
     for (DBuf<T> *b : {&G, &Fh, &E, &R, &P, &Q, &Z, &W, &Y}) b->ensure(ns);
     gram_work.ensure(std::max(gram_work_size(an.nG, s, s), gram_work_size(an.nG, s, 1)));
-    for (DBuf<double> *b : {&PtQ, &PtR, &QtZ, &Cg, &alpha, &beta, &Lwork, &K, &Cn})
+    for (DBuf<double> *b : {&PtQ, &PtR, &QtZ, &Cg, &alpha, &beta, &K, &Cn})
       b->ensure((size_t)s * s);
-    Rinv.ensure(3 * (size_t)s * s + s + 64);
+    Rinv.ensure((size_t)s * s);
+    Lwork.ensure(core_work_size(s));
     colsq.ensure(s);
     bnorm.ensure(s);
     ratio.ensure(1);
@@ -568,40 +638,42 @@ struct Engine : EngineBase {
     schur_apply(G.p, Fh.p, s, false);
     launch_col_sumsq<T>(Fh.p, an.nG, s, colsq.p, gram_work.p, st);
     launch_sqrt_vec(colsq.p, s, bnorm.p, st);
+    // Breakdown-free block PCG (the paper's inner solver, §5.1) with search directions kept
+    // S_Gamma-orthonormal: W spans the new directions, Qw = S W, C = W^T Qw = L L^T (columns
+    // whose pivot falls below drop_tol are dropped), P = W L^{-T}, Q = Qw L^{-T}, so that
+    // P^T Q = I and alpha = P^T R, beta = -Q^T Z need no s x s solve. The block Krylov
+    // space, hence every iterate E, is the one of the 2-norm-orthonormal form.
     NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
     NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    solve_G(R.p, Z.p, s);
-    gram(Z.p, Z.p, s, s, Cg.p);
-    launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, st);
-    launch_block_update<T>(Z.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
+    solve_G(R.p, W.p, s);                 // W = Z0 = A_G^{-1} R0
     int it = 0;
     double rat = 1.0;
     int active = s;
     while (it < prm.max_inner_it) {
-      schur_apply(P.p, Q.p, s, true);
-      gram(P.p, Q.p, s, s, PtQ.p);
-      gram(P.p, R.p, s, s, PtR.p);
-      launch_spd_solve_masked(PtQ.p, PtR.p, s, s, mask.p, 1.0, alpha.p, Lwork.p, dstat.p, st);
+      schur_apply(W.p, Z.p, s, true);     // Z holds Qw = S W
+      gram(W.p, Z.p, s, s, Cg.p);
+      launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
+      launch_block_update<T>(W.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
+      launch_block_update<T>(Z.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), Q.p, st);
+      gram(P.p, R.p, s, s, alpha.p);      // alpha = P^T R
       launch_block_update<T>(P.p, alpha.p, an.nG, s, s, T(1), E.p, T(1), E.p, st);
       launch_block_update<T>(Q.p, alpha.p, an.nG, s, s, T(-1), R.p, T(1), R.p, st);
       ++it;
       launch_col_sumsq<T>(R.p, an.nG, s, colsq.p, gram_work.p, st);
       launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st);
       NSP_CUDA(cudaMemcpyAsync(hscal, ratio.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-      sync();
-      rat = hscal[0];
-      if (!(rat > prm.eps_inner)) break;
-      solve_G(R.p, Z.p, s);
-      gram(Q.p, Z.p, s, s, QtZ.p);
-      launch_spd_solve_masked(PtQ.p, QtZ.p, s, s, mask.p, -1.0, beta.p, Lwork.p, dstat.p, st);
-      launch_block_update<T>(P.p, beta.p, an.nG, s, s, T(1), Z.p, T(1), W.p, st);
-      gram(W.p, W.p, s, s, Cg.p);
-      launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, st);
-      launch_block_update<T>(W.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
       NSP_CUDA(cudaMemcpyAsync(hint, nkept.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       sync();
+      rat = hscal[0];
       active = hint[0];
-      if (active == 0) break;
+      if (active == 0) {  // no search direction left: the last pass changed nothing
+        --it;
+        break;
+      }
+      if (!(rat > prm.eps_inner)) break;
+      solve_G(R.p, Z.p, s);               // Z = A_G^{-1} R
+      gram(Q.p, Z.p, s, s, beta.p);       // Q^T Z
+      launch_block_update<T>(P.p, beta.p, an.nG, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
     }
     check_status();
     info.it_inner = it;
@@ -649,8 +721,8 @@ struct Engine : EngineBase {
     }
     if (rank > 0) {
       zt_vec.ensure(k);
-      launch_gram<double, double>(Zs.p, r, an.nG, k, 1, zt_vec.p, dwork.p, st);
-      launch_block_update<double>(Zs.p, zt_vec.p, an.nG, k, 1, 1.0, z, 1.0, z, st);
+      launch_gemv_t(Zs.p, an.nG, k, r, zt_vec.p, dwork.p, st);
+      launch_gemv_n(Zs.p, an.nG, k, zt_vec.p, 1.0, z, st);
     }
   }
 
@@ -791,6 +863,7 @@ struct Engine : EngineBase {
     launch_dot(b_user, b_user, n, dscal.p + 9, dwork.p, st);
     NSP_CUDA(cudaMemcpyAsync(hscal + 8, dscal.p + 8, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     sync();
+    check_status();
     info.it_pcg = it;
     info.pcg_residual = rel;
     info.final_residual = hscal[9] > 0 ? std::sqrt(hscal[8] / hscal[9]) : 0.0;
@@ -867,12 +940,12 @@ struct Engine : EngineBase {
     std::fill(L, L + n_b * n_b, 0.0);
     for (int J = 0; J < F.nsn; ++J) {
       if (F.sn_block[J] != b) continue;
-      const int w = F.sn_w[J], m = F.sn_m[J];
+      const int w = F.sn_w[J], m = F.sn_m[J], ld = panel_ld(m);
       const T *Pj = pan.data() + F.sn_panel[J];
       // L11 = inv(Pj_top) by forward substitution; L21 = Pj_bot L11
       std::vector<double> Li((size_t)w * w, 0.0), L11((size_t)w * w, 0.0);
       for (int r = 0; r < w; ++r)
-        for (int c = 0; c <= r; ++c) Li[r + (size_t)c * w] = (double)Pj[r + (size_t)c * m];
+        for (int c = 0; c <= r; ++c) Li[r + (size_t)c * w] = (double)Pj[r + (size_t)c * ld];
       for (int c = 0; c < w; ++c)
         for (int r = c; r < w; ++r) {
           double v = (r == c) ? 1.0 : 0.0;
@@ -885,7 +958,7 @@ struct Engine : EngineBase {
           L[(first + r) + (first + c) * n_b] = L11[r + (size_t)c * w];
         for (int r = w; r < m; ++r) {
           double v = 0.0;
-          for (int t = c; t < w; ++t) v += (double)Pj[r + (size_t)t * m] * L11[t + (size_t)c * w];
+          for (int t = c; t < w; ++t) v += (double)Pj[r + (size_t)t * ld] * L11[t + (size_t)c * w];
           const int64_t row = F.rows[F.sn_rowptr[J] + r] - off;
           L[row + (first + c) * n_b] = v;
         }

@@ -59,30 +59,32 @@ __global__ void k_gather_values(const int64_t *src, int64_t count, const double 
 }
 
 // ---------------------------------------------------------------- Gram X^T Y
-// Stage 1: CTA (chunk, ta, tb) sums rows [chunk*rpc, ...) for the 64 x 64 output tile
-// (ta, tb); stage 2 adds the chunk partials in chunk order (deterministic).
-constexpr int GT = 64, GR = 32;
+// Stage 1: CTA (chunk, ta, tb) sums rows [chunk*rpc, ...) for a (16 RT) x (16 RT) output
+// tile (ta, tb); each thread owns RT x RT outputs; rows are staged GR at a time. Stage 2
+// adds the chunk partials in chunk order (deterministic).
+constexpr int GR = 16;
 
-template <typename T, typename AccT>
+template <typename T, typename AccT, int RT>
 __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
                                                      const T *__restrict__ Y, int64_t n,
                                                      int s1, int s2, int64_t rpc,
                                                      double *work) {
-  __shared__ T Xs[GR][GT + 1];
-  __shared__ T Ys[GR][GT + 1];
+  constexpr int TS = 16 * RT;
+  __shared__ T Xs[GR][TS];
+  __shared__ T Ys[GR][TS];
   const int chunk = blockIdx.x;
-  const int a0 = blockIdx.y * GT, b0 = blockIdx.z * GT;
+  const int a0 = blockIdx.y * TS, b0 = blockIdx.z * TS;
   const int64_t i0 = (int64_t)chunk * rpc;
   const int64_t i1 = min(n, i0 + rpc);
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  AccT acc[4][4];
+  AccT acc[RT][RT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = AccT(0);
+    for (int j = 0; j < RT; ++j) acc[i][j] = AccT(0);
   for (int64_t ib = i0; ib < i1; ib += GR) {
-    for (int q = tid; q < GR * GT; q += BT) {
-      const int r = q / GT, c = q % GT;
+    for (int q = tid; q < GR * TS; q += BT) {
+      const int r = q / TS, c = q % TS;
       const int64_t row = ib + r;
       Xs[r][c] = (row < i1 && a0 + c < s1) ? X[(size_t)row * s1 + a0 + c] : T(0);
       Ys[r][c] = (row < i1 && b0 + c < s2) ? Y[(size_t)row * s2 + b0 + c] : T(0);
@@ -90,22 +92,22 @@ __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
     __syncthreads();
 #pragma unroll 4
     for (int r = 0; r < GR; ++r) {
-      AccT xa[4], yb[4];
+      AccT xa[RT], yb[RT];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xa[i] = (AccT)Xs[r][ty + 16 * i];
+      for (int i = 0; i < RT; ++i) xa[i] = (AccT)Xs[r][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) yb[j] = (AccT)Ys[r][tx + 16 * j];
+      for (int j = 0; j < RT; ++j) yb[j] = (AccT)Ys[r][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += xa[i] * yb[j];
+        for (int j = 0; j < RT; ++j) acc[i][j] += xa[i] * yb[j];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RT; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RT; ++j) {
       const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
       if (a < s1 && b < s2) work[((size_t)chunk * s1 + a) * s2 + b] = (double)acc[i][j];
     }
@@ -119,11 +121,54 @@ __global__ void k_gram_reduce(const double *work, int nchunks, int64_t entries, 
   C[e] = acc;
 }
 
+int gram_rt(int s1, int s2) {
+  const int smax = std::max(s1, s2);
+  return smax <= 32 ? 2 : smax <= 64 ? 4 : smax <= 96 ? 6 : 8;
+}
+
 int gram_chunks(int64_t n, int s1, int s2) {
-  const int tiles = ceil_div(s1, GT) * ceil_div(s2, GT);
+  const int ts = 16 * gram_rt(s1, s2);
+  const int tiles = ceil_div(s1, ts) * ceil_div(s2, ts);
   int target = std::max(1, 2 * 152 / tiles);
-  int maxc = std::max<int64_t>(1, (n + GR - 1) / GR);
+  int maxc = (int)std::max<int64_t>(1, (n + 4 * GR - 1) / (4 * GR));
   return std::max(1, std::min(target, maxc));
+}
+
+// ---------------------------------------------------------------- FP64 GEMV with a tall Z
+// t = Z^T r (Z n x k row-major): partials per row chunk, then an ordered sum.
+__global__ void __launch_bounds__(BT) k_gemv_t_partial(const double *Z, int64_t n, int k,
+                                                       const double *r, int64_t rpc,
+                                                       double *work) {
+  __shared__ double red[8][33];
+  const int64_t i0 = (int64_t)blockIdx.x * rpc, i1 = min(n, i0 + rpc);
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+  for (int c0 = 0; c0 < k; c0 += 32) {
+    const int c = c0 + tx;
+    double acc = 0.0;
+    if (c < k)
+      for (int64_t i = i0 + ty; i < i1; i += 8) acc += Z[(size_t)i * k + c] * r[i];
+    red[ty][tx] = acc;
+    __syncthreads();
+    if (ty == 0 && c < k) {
+      double t = 0.0;
+      for (int q = 0; q < 8; ++q) t += red[q][tx];
+      work[(size_t)blockIdx.x * k + c] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// z[i] = beta z[i] + sum_j Z[i, j] t[j]: one warp per row.
+__global__ void __launch_bounds__(BT) k_gemv_n(const double *Z, int64_t n, int k,
+                                               const double *t, double beta, double *z) {
+  const int64_t i = (int64_t)blockIdx.x * (BT / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = lane; j < k; j += 32) acc += Z[(size_t)i * k + j] * t[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) z[i] = beta * z[i] + acc;
 }
 
 // ---------------------------------------------------------------- block update
@@ -354,17 +399,46 @@ size_t gram_work_size(int64_t n, int s1, int s2) {
   return std::max<size_t>(std::max(g, c), 4 * 152 + 8);
 }
 
+template <typename T, typename AccT, int RT>
+void gram_rt_launch(const T *X, const T *Y, int64_t n, int s1, int s2, double *C, double *work,
+                    cudaStream_t stream) {
+  const int ch = gram_chunks(n, s1, s2);
+  const int64_t rpc = std::max<int64_t>(GR, ((n + ch - 1) / ch + GR - 1) / GR * GR);
+  dim3 grid(ch, ceil_div(s1, 16 * RT), ceil_div(s2, 16 * RT));
+  k_gram_partial<T, AccT, RT><<<grid, BT, 0, stream>>>(X, Y, n, s1, s2, rpc, work);
+  NSP_LAUNCH_CHECK();
+  const int64_t ent = (int64_t)s1 * s2;
+  k_gram_reduce<<<ceil_div(ent, BT), BT, 0, stream>>>(work, ch, ent, C);
+  NSP_LAUNCH_CHECK();
+}
+
 template <typename T, typename AccT>
 void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C, double *work,
                  cudaStream_t stream) {
   if (s1 <= 0 || s2 <= 0) return;
-  const int ch = gram_chunks(n, s1, s2);
-  const int64_t rpc = ((n + ch - 1) / ch + GR - 1) / GR * GR;
-  dim3 grid(ch, ceil_div(s1, GT), ceil_div(s2, GT));
-  k_gram_partial<T, AccT><<<grid, BT, 0, stream>>>(X, Y, n, s1, s2, std::max<int64_t>(rpc, GR), work);
+  switch (gram_rt(s1, s2)) {
+    case 2: gram_rt_launch<T, AccT, 2>(X, Y, n, s1, s2, C, work, stream); break;
+    case 4: gram_rt_launch<T, AccT, 4>(X, Y, n, s1, s2, C, work, stream); break;
+    case 6: gram_rt_launch<T, AccT, 6>(X, Y, n, s1, s2, C, work, stream); break;
+    default: gram_rt_launch<T, AccT, 8>(X, Y, n, s1, s2, C, work, stream); break;
+  }
+}
+
+void launch_gemv_t(const double *Z, int64_t n, int k, const double *r, double *t, double *work,
+                   cudaStream_t stream) {
+  if (k <= 0) return;
+  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256));
+  const int64_t rpc = (n + cs - 1) / cs;
+  k_gemv_t_partial<<<(int)cs, BT, 0, stream>>>(Z, n, k, r, std::max<int64_t>(rpc, 1), work);
   NSP_LAUNCH_CHECK();
-  const int64_t ent = (int64_t)s1 * s2;
-  k_gram_reduce<<<ceil_div(ent, BT), BT, 0, stream>>>(work, ch, ent, C);
+  k_gram_reduce<<<ceil_div(k, BT), BT, 0, stream>>>(work, (int)cs, k, t);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_gemv_n(const double *Z, int64_t n, int k, const double *t, double beta, double *z,
+                   cudaStream_t stream) {
+  if (n <= 0 || k <= 0) return;
+  k_gemv_n<<<ceil_div(n, BT / 32), BT, 0, stream>>>(Z, n, k, t, beta, z);
   NSP_LAUNCH_CHECK();
 }
 

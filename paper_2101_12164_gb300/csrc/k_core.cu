@@ -1,7 +1,15 @@
-// Small dense FP64 linear algebra on one CTA: the s x s steps of the breakdown-free block
-// PCG (Cholesky-QR with column drop, alpha/beta solves) and the Nyström core of
-// Algorithm 2 steps 5-10 (Cholesky-QR of Y, EVD of C, T, EVD of T). s <= 256.
-// Matrices live in a global scratch area (row-major, s x s), cached in L1/L2.
+// Small dense linear algebra on one CTA: the s x s steps of the breakdown-free block PCG
+// (Cholesky-QR with column drop, alpha/beta solves) and the Nyström core of Algorithm 2
+// steps 5-10 (Cholesky-QR of Y, EVD of C, T, EVD of T). s <= 256. Working sets live in
+// shared memory when they fit (s <= 88), otherwise in a global scratch area.
+//
+// Symmetric EVD: cyclic Jacobi (rotation of pair (p, q) from Golub & Van Loan's 2x2
+// symmetric Schur decomposition: tau = (a_qq - a_pp)/(2 a_pq), t = sign(tau)/(|tau| +
+// sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c) with the round-robin ordering of disjoint
+// pairs, first in FP32; the FP32 eigenvectors are then orthonormalized in FP64 (modified
+// Gram-Schmidt), B = V^T C V is formed in FP64 and FP64 Jacobi sweeps with the threshold
+// |b_pq| > tol sqrt(|b_pp b_qq|) finish the decomposition, so eigenvalues and vectors are
+// FP64-accurate while most rotations run at FP32 speed.
 #include <cfloat>
 
 #include "kernels.cuh"
@@ -9,18 +17,22 @@
 namespace nsp {
 namespace {
 
-constexpr int CT = 512;  // threads of the single CTA
+constexpr int CT = 512;            // threads of the single CTA
+constexpr int SMEM_S = 88;         // largest s whose three s x s FP64 buffers fit in smem
+constexpr unsigned FULL = 0xffffffffu;
 
-// In-place thresholded right-looking Cholesky of L (s x s, row-major, lower part used):
-// column j is kept when its pivot exceeds drop_tol * diag0[j] (and diag0[j] > 0), otherwise
-// it is zeroed and skipped. mask[j] = kept.
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+
+// Thresholded right-looking Cholesky of L (s x s, row-major, lower part): column j is kept
+// when its pivot exceeds drop_tol * diag0[j] (diag0[j] > 0), otherwise zeroed and skipped.
 __device__ void chol_threshold(double *L, const double *diag0, int s, double drop_tol,
-                               int32_t *mask, int *nkept_sh) {
+                               int32_t *mask, int *nkept) {
+  __shared__ int keep;
   const int tid = threadIdx.x;
-  if (tid == 0) *nkept_sh = 0;
+  if (tid == 0) *nkept = 0;
   __syncthreads();
   for (int j = 0; j < s; ++j) {
-    __shared__ int keep;
     if (tid == 0) {
       const double piv = L[j * s + j];
       const double d0 = diag0[j];
@@ -28,7 +40,7 @@ __device__ void chol_threshold(double *L, const double *diag0, int s, double dro
       mask[j] = keep;
       if (keep) {
         L[j * s + j] = sqrt(piv);
-        *nkept_sh += 1;
+        *nkept += 1;
       }
     }
     __syncthreads();
@@ -48,102 +60,262 @@ __device__ void chol_threshold(double *L, const double *diag0, int s, double dro
   }
 }
 
-// Linv (s x s row-major) = inverse of the kept part of lower L; zero rows/cols for dropped.
-// One thread per column c: forward substitution L x = e_c over kept indices.
-__device__ void lower_inverse(const double *L, const int32_t *mask, int s, double *Linv) {
-  for (int c = threadIdx.x; c < s; c += CT) {
-    for (int i = 0; i < s; ++i) {
-      double v = 0.0;
-      if (mask[i] && mask[c] && i >= c) {
-        v = (i == c) ? 1.0 : 0.0;
-        for (int t = c; t < i; ++t)
-          if (mask[t]) v -= L[i * s + t] * Linv[t * s + c];
-        v /= L[i * s + i];
+// Solve L X = X (fwd) or L^T X = X (bwd) in place; L lower s x s (row-major), X s x r
+// (row-major); rows with mask == 0 are set to zero. Eight lanes share each column.
+__device__ void trsm_masked(const double *L, int s, const int32_t *mask, double *X, int r,
+                            bool transpose, bool identity_rhs = false) {
+  // lanes per column: enough groups to cover all r columns in one pass when possible
+  const int lpc = r <= CT / 8 ? 8 : 4;
+  const int lane8 = threadIdx.x % lpc, grp = threadIdx.x / lpc;
+  for (int c0 = 0; c0 < r; c0 += CT / lpc) {
+    const int c = c0 + grp;
+    const bool act = c < r;
+    for (int step = 0; step < s; ++step) {
+      const int i = transpose ? s - 1 - step : step;
+      double part = 0.0;
+      // forward solve of an identity column c: rows i < c stay zero
+      if (act && mask[i] && !(identity_rhs && !transpose && i < c)) {
+        if (!transpose) {
+          for (int t = (identity_rhs ? c : 0) + lane8; t < i; t += lpc)
+            if (mask[t]) part += L[i * s + t] * X[t * r + c];
+        } else {
+          for (int t = i + 1 + lane8; t < s; t += lpc)
+            if (mask[t]) part += L[t * s + i] * X[t * r + c];
+        }
       }
-      Linv[i * s + c] = v;
+      if (lpc == 8) part += __shfl_xor_sync(FULL, part, 4);
+      part += __shfl_xor_sync(FULL, part, 2);
+      part += __shfl_xor_sync(FULL, part, 1);
+      if (lane8 == 0 && act) X[i * r + c] = mask[i] ? (X[i * r + c] - part) / L[i * s + i] : 0.0;
+      __syncwarp();
     }
   }
   __syncthreads();
 }
 
-// Cholesky-QR with drop: Rinv[i][c] = Linv[c][i] (upper), so W Rinv has orthonormal kept cols.
+// Cyclic Jacobi on symmetric A (s x s row-major); V accumulates (A_in = V A_out V^T).
+// A rotation is applied when |a_pq| > tol * sqrt(|a_pp a_qq|) and |a_pq| > floor_rel ||A||_F
+// (below that the entry is at the rounding level of the matrix).
+template <typename F>
+__device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
+  __shared__ F cs[128], sn[128];
+  __shared__ int pp[128], qq[128], ring[258];
+  __shared__ int any;
+  __shared__ F fro_sh;
+  __shared__ float red[CT];
+  const int tid = threadIdx.x;
+  {  // ||A||_F (rotations keep it): off-diagonal entries below floor_rel ||A||_F are final
+    float acc = 0.0f;
+    for (int i = tid; i < s * s; i += CT) acc += (float)A[i] * (float)A[i];
+    red[tid] = acc;
+    __syncthreads();
+    for (int h = CT / 2; h > 0; h >>= 1) {
+      if (tid < h) red[tid] += red[tid + h];
+      __syncthreads();
+    }
+    if (tid == 0) fro_sh = (F)sqrtf(red[0]);
+    __syncthreads();
+  }
+  const F floor_abs = floor_rel * fro_sh;
+  const int se = s + (s & 1);
+  const int npair = se / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) any = 0;
+    for (int i = tid; i < se; i += CT) ring[i] = i;
+    __syncthreads();
+    for (int round = 0; round < se - 1; ++round) {
+      for (int k = tid; k < npair; k += CT) {
+        int p = ring[k], q = ring[se - 1 - k];
+        if (p > q) { const int x = p; p = q; q = x; }
+        pp[k] = p;
+        qq[k] = q;
+        F c = F(1), sv = F(0);
+        if (q < s) {
+          const F apq = A[p * s + q], app = A[p * s + p], aqq = A[q * s + q];
+          if (fabs(apq) > floor_abs && fabs(apq) > tol * sqrt_(fabs(app * aqq))) {
+            const F tau = (aqq - app) / (F(2) * apq);
+            const F tt = (tau >= F(0) ? F(1) : F(-1)) / (fabs(tau) + sqrt_(F(1) + tau * tau));
+            c = F(1) / sqrt_(F(1) + tt * tt);
+            sv = tt * c;
+            any = 1;
+          }
+        }
+        cs[k] = c;
+        sn[k] = sv;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npair * s; idx += CT) {  // A <- A J, V <- V J
+        const int k = idx / s, i = idx % s;
+        const F sv = sn[k];
+        if (sv == F(0)) continue;
+        const int p = pp[k], q = qq[k];
+        const F c = cs[k];
+        const F ap = A[i * s + p], aq = A[i * s + q];
+        A[i * s + p] = c * ap - sv * aq;
+        A[i * s + q] = sv * ap + c * aq;
+        const F vp = V[i * s + p], vq = V[i * s + q];
+        V[i * s + p] = c * vp - sv * vq;
+        V[i * s + q] = sv * vp + c * vq;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < npair * s; idx += CT) {  // A <- J^T A
+        const int k = idx / s, j = idx % s;
+        const F sv = sn[k];
+        if (sv == F(0)) continue;
+        const int p = pp[k], q = qq[k];
+        const F c = cs[k];
+        const F ap = A[p * s + j], aq = A[q * s + j];
+        A[p * s + j] = c * ap - sv * aq;
+        A[q * s + j] = sv * ap + c * aq;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const int last = ring[se - 1];
+        for (int i = se - 1; i > 1; --i) ring[i] = ring[i - 1];
+        ring[1] = last;
+      }
+      __syncthreads();
+    }
+    if (!any) break;
+    __syncthreads();
+  }
+}
+
+// Modified Gram-Schmidt on the columns of V (s x s row-major, FP64).
+__device__ void mgs_columns(double *V, int s) {
+  __shared__ double red[CT];
+  __shared__ double coef[256];
+  const int tid = threadIdx.x;
+  for (int j = 0; j < s; ++j) {
+    // coefficients against the previous columns, then subtract, then normalize
+    for (int i = tid; i < j; i += CT) {
+      double d = 0.0;
+      for (int r = 0; r < s; ++r) d += V[r * s + i] * V[r * s + j];
+      coef[i] = d;
+    }
+    __syncthreads();
+    for (int r = tid; r < s; r += CT) {
+      double v = V[r * s + j];
+      for (int i = 0; i < j; ++i) v -= coef[i] * V[r * s + i];
+      V[r * s + j] = v;
+    }
+    __syncthreads();
+    double sq = 0.0;
+    for (int r = tid; r < s; r += CT) sq += V[r * s + j] * V[r * s + j];
+    red[tid] = sq;
+    __syncthreads();
+    for (int h = CT / 2; h > 0; h >>= 1) {
+      if (tid < h) red[tid] += red[tid + h];
+      __syncthreads();
+    }
+    const double nrm = sqrt(red[0]);
+    for (int r = tid; r < s; r += CT) V[r * s + j] = nrm > 0.0 ? V[r * s + j] / nrm : 0.0;
+    __syncthreads();
+  }
+}
+
+// FP64-accurate EVD of the symmetric matrix held in Bm (s x s): on return the eigenvalues
+// are on the diagonal of Bm and the eigenvectors in the columns of V. W1 is s x s scratch,
+// also used for the two FP32 matrices of the first phase. All three may be shared memory.
+__device__ void eig_sym(double *Bm, int s, double *V, double *W1) {
+  const int tid = threadIdx.x;
+  const size_t ss = (size_t)s * s;
+  float *A32 = reinterpret_cast<float *>(W1), *V32 = A32 + ss;
+  for (size_t i = tid; i < ss; i += CT) {
+    A32[i] = (float)Bm[i];
+    V32[i] = (i / s == i % s) ? 1.0f : 0.0f;
+  }
+  __syncthreads();
+  jacobi<float>(A32, V32, s, 8, 1e-6f, 2e-7f);
+  for (size_t i = tid; i < ss; i += CT) V[i] = (double)V32[i];
+  __syncthreads();
+  mgs_columns(V, s);
+  // W1 = C V ; Bm = V^T W1
+  for (size_t idx = tid; idx < ss; idx += CT) {
+    const int i = idx / s, j = idx % s;
+    double v = 0.0;
+    for (int t = 0; t < s; ++t) v += Bm[i * s + t] * V[t * s + j];
+    W1[idx] = v;
+  }
+  __syncthreads();
+  for (size_t idx = tid; idx < ss; idx += CT) {
+    const int i = idx / s, j = idx % s;
+    if (j < i) continue;
+    double v = 0.0;
+    for (int t = 0; t < s; ++t) v += V[t * s + i] * W1[t * s + j];
+    Bm[i * s + j] = v;
+    Bm[j * s + i] = v;
+  }
+  __syncthreads();
+  jacobi<double>(Bm, V, s, 2, 1e-13, 1e-15);
+}
+
+struct Scratch {
+  double *b0, *b1, *b2;  // three s x s buffers (smem or global)
+};
+
+__device__ Scratch scratch(double *smem, double *global, int s, bool use_smem) {
+  const size_t ss = (size_t)s * s;
+  double *base = use_smem ? smem : global;
+  return Scratch{base, base + ss, base + 2 * ss};
+}
+
+// ---------------------------------------------------------------- block PCG kernels
+// C = W^T W -> thresholded Cholesky-QR: Rinv (upper, zero for dropped), mask, nkept.
 __global__ void __launch_bounds__(CT) k_chol_drop(const double *C, int s, double drop_tol,
                                                   double *Rinv, int32_t *mask, int32_t *nkept,
-                                                  double *work) {
+                                                  double *gwork, int use_smem) {
+  extern __shared__ __align__(16) double dsm[];
   __shared__ int nk;
-  double *L = work;              // s*s
-  double *Linv = work + s * s;   // s*s
-  double *diag0 = work + 2 * s * s;
-  for (int i = threadIdx.x; i < s * s; i += CT) L[i] = C[i];
-  for (int i = threadIdx.x; i < s; i += CT) diag0[i] = C[i * s + i];
-  __syncthreads();
-  chol_threshold(L, diag0, s, drop_tol, mask, &nk);
-  lower_inverse(L, mask, s, Linv);
-  for (int i = threadIdx.x; i < s * s; i += CT) {
-    const int r = i / s, c = i % s;
-    Rinv[i] = Linv[c * s + r];
+  __shared__ double diag0[256];
+  __shared__ int32_t msk[256];
+  const Scratch S = scratch(dsm, gwork, s, use_smem);
+  const int tid = threadIdx.x;
+  const size_t ss = (size_t)s * s;
+  for (size_t i = tid; i < ss; i += CT) {
+    S.b0[i] = C[i];
+    S.b1[i] = (i / s == i % s) ? 1.0 : 0.0;
   }
-  if (threadIdx.x == 0) *nkept = nk;
+  for (int i = tid; i < s; i += CT) diag0[i] = C[i * s + i];
+  __syncthreads();
+  chol_threshold(S.b0, diag0, s, drop_tol, msk, &nk);
+  trsm_masked(S.b0, s, msk, S.b1, s, false, true);  // b1 = L^{-1} (dropped rows zero)
+  for (size_t i = tid; i < ss; i += CT) {
+    const int r = i / s, c = i % s;
+    Rinv[i] = msk[c] ? S.b1[c * s + r] : 0.0;  // R^{-1} = L^{-T}
+  }
+  for (int i = tid; i < s; i += CT) mask[i] = msk[i];
+  if (tid == 0) *nkept = nk;
 }
 
-// out (s x r) = sign * A^{-1} Rhs on the kept index set of mask (A s x s SPD there).
+// out (s x r) = sign * A^{-1} Rhs on the kept index set of mask.
 __global__ void __launch_bounds__(CT) k_spd_solve_masked(const double *A, const double *Rhs, int s,
                                                          int r, const int32_t *mask, double sign,
-                                                         double *out, double *work, DevStatus *st) {
-  double *L = work;
+                                                         double *out, double *gwork, int use_smem,
+                                                         DevStatus *st) {
+  extern __shared__ __align__(16) double dsm[];
+  __shared__ int32_t msk[256];
+  __shared__ double diag0[256];
+  __shared__ int nk;
+  const Scratch S = scratch(dsm, gwork, s, use_smem);
   const int tid = threadIdx.x;
+  for (int i = tid; i < s; i += CT) msk[i] = mask[i];
+  __syncthreads();
   for (int i = tid; i < s * s; i += CT) {
     const int a = i / s, b = i % s;
-    L[i] = (mask[a] && mask[b]) ? A[i] : 0.0;
+    S.b0[i] = (msk[a] && msk[b]) ? A[i] : 0.0;
   }
+  for (int i = tid; i < s; i += CT) diag0[i] = msk[i] ? A[i * s + i] : 0.0;
+  for (int i = tid; i < s * r; i += CT) S.b1[i] = Rhs[i];
   __syncthreads();
-  for (int j = 0; j < s; ++j) {
-    if (!mask[j]) continue;  // uniform across the CTA
-    __shared__ double d;
-    if (tid == 0) {
-      double piv = L[j * s + j];
-      if (!(piv > 0.0)) {
-        dev_fail(st, DEV_BREAKDOWN, j);
-        piv = 1.0;
-      }
-      d = sqrt(piv);
-      L[j * s + j] = d;
-    }
-    __syncthreads();
-    for (int i = j + 1 + tid; i < s; i += CT)
-      if (mask[i]) L[i * s + j] /= d;
-    __syncthreads();
-    const int rem = s - j - 1;
-    for (int idx = tid; idx < rem * rem; idx += CT) {
-      const int a = j + 1 + idx / rem, b = j + 1 + idx % rem;
-      if (a >= b && mask[a] && mask[b]) L[a * s + b] -= L[a * s + j] * L[b * s + j];
-    }
-    __syncthreads();
-  }
-  // one thread per right-hand side column: L y = rhs, L^T x = y
-  for (int c = tid; c < r; c += CT) {
-    for (int i = 0; i < s; ++i) {
-      double v = 0.0;
-      if (mask[i]) {
-        v = Rhs[i * r + c];
-        for (int t = 0; t < i; ++t)
-          if (mask[t]) v -= L[i * s + t] * out[t * r + c];
-        v /= L[i * s + i];
-      }
-      out[i * r + c] = v;
-    }
-    for (int i = s - 1; i >= 0; --i) {
-      double v = 0.0;
-      if (mask[i]) {
-        v = out[i * r + c];
-        for (int t = i + 1; t < s; ++t)
-          if (mask[t]) v -= L[t * s + i] * out[t * r + c];
-        v /= L[i * s + i];
-      }
-      out[i * r + c] = v;
-    }
-    for (int i = 0; i < s; ++i) out[i * r + c] *= sign;
-  }
+  // plain Cholesky on the kept set: a dropped pivot here means P^T Q lost definiteness
+  __shared__ int32_t kept2[256];
+  chol_threshold(S.b0, diag0, s, 0.0, kept2, &nk);
+  for (int i = tid; i < s; i += CT)
+    if (msk[i] && !kept2[i]) dev_fail(st, DEV_BREAKDOWN, i);
+  trsm_masked(S.b0, s, kept2, S.b1, r, false);
+  trsm_masked(S.b0, s, kept2, S.b1, r, true);
+  for (int i = tid; i < s * r; i += CT) out[i] = sign * S.b1[i];
 }
 
 __global__ void k_max_ratio(const double *colsq, const double *bnorm, int s, double *ratio) {
@@ -166,166 +338,69 @@ __global__ void k_sqrt_vec(const double *in, int s, double *out) {
   for (int j = threadIdx.x; j < s; j += blockDim.x) out[j] = sqrt(in[j]);
 }
 
-// Cyclic Jacobi eigenvalue algorithm for a symmetric s x s matrix A (row-major, in place)
-// with parallel (round-robin tournament) ordering of the disjoint rotation pairs; V
-// accumulates the rotations (A_orig = V diag(A) V^T). Rotation of pair (p, q) per Golub &
-// Van Loan's 2x2 symmetric Schur decomposition: tau = (a_qq - a_pp) / (2 a_pq),
-// t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c.
-__device__ void jacobi_evd(double *A, double *V, int s, double *cs, double *sn, int *pp, int *qq,
-                           int *ring) {
-  const int tid = threadIdx.x;
-  for (int i = tid; i < s * s; i += CT) V[i] = (i / s == i % s) ? 1.0 : 0.0;
-  const int se = s + (s & 1);  // even player count; player s (if odd) is a bye
-  const int npair = se / 2;
-  __syncthreads();
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    __shared__ double off, tot;
-    __shared__ double red[CT];
-    double o = 0.0, t = 0.0;
-    for (int i = tid; i < s * s; i += CT) {
-      const double v = A[i] * A[i];
-      t += v;
-      if (i / s != i % s) o += v;
-    }
-    red[tid] = o;
-    __syncthreads();
-    for (int h = CT / 2; h > 0; h >>= 1) {
-      if (tid < h) red[tid] += red[tid + h];
-      __syncthreads();
-    }
-    if (tid == 0) off = red[0];
-    __syncthreads();
-    red[tid] = t;
-    __syncthreads();
-    for (int h = CT / 2; h > 0; h >>= 1) {
-      if (tid < h) red[tid] += red[tid + h];
-      __syncthreads();
-    }
-    if (tid == 0) tot = red[0];
-    __syncthreads();
-    if (off <= 1e-30 * tot || off == 0.0) break;
-    for (int i = tid; i < se; i += CT) ring[i] = i;
-    __syncthreads();
-    for (int round = 0; round < se - 1; ++round) {
-      // pairs of this round: (ring[i], ring[se-1-i])
-      for (int k = tid; k < npair; k += CT) {
-        int p = ring[k], q = ring[se - 1 - k];
-        if (p > q) { const int x = p; p = q; q = x; }
-        pp[k] = p;
-        qq[k] = q;
-        double c = 1.0, sv = 0.0;
-        if (q < s) {
-          const double apq = A[p * s + q];
-          if (apq != 0.0) {
-            const double tau = (A[q * s + q] - A[p * s + p]) / (2.0 * apq);
-            const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + tt * tt);
-            sv = tt * c;
-          }
-        }
-        cs[k] = c;
-        sn[k] = sv;
-      }
-      __syncthreads();
-      // A <- A J (columns p, q), V <- V J
-      for (int idx = tid; idx < npair * s; idx += CT) {
-        const int k = idx / s, i = idx % s;
-        const int p = pp[k], q = qq[k];
-        if (q >= s) continue;
-        const double c = cs[k], sv = sn[k];
-        const double ap = A[i * s + p], aq = A[i * s + q];
-        A[i * s + p] = c * ap - sv * aq;
-        A[i * s + q] = sv * ap + c * aq;
-        const double vp = V[i * s + p], vq = V[i * s + q];
-        V[i * s + p] = c * vp - sv * vq;
-        V[i * s + q] = sv * vp + c * vq;
-      }
-      __syncthreads();
-      // A <- J^T A (rows p, q)
-      for (int idx = tid; idx < npair * s; idx += CT) {
-        const int k = idx / s, j = idx % s;
-        const int p = pp[k], q = qq[k];
-        if (q >= s) continue;
-        const double c = cs[k], sv = sn[k];
-        const double ap = A[p * s + j], aq = A[q * s + j];
-        A[p * s + j] = c * ap - sv * aq;
-        A[q * s + j] = sv * ap + c * aq;
-      }
-      __syncthreads();
-      // rotate the tournament ring (player 0 fixed)
-      if (tid == 0) {
-        const int last = ring[se - 1];
-        for (int i = se - 1; i > 1; --i) ring[i] = ring[i - 1];
-        ring[1] = last;
-      }
-      __syncthreads();
-    }
+// ---------------------------------------------------------------- Nyström core
+// Algorithm 2 steps 5-10 from K = Y^T Y and C = G^T Y (s x s):
+//  5. Y = QR by Cholesky-QR: K = L L^T on the kept columns S (threshold drop_tol),
+//     R_full = L^{-1} K[S, :] (= R when nothing is dropped), Q = Y_S L^{-T};
+//  6. C = (C + C^T)/2;  7. EVD C = V D V^T, keep d >= eps_rel max(d), d > 0 (r values);
+//  8. T = R_full V1 D1^{-1} V1^T R_full^T;  9. EVD T = W E W^T, descending;
+// 10. U = Q W(:, 1:k) = Y (L^{-T} W(:, 1:k)): Mix (s x k), Sigma(1:kk), kk = min(k, r, |S|);
+//     columns and Sigma beyond kk are zero.
+// Three s x s buffers b0, b1, b2 (shared memory when s <= SMEM_S); gw (global) keeps L^{-1}
+// and R_full between phases (2 s x s) plus the fallback buffers (3 s x s).
+__device__ void gemm_nn(const double *A, const double *B, double *Cm, int s) {  // C = A B
+  for (size_t idx = threadIdx.x; idx < (size_t)s * s; idx += CT) {
+    const int i = idx / s, j = idx % s;
+    double v = 0.0;
+    for (int t = 0; t < s; ++t) v += A[i * s + t] * B[t * s + j];
+    Cm[idx] = v;
   }
   __syncthreads();
 }
 
-// Algorithm 2 steps 5-10 from K = Y^T Y and C = G^T Y (s x s):
-//  5. Y = QR by Cholesky-QR: K = R^T R on the kept columns S (threshold drop_tol);
-//     R_full = L^{-1} K[S, :] (|S| x s), equal to R when nothing is dropped.
-//  6. C = (C + C^T)/2;  7. EVD C = V D V^T, keep d >= eps_rel max(d), d > 0 (r values);
-//  8. T = R_full V1 D1^{-1} V1^T R_full^T;  9. EVD T = W E W^T, descending;
-// 10. U = Q W(:, 1:k) = Y (R_SS^{-1} W(:, 1:k)): Mix = L^{-T} W_k (s x kk), Sigma = E(1:kk),
-//     kk = min(k, r).
 __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C, int s, int k,
                                                 double eps_rel, double drop_tol, double *Mix,
-                                                double *Sigma, int32_t *rank, double *work) {
-  __shared__ int nk;
-  __shared__ int r_keep;
+                                                double *Sigma, int32_t *rank, double *gw,
+                                                int use_smem) {
+  extern __shared__ __align__(16) double dsm[];
+  __shared__ int nk, r_keep;
+  __shared__ int32_t msk[256], keepc[256], order[256];
+  __shared__ double diag0[256], dvals[256], evals[256];
   const int tid = threadIdx.x;
   const size_t ss = (size_t)s * s;
-  double *L = work;            // Cholesky of K
-  double *Linv = L + ss;
-  double *Rf = Linv + ss;      // R_full (s x s, rows of dropped = 0)
-  double *Cs = Rf + ss;        // symmetric C -> eigenvalues on diagonal
-  double *V = Cs + ss;
-  double *RV = V + ss;         // R_full V1 D1^{-1/2}
-  double *T = RV + ss;
-  double *W = T + ss;
-  double *diag0 = W + ss;
-  double *dvals = diag0 + s;
-  double *evals = dvals + s;
-  double *cs = evals + s;
-  double *sn = cs + s;
-  int32_t *mask = reinterpret_cast<int32_t *>(sn + s);
-  int32_t *keepc = mask + s;
-  int32_t *order = keepc + s;
-  int *pp = order + s;
-  int *qq = pp + s;
-  int *ring = qq + s;
+  double *gLinv = gw, *gRf = gw + ss;
+  const Scratch S = scratch(dsm, gw + 2 * ss, s, use_smem);
 
-  // step 5: Cholesky-QR
-  for (size_t i = tid; i < ss; i += CT) L[i] = K[i];
+  // step 5: Cholesky-QR of Y through K: b0 = L, b1 = L^{-1}
+  for (size_t i = tid; i < ss; i += CT) {
+    S.b0[i] = K[i];
+    S.b1[i] = (i / s == i % s) ? 1.0 : 0.0;
+  }
   for (int i = tid; i < s; i += CT) diag0[i] = K[i * s + i];
   __syncthreads();
-  chol_threshold(L, diag0, s, drop_tol, mask, &nk);
-  lower_inverse(L, mask, s, Linv);
-  // R_full = Linv K
-  for (size_t idx = tid; idx < ss; idx += CT) {
-    const int i = idx / s, j = idx % s;
-    double v = 0.0;
-    if (mask[i])
-      for (int t = 0; t <= i; ++t) v += Linv[i * s + t] * K[t * s + j];
-    Rf[idx] = v;
-  }
-  // step 6: symmetrize C
-  for (size_t idx = tid; idx < ss; idx += CT) {
-    const int i = idx / s, j = idx % s;
-    Cs[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
+  chol_threshold(S.b0, diag0, s, drop_tol, msk, &nk);
+  trsm_masked(S.b0, s, msk, S.b1, s, false, true);
+  for (size_t i = tid; i < ss; i += CT) {
+    gLinv[i] = S.b1[i];
+    S.b2[i] = K[i];
   }
   __syncthreads();
-  // step 7: EVD of C
-  jacobi_evd(Cs, V, s, cs, sn, pp, qq, ring);
+  gemm_nn(S.b1, S.b2, S.b0, s);  // R_full = L^{-1} K (rows of dropped columns are zero)
+  for (size_t i = tid; i < ss; i += CT) gRf[i] = S.b0[i];
+  // step 6: symmetric C into b0
+  for (size_t idx = tid; idx < ss; idx += CT) {
+    const int i = idx / s, j = idx % s;
+    S.b0[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
+  }
+  __syncthreads();
+  // step 7: EVD of C: eigenvalues on b0's diagonal, V in b1
+  eig_sym(S.b0, s, S.b1, S.b2);
   if (tid == 0) {
     double dmax = 0.0;
-    for (int j = 0; j < s; ++j) dmax = fmax(dmax, Cs[j * s + j]);
+    for (int j = 0; j < s; ++j) dmax = fmax(dmax, S.b0[j * s + j]);
     int r = 0;
     for (int j = 0; j < s; ++j) {
-      const double d = Cs[j * s + j];
+      const double d = S.b0[j * s + j];
       dvals[j] = d;
       keepc[j] = (d > 0.0 && d >= eps_rel * dmax) ? 1 : 0;
       r += keepc[j];
@@ -333,28 +408,30 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
     r_keep = r;
   }
   __syncthreads();
-  // step 8: RV = R_full V1 D1^{-1/2} (s x s, zero columns for dropped eigenvalues)
+  // step 8: b0 = RV = R_full V1 D1^{-1/2}; b2 = R_full
+  for (size_t i = tid; i < ss; i += CT) S.b2[i] = gRf[i];
+  __syncthreads();
+  gemm_nn(S.b2, S.b1, S.b0, s);
   for (size_t idx = tid; idx < ss; idx += CT) {
-    const int i = idx / s, j = idx % s;
-    double v = 0.0;
-    if (keepc[j]) {
-      for (int t = 0; t < s; ++t) v += Rf[i * s + t] * V[t * s + j];
-      v /= sqrt(dvals[j]);
-    }
-    RV[idx] = v;
+    const int j = idx % s;
+    S.b0[idx] = keepc[j] ? S.b0[idx] / sqrt(dvals[j]) : 0.0;
   }
   __syncthreads();
-  for (size_t idx = tid; idx < ss; idx += CT) {
+  for (size_t idx = tid; idx < ss; idx += CT) {  // b1 = T = RV RV^T
     const int i = idx / s, j = idx % s;
+    if (j < i) continue;
     double v = 0.0;
-    for (int t = 0; t < s; ++t) v += RV[i * s + t] * RV[j * s + t];
-    T[idx] = v;
+    for (int t = 0; t < s; ++t) v += S.b0[i * s + t] * S.b0[j * s + t];
+    S.b1[i * s + j] = v;
+    S.b1[j * s + i] = v;
   }
   __syncthreads();
-  // step 9: EVD of T, order descending
-  jacobi_evd(T, W, s, cs, sn, pp, qq, ring);
+  for (size_t i = tid; i < ss; i += CT) S.b0[i] = S.b1[i];
+  __syncthreads();
+  // step 9: EVD of T: eigenvalues on b0's diagonal, W in b1
+  eig_sym(S.b0, s, S.b1, S.b2);
   if (tid == 0) {
-    for (int j = 0; j < s; ++j) { evals[j] = T[j * s + j]; order[j] = j; }
+    for (int j = 0; j < s; ++j) { evals[j] = S.b0[j * s + j]; order[j] = j; }
     for (int a = 0; a < s; ++a) {  // selection sort, descending
       int best = a;
       for (int b = a + 1; b < s; ++b)
@@ -364,34 +441,49 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
     const int kk = min(k, min(r_keep, nk));
     *rank = kk;
     for (int j = 0; j < k; ++j) Sigma[j] = j < kk ? fmax(evals[order[j]], 0.0) : 0.0;
+    r_keep = kk;
   }
+  for (size_t i = tid; i < ss; i += CT) S.b2[i] = gLinv[i];
   __syncthreads();
-  // step 10: Mix = Linv^T W(:, order[0:kk])  (U = Y Mix = Q W_k)
-  const int kk = min(k, min(r_keep, nk));
+  // step 10: Mix = L^{-T} W(:, order[0:kk])
+  const int kk = r_keep;
   for (size_t idx = tid; idx < (size_t)s * k; idx += CT) {
     const int i = idx / k, j = idx % k;
     double v = 0.0;
-    if (j < kk && mask[i]) {
+    if (j < kk && msk[i]) {
       const int col = order[j];
-      for (int t = i; t < s; ++t) v += Linv[t * s + i] * W[t * s + col];
+      for (int t = i; t < s; ++t) v += S.b2[t * s + i] * S.b1[t * s + col];
     }
     Mix[idx] = v;
   }
 }
 
+size_t smem_for(int s) { return s <= SMEM_S ? 3 * (size_t)s * s * sizeof(double) : 0; }
+
+template <typename K>
+void set_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    NSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
 }  // namespace
 
+size_t core_work_size(int s) { return 8 * (size_t)s * s + 64; }
+
 void launch_chol_drop(const double *C, int s, double drop_tol, double *Rinv, int32_t *mask,
-                      int32_t *nkept, cudaStream_t stream) {
-  // the scratch follows Rinv: callers allocate 3*s*s + s doubles after Rinv (see engine)
-  k_chol_drop<<<1, CT, 0, stream>>>(C, s, drop_tol, Rinv, mask, nkept, Rinv + (size_t)s * s);
+                      int32_t *nkept, double *gwork, cudaStream_t stream) {
+  const size_t sm = smem_for(s);
+  set_smem(k_chol_drop, sm);
+  k_chol_drop<<<1, CT, sm, stream>>>(C, s, drop_tol, Rinv, mask, nkept, gwork, sm > 0);
   NSP_LAUNCH_CHECK();
 }
 
 void launch_spd_solve_masked(const double *PtQ, const double *Rhs, int s, int r,
-                             const int32_t *mask, double sign, double *out, double *Lwork,
+                             const int32_t *mask, double sign, double *out, double *gwork,
                              DevStatus *st, cudaStream_t stream) {
-  k_spd_solve_masked<<<1, CT, 0, stream>>>(PtQ, Rhs, s, r, mask, sign, out, Lwork, st);
+  const size_t sm = (s <= SMEM_S && r <= s) ? smem_for(s) : 0;
+  set_smem(k_spd_solve_masked, sm);
+  k_spd_solve_masked<<<1, CT, sm, stream>>>(PtQ, Rhs, s, r, mask, sign, out, gwork, sm > 0, st);
   NSP_LAUNCH_CHECK();
 }
 
@@ -406,12 +498,14 @@ void launch_sqrt_vec(const double *in, int s, double *out, cudaStream_t stream) 
   NSP_LAUNCH_CHECK();
 }
 
-size_t nystrom_work_size(int s) { return 8 * (size_t)s * s + 16 * (size_t)s + 64; }
+size_t nystrom_work_size(int s) { return 5 * (size_t)s * s + 64; }
 
 void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
                          double drop_tol, double *Mix, double *Sigma, int32_t *rank,
                          double *work, cudaStream_t stream) {
-  k_nystrom<<<1, CT, 0, stream>>>(K, C, s, k, eps_rel, drop_tol, Mix, Sigma, rank, work);
+  const size_t sm = smem_for(s);
+  set_smem(k_nystrom, sm);
+  k_nystrom<<<1, CT, sm, stream>>>(K, C, s, k, eps_rel, drop_tol, Mix, Sigma, rank, work, sm > 0);
   NSP_LAUNCH_CHECK();
 }
 

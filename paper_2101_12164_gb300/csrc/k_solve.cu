@@ -1,22 +1,262 @@
-// Supernodal triangular solves with s right-hand sides: X = A_b^{-1} B for every block b
-// of a forest at once (the A_I^{-1} inside S_Gamma, §2.3 eq. (schur_complement), and
-// A_G^{-1}, the first-level preconditioner S1 of eq. (S1)).
+// Supernodal triangular solves X = A_b^{-1} B for every block b of a forest at once, s right-
+// hand sides (the A_I^{-1} inside S_Gamma, §2.3 eq. (schur_complement), and A_G^{-1}, the
+// first-level preconditioner S1 of §2.3 eq. (S1)).
 //
-// With the panel P_J = [inv(L11); L21 inv(L11)] of each supernode J:
+// With the panel P_J = [inv(L11); L21 inv(L11)] of each supernode J (see k_factor.cu):
 //   forward  (L y = b):  y_J = P_top f_top,  u_J = f_bot - P_bot f_top,
 //     f = b on J's columns plus the children's update rows u_C (extend-add gather);
 //   backward (L^T x = y): x_J = P_top^T y_J - P_bot^T x[rows of J below its columns].
-// Each work item is one tile of rows of one supernode; items of one tree level run in one
-// launch. The tile is a dense (TM x K) * (K x s) product on CUDA cores, K staged in chunks
-// of TK through shared memory.
+//
+// One persistent launch runs a whole solve: CTAs claim work items in topological order
+// (all forward items by tree level, then all backward items by reverse level) from an atomic
+// counter and wait, with a bounded spin, on per-supernode completion counters:
+//   forward item of J   : after every forward item of J's children;
+//   backward item of J  : after every backward item of J's parent (after J's own forward
+//                         items for a root).
+// A CTA only waits for items claimed before its own, so the schedule cannot deadlock.
+// Counters grow monotonically; launch e waits for e x (units per supernode).
+// Item kinds:
+//   vector (s = 1): 16-byte vector loads of the panel, 8 warps split the K dimension
+//                   (forward) or a warp per panel column (backward); supernodes with
+//                   m <= 96, w <= 32 are processed a warp each, up to 8 per item;
+//   block (s > 1):  a register-blocked (TM x K) * (K x s) product per tile on CUDA cores.
 #include "kernels.cuh"
 
 namespace nsp {
 namespace {
 
-constexpr int ST = 256;  // threads
-constexpr int TK = 32;   // K chunk
+constexpr int ST = 256;      // threads per CTA
+constexpr int TK = 32;       // K chunk of the block product
+constexpr int MAX_SPINS = 1 << 22;
 
+// ---------------------------------------------------------------- synchronization
+__device__ __forceinline__ int ld_acquire(const int32_t *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0 waits until *p >= target. Returns false (and sets the abort flag) on timeout or
+// when another CTA has aborted.
+__device__ bool wait_geq(const int32_t *p, int32_t target, int32_t *abort_flag, DevStatus *st,
+                         int32_t where) {
+  int spins = 0;
+  while (ld_acquire(p) < target) {
+    if (ld_relaxed(abort_flag)) return false;
+    if (++spins > MAX_SPINS) {
+      atomicExch(abort_flag, 1);
+      dev_fail(st, DEV_TIMEOUT, where);
+      return false;
+    }
+    __nanosleep(64);
+  }
+  return true;
+}
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static V load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
+  __device__ static float get(const V &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+};
+template <>
+struct Vec<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static V load(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
+  __device__ static double get(const V &v, int i) { return i == 0 ? v.x : v.y; }
+};
+
+struct SweepCtx {
+  ForestDev f;
+  SweepPlan p;
+  int32_t epoch;
+  int32_t claim_base;
+  int s;
+  DevStatus *st;
+};
+
+// f_top / f_bot entry k of supernode J (column b, s columns): B row + children's update rows
+template <typename T>
+__device__ __forceinline__ T front_rhs(const SweepCtx &c, const T *B, const T *U, int J, int k,
+                                       int col, bool with_b) {
+  const int64_t rp = c.f.sn_rowptr[J];
+  T v = (with_b && B) ? B[(size_t)(c.f.sn_first[J] + k) * c.s + col] : T(0);
+  for (int64_t e = c.f.gptr[rp + k]; e < c.f.gptr[rp + k + 1]; ++e)
+    v += __ldcg(&U[(size_t)c.f.gsrc[e] * c.s + col]);
+  return v;
+}
+
+// ---------------------------------------------------------------- vector items (s = 1)
+// Forward tile: 16 row groups of VN rows x 16 K groups; each thread keeps 8 vector loads in
+// flight. Rows of the tile: 16 VN (64 floats / 32 doubles).
+template <typename T>
+__device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y, T *U, int J,
+                             int r0, T *sm) {
+  using VT = Vec<T>;
+  constexpr int VN = VT::N, TMV = 16 * VN;
+  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
+  const int first = c.f.sn_first[J];
+  const T *P = panel + c.f.sn_panel[J];
+  const int r1 = min(r0 + TMV, m);
+  const int kmax = (r1 <= w) ? r1 : w;
+  T *fs = sm;                      // [kmax]
+  T *red = sm + ((ld + 3) & ~3);   // [16][TMV]
+  const int tid = threadIdx.x;
+  for (int k = tid; k < kmax; k += ST) fs[k] = front_rhs<T>(c, B, U, J, k, 0, true);
+  __syncthreads();
+  const int rg = tid & 15, kg = tid >> 4;
+  const int row = r0 + VN * rg;
+  T acc[VN];
+#pragma unroll
+  for (int i = 0; i < VN; ++i) acc[i] = T(0);
+  if (row < ld) {
+    int k = kg;
+    for (; k + 112 < kmax; k += 128) {
+      typename VT::V v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = VT::load(P + row + (size_t)(k + 16 * u) * ld);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const T f = fs[k + 16 * u];
+#pragma unroll
+        for (int i = 0; i < VN; ++i) acc[i] += VT::get(v[u], i) * f;
+      }
+    }
+    for (; k < kmax; k += 16) {
+      typename VT::V v0 = VT::load(P + row + (size_t)k * ld);
+      const T f0 = fs[k];
+#pragma unroll
+      for (int i = 0; i < VN; ++i) acc[i] += VT::get(v0, i) * f0;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < VN; ++i) red[kg * TMV + VN * rg + i] = acc[i];
+  __syncthreads();
+  if (tid < TMV) {
+    const int r = r0 + tid;
+    if (r < r1) {
+      T v = T(0);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) v += red[q * TMV + tid];
+      if (r < w) {
+        Y[first + r] = v;
+      } else {
+        U[c.f.sn_upd[J] + r - w] = front_rhs<T>(c, B, U, J, r, 0, false) - v;
+      }
+    }
+  }
+}
+
+// Backward tile: 8 consecutive panel columns, one warp each; a lane keeps up to 4 vector
+// loads of its column in flight.
+template <typename T>
+__device__ void vec_bwd_tile(const SweepCtx &c, const T *panel, const T *Y, T *X, int J, int c0,
+                             T *sm) {
+  using VT = Vec<T>;
+  constexpr int VN = VT::N, STEP = 32 * VN;
+  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
+  const int first = c.f.sn_first[J];
+  const int64_t rp = c.f.sn_rowptr[J];
+  const T *P = panel + c.f.sn_panel[J];
+  const int kbeg = c0 & ~(VN - 1);
+  T *g = sm;  // [ld]
+  const int tid = threadIdx.x;
+  for (int k = kbeg + tid; k < ld; k += ST) {
+    T v = T(0);
+    if (k < w) v = __ldcg(&Y[first + k]);
+    else if (k < m) v = -__ldcg(&X[c.f.rows[rp + k]]);
+    g[k] = v;
+  }
+  __syncthreads();
+  const int lane = tid & 31, wid = tid >> 5;
+  const int col = c0 + wid;
+  if (col >= w) return;
+  const T *Pc = P + (size_t)col * ld;
+  const int ks = col & ~(VN - 1);
+  T acc = T(0);
+  int k = ks + VN * lane;
+  for (; k + 3 * STEP < ld; k += 4 * STEP) {
+    typename VT::V v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = VT::load(Pc + k + u * STEP);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int i = 0; i < VN; ++i) acc += VT::get(v[u], i) * g[k + u * STEP + i];
+  }
+  for (; k < ld; k += STEP) {
+    typename VT::V v = VT::load(Pc + k);
+#pragma unroll
+    for (int i = 0; i < VN; ++i) acc += VT::get(v, i) * g[k + i];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) X[first + col] = acc;
+}
+
+// a warp processes one small supernode (m <= 96, w <= 32)
+template <typename T>
+__device__ void vec_fwd_small(const SweepCtx &c, const T *panel, const T *B, T *Y, T *U, int J) {
+  const int lane = threadIdx.x & 31;
+  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
+  const int first = c.f.sn_first[J];
+  const T *P = panel + c.f.sn_panel[J];
+  const T fk = lane < w ? front_rhs<T>(c, B, U, J, lane, 0, true) : T(0);
+  T acc[3] = {T(0), T(0), T(0)};
+  for (int k = 0; k < w; ++k) {
+    const T f = __shfl_sync(0xffffffffu, fk, k);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int r = lane + 32 * q;
+      if (r < m) acc[q] += __ldg(&P[r + (size_t)k * ld]) * f;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int r = lane + 32 * q;
+    if (r >= m) continue;
+    if (r < w) Y[first + r] = acc[q];
+    else U[c.f.sn_upd[J] + r - w] = front_rhs<T>(c, B, U, J, r, 0, false) - acc[q];
+  }
+}
+
+template <typename T>
+__device__ void vec_bwd_small(const SweepCtx &c, const T *panel, const T *Y, T *X, int J,
+                              T *tile /* [32][33] of this warp */) {
+  const int lane = threadIdx.x & 31;
+  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
+  const int first = c.f.sn_first[J];
+  const int64_t rp = c.f.sn_rowptr[J];
+  const T *P = panel + c.f.sn_panel[J];
+  T acc = T(0);
+  for (int kb = 0; kb < m; kb += 32) {
+    const int k = kb + lane;
+    T gk = T(0);
+    if (k < w) gk = __ldcg(&Y[first + k]);
+    else if (k < m) gk = -__ldcg(&X[c.f.rows[rp + k]]);
+    for (int col = 0; col < w; ++col)
+      tile[lane * 33 + col] = k < m ? __ldg(&P[k + (size_t)col * ld]) : T(0);
+    __syncwarp();
+    const int kn = min(32, m - kb);
+    for (int kk = 0; kk < kn; ++kk) {
+      const T gv = __shfl_sync(0xffffffffu, gk, kk);
+      if (lane < w) acc += tile[kk * 33 + lane] * gv;
+    }
+    __syncwarp();
+  }
+  if (lane < w) X[first + lane] = acc;
+}
+
+// ---------------------------------------------------------------- block items (s > 1)
 template <int TC, int CM, int RM>
 struct Cfg {
   static constexpr int TR = ST / TC;
@@ -24,48 +264,87 @@ struct Cfg {
   static constexpr int NCP = TC * CM;
 };
 
+// Sources of the extend-add gather for front positions [p0, p0 + cnt) of supernode J staged
+// in shared memory: off[i] = first source of position p0 + i relative to off[0],
+// src[j] = update row (valid when off[cnt] <= kSrcCap; otherwise read from global memory).
+constexpr int kSrcCap = 4 * 64;
+struct GatherStage {
+  int32_t off[257];
+  int32_t src[kSrcCap];
+  int64_t base;
+  int total;
+};
+
+__device__ void stage_sources(const SweepCtx &c, int J, int p0, int cnt, GatherStage &g) {
+  const int64_t rp = c.f.sn_rowptr[J];
+  const int64_t b0 = c.f.gptr[rp + p0];
+  for (int i = threadIdx.x; i <= cnt; i += ST) g.off[i] = (int32_t)(c.f.gptr[rp + p0 + i] - b0);
+  if (threadIdx.x == 0) g.base = b0;
+  __syncthreads();
+  g.total = g.off[cnt];
+  if (g.total <= kSrcCap)
+    for (int i = threadIdx.x; i < g.total; i += ST) g.src[i] = (int32_t)c.f.gsrc[b0 + i];
+  __syncthreads();
+}
+
+// sum of the update rows landing on staged position i, column col
+template <typename T>
+__device__ __forceinline__ T gather_sum(const SweepCtx &c, const GatherStage &g, const T *U, int i,
+                                        int col) {
+  const int e0 = g.off[i], e1 = g.off[i + 1];
+  const int s = c.s;
+  T v = T(0);
+  if (g.total <= kSrcCap) {
+    T t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = (e0 + q < e1) ? __ldcg(&U[(size_t)g.src[e0 + q] * s + col]) : T(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v += t[q];
+    for (int e = e0 + 4; e < e1; ++e) v += __ldcg(&U[(size_t)g.src[e] * s + col]);
+  } else {
+    for (int e = e0; e < e1; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[g.base + e] * s + col]);
+  }
+  return v;
+}
+
 template <typename T, int TC, int CM, int RM>
-__global__ void __launch_bounds__(ST) k_fwd(ForestDev f, const TileItem *items,
-                                            const T *__restrict__ panel,
-                                            const T *__restrict__ B, T *__restrict__ Y,
-                                            T *__restrict__ U, int s) {
+__device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *B, T *Y,
+                             T *U, int J, int r0, T *sm) {
   using C = Cfg<TC, CM, RM>;
   constexpr int TM = C::TM, NCP = C::NCP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *As = reinterpret_cast<T *>(smem_raw);  // [TK][TM + 1]
-  T *Bs = As + TK * (TM + 1);               // [TK][NCP]
-  const TileItem it = items[blockIdx.x];
-  const int J = it.sn, r0 = it.r0;
-  const int w = f.sn_w[J], m = f.sn_m[J];
-  const int first = f.sn_first[J];
-  const int64_t rp = f.sn_rowptr[J];
-  const T *P = panel + f.sn_panel[J];
+  static_assert(TK <= 256 && TM <= 256, "gather staging holds 256 positions");
+  __shared__ GatherStage gs;
+  T *As = sm;                  // [TK][TM + 1]
+  T *Bs = As + TK * (TM + 1);  // [TK][NCP]
+  const int s = c.s;
+  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
+  const int first = c.f.sn_first[J];
+  const T *P = panel + c.f.sn_panel[J];
   const int r1 = min(r0 + TM, m);
-  const int kmax = (r1 <= w) ? r1 : w;  // inv(L11) is lower triangular
+  const int kmax = (r1 <= w) ? r1 : w;
   const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
   T acc[RM][CM];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
-
   for (int k0 = 0; k0 < kmax; k0 += TK) {
+    const int kc = min(TK, kmax - k0);
+    stage_sources(c, J, k0, kc, gs);
     for (int i = tid; i < TK * TM; i += ST) {
       const int r = i % TM, k = i / TM;
       T v = T(0);
-      if (r0 + r < m && k0 + k < kmax) v = P[(size_t)(r0 + r) + (size_t)(k0 + k) * m];
+      if (r0 + r < m && k < kc) v = __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]);
       As[k * (TM + 1) + r] = v;
     }
     for (int i = tid; i < TK * NCP; i += ST) {
-      const int c = i % NCP, k = i / NCP;
-      const int kk = k0 + k;
+      const int col = i % NCP, k = i / NCP;
       T v = T(0);
-      if (kk < kmax && c < s) {
-        if (B) v = B[(size_t)(first + kk) * s + c];
-        for (int64_t e = f.gptr[rp + kk]; e < f.gptr[rp + kk + 1]; ++e)
-          v += U[(size_t)f.gsrc[e] * s + c];
+      if (k < kc && col < s) {
+        if (B) v = B[(size_t)(first + k0 + k) * s + col];
+        v += gather_sum<T>(c, gs, U, k, col);
       }
-      Bs[k * NCP + c] = v;
+      Bs[k * NCP + col] = v;
     }
     __syncthreads();
 #pragma unroll 8
@@ -82,7 +361,10 @@ __global__ void __launch_bounds__(ST) k_fwd(ForestDev f, const TileItem *items,
     }
     __syncthreads();
   }
-  const int64_t upd = f.sn_upd[J];
+  // epilogue: y rows, or update rows u = f_bot - P_bot f_top
+  const int64_t upd = c.f.sn_upd[J];
+  const int rb = max(r0, w);
+  if (r1 > rb) stage_sources(c, J, rb, r1 - rb, gs);
 #pragma unroll
   for (int i = 0; i < RM; ++i) {
     const int r = r0 + tr * RM + i;
@@ -90,40 +372,33 @@ __global__ void __launch_bounds__(ST) k_fwd(ForestDev f, const TileItem *items,
     if (r < w) {
 #pragma unroll
       for (int j = 0; j < CM; ++j) {
-        const int c = tc + TC * j;
-        if (c < s) Y[(size_t)(first + r) * s + c] = acc[i][j];
+        const int col = tc + TC * j;
+        if (col < s) Y[(size_t)(first + r) * s + col] = acc[i][j];
       }
     } else {
-      const int64_t g0 = f.gptr[rp + r], g1 = f.gptr[rp + r + 1];
 #pragma unroll
       for (int j = 0; j < CM; ++j) {
-        const int c = tc + TC * j;
-        if (c < s) {
-          T v = -acc[i][j];
-          for (int64_t e = g0; e < g1; ++e) v += U[(size_t)f.gsrc[e] * s + c];
-          U[(size_t)(upd + r - w) * s + c] = v;
-        }
+        const int col = tc + TC * j;
+        if (col < s)
+          U[(size_t)(upd + r - w) * s + col] = gather_sum<T>(c, gs, U, r - rb, col) - acc[i][j];
       }
     }
   }
 }
 
 template <typename T, int TC, int CM, int RM>
-__global__ void __launch_bounds__(ST) k_bwd(ForestDev f, const TileItem *items,
-                                            const T *__restrict__ panel,
-                                            const T *__restrict__ Y, T *__restrict__ X,
-                                            int s) {
+__device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *Y, T *X,
+                             int J, int r0, T *sm) {
   using C = Cfg<TC, CM, RM>;
   constexpr int TM = C::TM, NCP = C::NCP;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *As = reinterpret_cast<T *>(smem_raw);  // [TK][TM + 1]
-  T *Bs = As + TK * (TM + 1);               // [TK][NCP]
-  const TileItem it = items[blockIdx.x];
-  const int J = it.sn, r0 = it.r0;
-  const int w = f.sn_w[J], m = f.sn_m[J];
-  const int first = f.sn_first[J];
-  const int64_t rp = f.sn_rowptr[J];
-  const T *P = panel + f.sn_panel[J];
+  __shared__ int32_t rows_s[TK];
+  T *As = sm;
+  T *Bs = As + TK * (TM + 1);
+  const int s = c.s;
+  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
+  const int first = c.f.sn_first[J];
+  const int64_t rp = c.f.sn_rowptr[J];
+  const T *P = panel + c.f.sn_panel[J];
   const int r1 = min(r0 + TM, w);
   const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
   T acc[RM][CM];
@@ -131,23 +406,24 @@ __global__ void __launch_bounds__(ST) k_bwd(ForestDev f, const TileItem *items,
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
-
   for (int k0 = r0; k0 < m; k0 += TK) {
+    for (int i = tid; i < TK; i += ST) rows_s[i] = (k0 + i < m) ? c.f.rows[rp + k0 + i] : 0;
     for (int i = tid; i < TK * TM; i += ST) {
       const int k = i % TK, r = i / TK;
       T v = T(0);
-      if (r0 + r < r1 && k0 + k < m) v = P[(size_t)(k0 + k) + (size_t)(r0 + r) * m];
+      if (r0 + r < r1 && k0 + k < m) v = __ldg(&P[(size_t)(k0 + k) + (size_t)(r0 + r) * ld]);
       As[k * (TM + 1) + r] = v;
     }
+    __syncthreads();
     for (int i = tid; i < TK * NCP; i += ST) {
-      const int c = i % NCP, k = i / NCP;
+      const int col = i % NCP, k = i / NCP;
       const int kk = k0 + k;
       T v = T(0);
-      if (kk < m && c < s) {
-        if (kk < w) v = Y[(size_t)(first + kk) * s + c];
-        else v = -X[(size_t)f.rows[rp + kk] * s + c];
+      if (kk < m && col < s) {
+        if (kk < w) v = __ldcg(&Y[(size_t)(first + kk) * s + col]);
+        else v = -__ldcg(&X[(size_t)rows_s[k] * s + col]);
       }
-      Bs[k * NCP + c] = v;
+      Bs[k * NCP + col] = v;
     }
     __syncthreads();
 #pragma unroll 8
@@ -170,94 +446,164 @@ __global__ void __launch_bounds__(ST) k_bwd(ForestDev f, const TileItem *items,
     if (r >= r1) continue;
 #pragma unroll
     for (int j = 0; j < CM; ++j) {
-      const int c = tc + TC * j;
-      if (c < s) X[(size_t)(first + r) * s + c] = acc[i][j];
+      const int col = tc + TC * j;
+      if (col < s) X[(size_t)(first + r) * s + col] = acc[i][j];
     }
   }
 }
 
+// ---------------------------------------------------------------- the persistent sweep
+// item_b >= 0: tile of supernode item_a starting at row/column item_b;
+// item_b < 0 : group of -item_b small supernodes group_sn[item_a ...] (vector mode only).
+template <typename T, int TC, int CM, int RM, bool VECTOR>
+__global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ panel,
+                                              const T *B, T *Y, T *U, T *X) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  __shared__ int s_item, s_ok;
+  const SweepPlan &p = c.p;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(p.claim, 1) - c.claim_base;
+    __syncthreads();
+    const int it = s_item;
+    if (it >= p.nitems) break;
+    const bool fwd = it < p.nfwd;
+    const int a = p.item_a[it], b = p.item_b[it];
+    const int nmem = b < 0 ? -b : 1;
+    // dependencies
+    if (threadIdx.x == 0) {
+      bool ok = ld_relaxed(p.abort_flag) == 0;
+      for (int q = 0; q < nmem && ok; ++q) {
+        const int J = b < 0 ? p.group_sn[a + q] : a;
+        if (fwd) {
+          ok = wait_geq(&p.cnt_f[J], c.epoch * p.need_f[J], p.abort_flag, c.st, J);
+        } else {
+          const int par = p.sn_parent[J];
+          ok = par >= 0 ? wait_geq(&p.done_b[par], c.epoch * p.units_b[par], p.abort_flag, c.st, J)
+                        : wait_geq(&p.self_f[J], c.epoch * p.units_f[J], p.abort_flag, c.st, J);
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (s_ok) {
+      if (b < 0) {
+        const int wid = threadIdx.x >> 5;
+        if (wid < nmem) {
+          const int J = p.group_sn[a + wid];
+          if (fwd) vec_fwd_small<T>(c, panel, B, Y, U, J);
+          else vec_bwd_small<T>(c, panel, Y, X, J, sm + wid * 32 * 33);
+        }
+      } else if (VECTOR) {
+        if (fwd) vec_fwd_tile<T>(c, panel, B, Y, U, a, b, sm);
+        else vec_bwd_tile<T>(c, panel, Y, X, a, b, sm);
+      } else {
+        if (fwd) blk_fwd_tile<T, TC, CM, RM>(c, panel, B, Y, U, a, b, sm);
+        else blk_bwd_tile<T, TC, CM, RM>(c, panel, Y, X, a, b, sm);
+      }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && s_ok) {
+      for (int q = 0; q < nmem; ++q) {
+        const int J = b < 0 ? p.group_sn[a + q] : a;
+        if (fwd) {
+          atomicAdd(&p.self_f[J], 1);
+          const int par = p.sn_parent[J];
+          if (par >= 0) atomicAdd(&p.cnt_f[par], 1);
+        } else {
+          atomicAdd(&p.done_b[J], 1);
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int TC, int CM, int RM, bool VECTOR>
+void run_sweep(const SweepCtx &c, int grid, size_t smem, const T *panel, const T *B, T *Y,
+               T *U, T *X, cudaStream_t st) {
+  static size_t attr = 0;
+  if (smem > 48 * 1024 && smem > attr) {
+    NSP_CUDA(cudaFuncSetAttribute(k_sweep<T, TC, CM, RM, VECTOR>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  k_sweep<T, TC, CM, RM, VECTOR><<<grid, ST, smem, st>>>(c, panel, B, Y, U, X);
+  NSP_LAUNCH_CHECK();
+}
+
 template <typename T, int TC, int CM, int RM>
-size_t smem_bytes() {
+size_t blk_smem() {
   using C = Cfg<TC, CM, RM>;
   return sizeof(T) * (size_t)(TK * (C::TM + 1) + TK * C::NCP);
 }
 
-template <typename T, int TC, int CM, int RM>
-void run_fwd(const ForestDev &f, const TileItem *items, int n, const T *panel, const T *B,
-             T *Y, T *U, int s, cudaStream_t st) {
-  const size_t sm = smem_bytes<T, TC, CM, RM>();
-  static bool attr = false;
-  if (!attr) {
-    NSP_CUDA(cudaFuncSetAttribute(k_fwd<T, TC, CM, RM>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
+template <typename T, int TC, int CM, int RM, bool VECTOR>
+int sweep_grid(size_t smem) {
+  static int grid = 0;
+  static size_t for_smem = 0;
+  if (grid == 0 || for_smem != smem) {
+    int dev = 0, sms = 0, per = 0;
+    NSP_CUDA(cudaGetDevice(&dev));
+    NSP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (smem > 48 * 1024)
+      NSP_CUDA(cudaFuncSetAttribute(k_sweep<T, TC, CM, RM, VECTOR>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    NSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<T, TC, CM, RM, VECTOR>,
+                                                           ST, smem));
+    grid = sms * std::max(1, std::min(per, 4));
+    for_smem = smem;
   }
-  k_fwd<T, TC, CM, RM><<<n, ST, sm, st>>>(f, items, panel, B, Y, U, s);
-  NSP_LAUNCH_CHECK();
+  return grid;
 }
 
-template <typename T, int TC, int CM, int RM>
-void run_bwd(const ForestDev &f, const TileItem *items, int n, const T *panel, const T *Y,
-             T *X, int s, cudaStream_t st) {
-  const size_t sm = smem_bytes<T, TC, CM, RM>();
-  static bool attr = false;
-  if (!attr) {
-    NSP_CUDA(cudaFuncSetAttribute(k_bwd<T, TC, CM, RM>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    attr = true;
-  }
-  k_bwd<T, TC, CM, RM><<<n, ST, sm, st>>>(f, items, panel, Y, X, s);
-  NSP_LAUNCH_CHECK();
+template <typename T, int TC, int CM, int RM, bool VECTOR>
+void dispatch(SweepCtx c, size_t smem, const T *panel, const T *B, T *Y, T *U, T *X,
+              cudaStream_t st, int *grid_out) {
+  const int grid = sweep_grid<T, TC, CM, RM, VECTOR>(smem);
+  *grid_out = grid;
+  run_sweep<T, TC, CM, RM, VECTOR>(c, grid, smem, panel, B, Y, U, X, st);
 }
-
-// Column configurations: s == 1 (vector), else 16 threads across columns with CM columns
-// each and 4 rows per thread (64-row tiles).
-#define NSP_SOLVE_DISPATCH(FN, ...)                                  \
-  do {                                                               \
-    if (s == 1) FN<T, 1, 1, 1>(__VA_ARGS__);                         \
-    else if (s <= 16) FN<T, 16, 1, 4>(__VA_ARGS__);                  \
-    else if (s <= 32) FN<T, 16, 2, 4>(__VA_ARGS__);                  \
-    else if (s <= 48) FN<T, 16, 3, 4>(__VA_ARGS__);                  \
-    else if (s <= 64) FN<T, 16, 4, 4>(__VA_ARGS__);                  \
-    else if (s <= 80) FN<T, 16, 5, 4>(__VA_ARGS__);                  \
-    else if (s <= 96) FN<T, 16, 6, 4>(__VA_ARGS__);                  \
-    else if (s <= 128) FN<T, 16, 8, 4>(__VA_ARGS__);                 \
-    else if (s <= 160) FN<T, 16, 10, 4>(__VA_ARGS__);                \
-    else if (s <= 256) FN<T, 16, 16, 4>(__VA_ARGS__);                \
-    else throw Error(NSP_ERR_UNSUPPORTED, "more than 256 right-hand sides"); \
-  } while (0)
 
 }  // namespace
 
-int solve_tile_rows(int s) { return s == 1 ? ST : 64; }
+int sweep_vector_rows(int elem_bytes) { return 16 * (16 / elem_bytes); }
 
 template <typename T>
-void launch_solve_fwd(const ForestDev &f, const TileItem *items, int nitems, int tm,
-                      const T *panel, const T *B, T *Y, T *U, int s, cudaStream_t stream) {
-  if (nitems <= 0) return;
-  require(tm == solve_tile_rows(s), NSP_ERR_INVALID_ARG, "tile height mismatch");
-  NSP_SOLVE_DISPATCH(run_fwd, f, items, nitems, panel, B, Y, U, s, stream);
+int launch_sweep(const ForestDev &f, const SweepPlan &p, int32_t epoch, int32_t claim_base,
+                 const T *panel, const T *B, T *Y, T *U, T *X, int s, DevStatus *st,
+                 cudaStream_t stream) {
+  SweepCtx c{f, p, epoch, claim_base, s, st};
+  int grid = 0;
+  if (s == 1) {
+    require(p.vector, NSP_ERR_INVALID_ARG, "vector plan needed for one right-hand side");
+    const size_t ldmax = (size_t)((p.max_m + 3) & ~3) + 8;
+    const size_t smem = sizeof(T) * std::max<size_t>(ldmax + 16 * 16 * (16 / sizeof(T)), 8 * 32 * 33);
+    dispatch<T, 1, 1, 1, true>(c, smem, panel, B, Y, U, X, stream, &grid);
+    return grid;
+  }
+  require(!p.vector, NSP_ERR_INVALID_ARG, "block plan needed for several right-hand sides");
+#define NSP_BLK(TC_, CM_, RM_) \
+  dispatch<T, TC_, CM_, RM_, false>(c, blk_smem<T, TC_, CM_, RM_>(), panel, B, Y, U, X, stream, &grid)
+  if (s <= 16) NSP_BLK(16, 1, 4);
+  else if (s <= 32) NSP_BLK(16, 2, 4);
+  else if (s <= 48) NSP_BLK(16, 3, 4);
+  else if (s <= 64) NSP_BLK(16, 4, 4);
+  else if (s <= 80) NSP_BLK(16, 5, 4);
+  else if (s <= 96) NSP_BLK(16, 6, 4);
+  else if (s <= 128) NSP_BLK(16, 8, 4);
+  else if (s <= 160) NSP_BLK(16, 10, 4);
+  else if (s <= 256) NSP_BLK(16, 16, 4);
+  else throw Error(NSP_ERR_UNSUPPORTED, "more than 256 right-hand sides");
+#undef NSP_BLK
+  return grid;
 }
 
-template <typename T>
-void launch_solve_bwd(const ForestDev &f, const TileItem *items, int nitems, int tm,
-                      const T *panel, const T *Y, T *X, int s, cudaStream_t stream) {
-  if (nitems <= 0) return;
-  require(tm == solve_tile_rows(s), NSP_ERR_INVALID_ARG, "tile height mismatch");
-  NSP_SOLVE_DISPATCH(run_bwd, f, items, nitems, panel, Y, X, s, stream);
-}
-
-template void launch_solve_fwd<float>(const ForestDev &, const TileItem *, int, int,
-                                      const float *, const float *, float *, float *, int,
-                                      cudaStream_t);
-template void launch_solve_fwd<double>(const ForestDev &, const TileItem *, int, int,
-                                       const double *, const double *, double *, double *,
-                                       int, cudaStream_t);
-template void launch_solve_bwd<float>(const ForestDev &, const TileItem *, int, int,
-                                      const float *, const float *, float *, int,
-                                      cudaStream_t);
-template void launch_solve_bwd<double>(const ForestDev &, const TileItem *, int, int,
-                                       const double *, const double *, double *, int,
-                                       cudaStream_t);
+template int launch_sweep<float>(const ForestDev &, const SweepPlan &, int32_t, int32_t,
+                                 const float *, const float *, float *, float *, float *, int,
+                                 DevStatus *, cudaStream_t);
+template int launch_sweep<double>(const ForestDev &, const SweepPlan &, int32_t, int32_t,
+                                  const double *, const double *, double *, double *, double *,
+                                  int, DevStatus *, cudaStream_t);
 
 }  // namespace nsp

@@ -29,34 +29,45 @@ struct CsrDev {
   const T *val = nullptr;
 };
 
-// Work item of a level: one tile of TM rows of supernode sn, starting at row r0.
-struct TileItem {
-  int32_t sn;
-  int32_t r0;
+// Work list of one persistent solve (see k_solve.cu): nfwd forward items, then backward
+// items. Item i is a tile of supernode item_a[i] starting at row/column item_b[i], or, when
+// item_b[i] < 0, a group of -item_b[i] small supernodes group_sn[item_a[i] ...]. Counters
+// grow across launches; launch number `epoch` waits for epoch x (units per supernode).
+struct SweepPlan {
+  int32_t nitems = 0, nfwd = 0, max_m = 0;
+  bool vector = false;
+  const int32_t *item_a = nullptr, *item_b = nullptr, *group_sn = nullptr;
+  const int32_t *sn_parent = nullptr, *need_f = nullptr, *units_f = nullptr, *units_b = nullptr;
+  int32_t *cnt_f = nullptr, *self_f = nullptr, *done_b = nullptr;
+  int32_t *claim = nullptr, *abort_flag = nullptr;
 };
 
 // ---- numeric factorization (k_factor.cu) -----------------------------------------
 // Multifrontal partial Cholesky of the supernodes level_sn[0..count) (one CTA each), then
-// the panel [inv(L_JJ); L_J2 inv(L_JJ)] (m x w, column-major) written to panel.
-// block_of_sn gives the block id reported on a non-positive pivot.
+// the panel [inv(L_JJ); L_J2 inv(L_JJ)] (column-major, leading dimension panel_ld(m)).
+// A non-positive pivot records DEV_NOT_SPD with the supernode's block id.
+// clustered: each front is factorized by a cluster of factor_cluster_size() CTAs.
 template <typename T>
 void launch_factor_level(const ForestDev &f, const int32_t *level_sn, int count,
                          const double *Aval, T *front, T *panel, DevStatus *st,
-                         cudaStream_t stream);
+                         cudaStream_t stream, bool clustered);
+int factor_cluster_size();
+constexpr int kBigFront = 192;   // fronts with m >= kBigFront use the cluster kernel
 
 // ---- supernodal multi-RHS solves (k_solve.cu) ------------------------------------
-// Forward sweep over one level: for each item (sn, r0): rows [r0, r0+TM) of
-//   [y_J; u_J] = P_J f_top  (+ f_bot for update rows, minus sign),
-// f_top = B[J's columns] + children's update rows. Y, U outputs.
-// Backward: x_J = P_top^T y_J - P_bot^T x[struct rows] for output rows [r0, r0+TM).
+// One persistent launch: X = A_b^{-1} B for every block of the forest (s columns). B, X in
+// the forest's internal order; Y (n x s) and U (update rows x s) are workspaces. claim_base
+// is the claim counter's value before the launch; returns the grid size used (the counter
+// advances by nitems + grid).
 template <typename T>
-void launch_solve_fwd(const ForestDev &f, const TileItem *items, int nitems, int tm,
-                      const T *panel, const T *B, T *Y, T *U, int s, cudaStream_t stream);
-template <typename T>
-void launch_solve_bwd(const ForestDev &f, const TileItem *items, int nitems, int tm,
-                      const T *panel, const T *Y, T *X, int s, cudaStream_t stream);
-// rows per tile used by the solve kernels for s columns
-int solve_tile_rows(int s);
+int launch_sweep(const ForestDev &f, const SweepPlan &p, int32_t epoch, int32_t claim_base,
+                 const T *panel, const T *B, T *Y, T *U, T *X, int s, DevStatus *st,
+                 cudaStream_t stream);
+// rows of a forward tile in vector mode for elements of elem_bytes
+int sweep_vector_rows(int elem_bytes);
+constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
+constexpr int kSweepVectorCols = 8;   // columns per backward tile in vector mode (a warp each)
+constexpr int kSmallM = 96, kSmallW = 32, kGroup = 8;
 
 // ---- BLAS-like kernels (k_blas.cu) ------------------------------------------------
 // Y = alpha * A X + beta * C  (C may be nullptr; Y may alias C)
@@ -89,6 +100,11 @@ void launch_block_update(const T *A, const double *M, int64_t n, int s1, int s2,
 // X[i*s + j] *= scale[j]
 void launch_scale_cols(double *X, int64_t n, int s, const double *scale, bool take_sqrt,
                        cudaStream_t stream);
+// t = Z^T r and z = beta z + Z t for Z (n x k, FP64 row-major); work >= gram_work_size(n,k,1)
+void launch_gemv_t(const double *Z, int64_t n, int k, const double *r, double *t, double *work,
+                   cudaStream_t stream);
+void launch_gemv_n(const double *Z, int64_t n, int k, const double *t, double beta, double *z,
+                   cudaStream_t stream);
 // colsq[j] = sum_i X[i*s+j]^2 (FP64), deterministic; work >= gram_work_size(n, s, 1)
 template <typename T>
 void launch_col_sumsq(const T *X, int64_t n, int s, double *colsq, double *work,
@@ -108,11 +124,13 @@ void launch_pcg_scalars(const double *rz_new, const double *rz_old, const double
 // Cholesky-QR with column drop: C (s x s) = W^T W; writes Rinv (s x s, zero outside the kept
 // columns) such that W Rinv has orthonormal kept columns, mask[j] = kept, *nkept.
 void launch_chol_drop(const double *C, int s, double drop_tol, double *Rinv, int32_t *mask,
-                      int32_t *nkept, cudaStream_t stream);
-// alpha (s x r) = PtQ^{-1} Rhs on the kept rows/cols (mask), zero elsewhere; sign scales.
-// Factor of PtQ kept in Lwork (s x s). Non-SPD PtQ -> DEV_BREAKDOWN.
+                      int32_t *nkept, double *gwork, cudaStream_t stream);
+// doubles of scratch for launch_chol_drop / launch_spd_solve_masked
+size_t core_work_size(int s);
+// out (s x r) = sign * PtQ^{-1} Rhs on the kept rows/cols (mask), zero elsewhere (r <= s).
+// Non-SPD PtQ -> DEV_BREAKDOWN.
 void launch_spd_solve_masked(const double *PtQ, const double *Rhs, int s, int r,
-                             const int32_t *mask, double sign, double *out, double *Lwork,
+                             const int32_t *mask, double sign, double *out, double *gwork,
                              DevStatus *st, cudaStream_t stream);
 // max_j sqrt(colsq[j]) / bnorm[j] -> *ratio
 void launch_max_ratio(const double *colsq, const double *bnorm, int s, double *ratio,

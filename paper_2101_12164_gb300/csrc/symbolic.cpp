@@ -308,16 +308,25 @@ void local_symbolic(const BlockPattern &P, LocalSym &L) {
   }
 }
 
+// Allowed fraction of explicit zeros in a merged supernode by merged width (<=16, <=32,
+// <=64, larger), per relaxation level.
+const double kRelax[4][4] = {{0, 0, 0, 0},
+                             {0.5, 0.15, 0.1, 0.05},
+                             {0.8, 0.5, 0.25, 0.05},
+                             {0.9, 0.7, 0.4, 0.1}};
+
 // Whether merging (child C immediately before J) is acceptable.
 bool accept_merge(int relax, int64_t wc, int64_t wj, int64_t mj, int64_t nz) {
   if (relax <= 0) return false;
-  int64_t w = wc + wj, m = wc + mj;
-  int64_t ent = w * m - w * (w - 1) / 2;
-  double zf = double(ent - nz) / double(ent);
-  if (w <= 4 * relax) return true;
-  if (w <= 16 * relax) return zf < 0.5;
-  if (w <= 48 * relax) return zf < 0.15;
-  return zf < 0.05;
+  const int64_t w = wc + wj, m = wc + mj;
+  const int64_t ent = w * m - w * (w - 1) / 2;
+  const double zf = double(ent - nz) / double(ent);
+  const double *tab = kRelax[relax > 3 ? 3 : relax];
+  if (w <= 8) return true;
+  if (w <= 16) return zf < tab[0];
+  if (w <= 32) return zf < tab[1];
+  if (w <= 64) return zf < tab[2];
+  return zf < tab[3];
 }
 
 }  // namespace
@@ -461,7 +470,7 @@ void analyze_forest(const std::vector<BlockPattern> &blocks, int relax, Forest &
       f.sn_panel.push_back(panel);
       f.sn_front.push_back(front);
       f.sn_upd.push_back(upd);
-      panel += (int64_t)m * w;
+      panel += (int64_t)panel_ld(m) * w;
       front += (int64_t)m * m;
       upd += m - w;
       for (int32_t r = w; r < m; ++r) f.relmap.push_back(-1);

@@ -13,6 +13,10 @@
 
 namespace nsp {
 
+// Leading dimension of a supernode panel with m rows: rounded up to 4 elements so that every
+// panel column starts on a 16-byte boundary (vector loads in the solve sweeps).
+inline int32_t panel_ld(int32_t m) { return (m + 3) & ~3; }
+
 // Lower triangle (diagonal included) of one block by columns, in the block's initial order.
 struct BlockPattern {
   int32_t n = 0;
@@ -31,7 +35,7 @@ struct Forest {
   std::vector<int32_t> sn_first, sn_w, sn_m, sn_parent, sn_block, sn_level;
   std::vector<int64_t> sn_rowptr;        // nsn + 1, into rows
   std::vector<int32_t> rows;             // internal indices (forest numbering)
-  std::vector<int64_t> sn_panel;         // offset of the m x w panel (column-major)
+  std::vector<int64_t> sn_panel;         // offset of the panel_ld(m) x w panel (column-major)
   std::vector<int64_t> sn_front;         // offset of the m x m front (column-major)
   std::vector<int64_t> sn_upd;           // first update row (the m - w rows below the panel)
   std::vector<int32_t> relmap;           // update row -> position in the parent's front
