@@ -162,6 +162,27 @@ nsp_status nsp_solve(const nsp_handle *h, const double *b, double *x, double rto
  * stream before reading Y. Only the first call with a new width s allocates. */
 nsp_status nsp_schur_apply(const nsp_handle *h, const void *X, void *Y, int32_t s);
 
+/* Same result as nsp_schur_apply, for callers that cannot allocate device memory (for
+ * example code that runs while a CUDA stream is being captured into a graph, or under an
+ * allocator that forbids cudaMalloc): this call allocates nothing. Its temporaries live in
+ * one fixed device array of NSP_NOALLOC_SCRATCH_BYTES (16 MiB) that the library defines and
+ * that every GPU using the library keeps until the process exits. The paper has no
+ * counterpart; it is an interface convenience.
+ *  - Limit: (2 n_Gamma + 3 n_interior + update rows of the interior factor) * s * element
+ *    size, each part rounded up to 256 bytes, must fit in the array; otherwise
+ *    NSP_ERR_INVALID_ARG and nothing runs.
+ *  - The sweep plan for the width class (s = 1, or s > 1) must exist: s > 1 is ready after
+ *    nsp_build; s = 1 after any nsp_solve, nsp_apply or s = 1 nsp_schur_apply on the handle
+ *    (NSP_ERR_INVALID_ARG otherwise).
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - All calls share the array, so calls whose work overlaps on the GPU (other streams or
+ *    other handles) race; the array keeps the last call's contents (every temporary is fully
+ *    written before it is read, nothing needs clearing).
+ * Asynchronous on the handle's stream like nsp_schur_apply. */
+#define NSP_NOALLOC_SCRATCH_BYTES (16u << 20)
+nsp_status nsp_schur_apply_noalloc(const nsp_handle *h, const void *X, void *Y, int32_t s);
+
 /* X = A_I^{-1} B (interior order, n_interior x s) or X = A_G^{-1} B (Gamma order,
  * n_Gamma x s) with the device Cholesky factors, in the handle's precision (see
  * nsp_schur_apply). which: 0 = interior blocks, 1 = A_G. Device pointers. Asynchronous on

@@ -24,7 +24,7 @@ STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_
 EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_solve",
            "nsp_schur_apply", "nsp_factor_solve", "nsp_get_basis", "nsp_get_intermediate",
            "nsp_get_factor", "nsp_get_info", "nsp_destroy", "nsp_status_string", "nsp_gaussian",
-           "nsp_analyze", "nsp_kernel_launches"]
+           "nsp_analyze", "nsp_kernel_launches", "nsp_schur_apply_noalloc"]
 
 
 class NspError(RuntimeError):
@@ -95,6 +95,7 @@ def lib():
             "nsp_analyze": (C.c_int, [C.POINTER(nsp_csr), C.POINTER(nsp_partition),
                                       C.POINTER(nsp_info)]),
             "nsp_kernel_launches": (C.c_int64, []),
+            "nsp_schur_apply_noalloc": (C.c_int, [P, P, P, C.c_int32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -251,6 +252,13 @@ class Handle:
     def schur_apply(self, X, Y):
         s = 1 if X.dim() == 1 else X.shape[1]
         _check(lib().nsp_schur_apply(self._handle(), _ptr(X), _ptr(Y), int(s)), "nsp_schur_apply")
+        return Y
+
+    def schur_apply_noalloc(self, X, Y):
+        """nsp_schur_apply_noalloc: same result as schur_apply, no device allocation."""
+        s = 1 if X.dim() == 1 else X.shape[1]
+        _check(lib().nsp_schur_apply_noalloc(self._handle(), _ptr(X), _ptr(Y), int(s)),
+               "nsp_schur_apply_noalloc")
         return Y
 
     def factor_solve(self, which, B, X):

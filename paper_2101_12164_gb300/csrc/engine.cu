@@ -19,6 +19,7 @@
 #include <functional>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -403,6 +404,8 @@ struct EngineBase {
   virtual void apply_m2(const double *r, double *z) = 0;
   virtual void solve(const double *b, double *x, double rtol, int maxit, int form) = 0;
   virtual void schur_apply_user(const void *X, void *Y, int s) = 0;
+  virtual size_t schur_noalloc_bytes(int s) const = 0;
+  virtual void schur_apply_noalloc(const void *X, void *Y, int s, unsigned char *scratch) = 0;
   virtual void factor_solve_user(int which, const void *B, void *X, int s) = 0;
   virtual void get_basis(double *Z, double *Sigma, int32_t *rank) = 0;
   virtual void get_intermediate(int which, double *out) = 0;
@@ -585,6 +588,31 @@ struct Engine : EngineBase {
     } else {
       launch_spmm<T>(A_GI.dT(), Xw.p, Yo, sc, T(1), nullptr, T(0), st);
     }
+  }
+
+  // ---- S_Gamma X with caller-order X, Y and every temporary carved from `scratch`
+  // (no allocation). The sweep plan of the needed kind must already exist.
+  static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+  size_t schur_noalloc_bytes(int sc) const override {
+    const size_t e = sizeof(T) * (size_t)sc;
+    return 2 * align256(an.nG * e) + 3 * align256(an.nI * e) +
+           align256(std::max<int64_t>(FI.h.upd_rows, 1) * e);
+  }
+  void schur_apply_noalloc(const void *X, void *Yv, int sc, unsigned char *scratch) override {
+    require(FI.plans[sc == 1 ? 1 : 0] != nullptr, NSP_ERR_INVALID_ARG,
+            "no sweep plan for this width yet: run nsp_schur_apply once with the same s");
+    const size_t e = sizeof(T) * (size_t)sc;
+    unsigned char *q = scratch;
+    auto take = [&](size_t bytes) { T *p = reinterpret_cast<T *>(q); q += align256(bytes); return p; };
+    T *xi = take(an.nG * e), *yi = take(an.nG * e);
+    T *b = take(an.nI * e), *yw = take(an.nI * e), *xw = take(an.nI * e);
+    T *uw = take(std::max<int64_t>(FI.h.upd_rows, 1) * e);
+    launch_gather_rows<T, T>(i2u_G.p, an.nG, (const T *)X, xi, sc, st);
+    launch_spmm<T>(A_IG.dT(), xi, b, sc, T(1), nullptr, T(0), st);
+    solve_forest(FI, panelI.p, b, yw, uw, xw, sc);
+    launch_spmm<T>(A_G.dT(), xi, yi, sc, T(1), nullptr, T(0), st);
+    launch_spmm<T>(A_GI.dT(), xw, yi, sc, T(-1), yi, T(1), st);
+    launch_scatter_rows<T, T>(i2u_G.p, an.nG, yi, (T *)Yv, sc, st);
   }
 
   void gram(const T *X, const T *Yv, int s1, int s2, double *C) {
@@ -1163,6 +1191,44 @@ nsp_status nsp_destroy(nsp_handle *h) {
 }
 
 int64_t nsp_kernel_launches(void) { return nsp::g_launches.load(); }
+
+}  // extern "C"
+
+// Scratch of nsp_schur_apply_noalloc: a fixed device array that every GPU using this library
+// holds until the process exits. Host code must not use the symbol as an address: the device
+// address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_schur_scratch[NSP_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[128] = {nullptr};
+
+unsigned char *scratch_for_current_device() {
+  int dev = 0;
+  NSP_CUDA(cudaGetDevice(&dev));
+  nsp::require(dev >= 0 && dev < 128, NSP_ERR_UNSUPPORTED, "device ordinal beyond 127");
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    NSP_CUDA(cudaGetSymbolAddress(&p, g_schur_scratch));
+    g_scratch_ptr[dev] = p;
+  }
+  return static_cast<unsigned char *>(g_scratch_ptr[dev]);
+}
+}  // namespace
+
+extern "C" {
+
+nsp_status nsp_schur_apply_noalloc(const nsp_handle *h, const void *X, void *Y, int32_t s) {
+  if (!h || !h->eng || !X || !Y || s < 1 || s > 256) return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    nsp::require(h->eng->schur_noalloc_bytes(s) <= (size_t)NSP_NOALLOC_SCRATCH_BYTES,
+                 NSP_ERR_INVALID_ARG,
+                 "problem too large for the fixed scratch of nsp_schur_apply_noalloc");
+    unsigned char *scratch = scratch_for_current_device();
+    h->eng->schur_apply_noalloc(X, Y, s, scratch);
+  });
+}
 
 nsp_status nsp_gaussian(uint64_t seed, int64_t count, double *out, void *stream) {
   if (!out || count < 0) return NSP_ERR_INVALID_ARG;
