@@ -137,6 +137,34 @@ void nsp_default_params(nsp_params *prm);
 nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params *prm,
                      nsp_handle **out);
 
+/* Many independent SPD systems in one handle (the paper builds M2 for one matrix; a batch
+ * applies Algorithm 2 to each matrix on its own): A[0..count), P[0..count) host CSRs and
+ * partitions (perm given for all or none), one parameter set for all (k + p <= 96, and
+ * k + p <= n_Gamma of every matrix). The matrices are concatenated block-diagonally, so
+ * one factorization launch per tree level and one persistent sweep launch per triangular
+ * solve serve all of them, while every quantity of Algorithm 2 (s x s Grams, Cholesky-QR,
+ * drop decisions, stopping test, Nyström core) and of the outer PCG (scalars, stopping
+ * test) is computed per matrix; a matrix that has converged stops changing.
+ * On a batched handle: vectors are the matrices' vectors stacked in matrix order (Gamma
+ * vectors likewise: matrix 0's Gamma unknowns in its order, then matrix 1's, ...);
+ * prm->sketch, if given, is the matrices' sketches stacked that way; nsp_rebuild takes the
+ * concatenated value arrays; nsp_apply, nsp_schur_apply and nsp_factor_solve act on all
+ * matrices at once; nsp_get_basis returns all k columns (rank = k) and count x k values of
+ * Sigma (per matrix, zero beyond its rank, see nsp_solve_batched's infos for the ranks);
+ * nsp_solve is refused (INVALID_ARG), use nsp_solve_batched. Errors as nsp_build. */
+nsp_status nsp_build_batched(int32_t count, const nsp_csr *A, const nsp_partition *P,
+                             const nsp_params *prm, nsp_handle **out);
+
+/* Solve every system of a batched handle: b and x are the matrices' vectors stacked in
+ * matrix order (sum of n doubles; host or device pointers, detected). Each matrix runs its
+ * own outer PCG (full-space form with the block preconditioner, see nsp_outer_form) until
+ * its own ||r|| / ||r0|| <= rtol; one launch of every kernel serves all matrices still
+ * iterating. infos (may be NULL) receives count nsp_info records (it_inner, inner_residual,
+ * rank, it_pcg, pcg_residual, final_residual of that matrix). NOT_CONVERGED if some matrix
+ * reached maxit (x holds every matrix's last iterate). */
+nsp_status nsp_solve_batched(const nsp_handle *h, const double *b, double *x, double rtol,
+                             int32_t maxit, nsp_info *infos);
+
 /* Repeat the numeric part of nsp_build (factorization + Algorithm 2) for new values of A
  * with the same pattern (val has nnz entries in the CSR order given to nsp_build; device
  * memory if on_device). prm may change k, p, tolerances, seed, sketch (not precision). */

@@ -24,7 +24,8 @@ STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_
 EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_solve",
            "nsp_schur_apply", "nsp_factor_solve", "nsp_get_basis", "nsp_get_intermediate",
            "nsp_get_factor", "nsp_get_info", "nsp_destroy", "nsp_status_string", "nsp_gaussian",
-           "nsp_analyze", "nsp_kernel_launches", "nsp_schur_apply_noalloc"]
+           "nsp_analyze", "nsp_kernel_launches", "nsp_schur_apply_noalloc", "nsp_build_batched",
+           "nsp_solve_batched"]
 
 
 class NspError(RuntimeError):
@@ -96,6 +97,9 @@ def lib():
                                       C.POINTER(nsp_info)]),
             "nsp_kernel_launches": (C.c_int64, []),
             "nsp_schur_apply_noalloc": (C.c_int, [P, P, P, C.c_int32]),
+            "nsp_build_batched": (C.c_int, [C.c_int32, P, P, C.POINTER(nsp_params),
+                                            C.POINTER(P)]),
+            "nsp_solve_batched": (C.c_int, [P, P, P, C.c_double, C.c_int32, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -190,6 +194,23 @@ def nsp_build(A, part, nblocks, perm=None, **kw):
     return Handle(h, prm, keep)
 
 
+def nsp_build_batched(mats, **kw):
+    """Build one handle for a batch of matrices: mats = [(A, part, nblocks), ...]."""
+    keep = []
+    csrs = (nsp_csr * len(mats))()
+    parts = (nsp_partition * len(mats))()
+    for i, (A, part, nb) in enumerate(mats):
+        csrs[i] = _csr_struct(A, keep)
+        parts[i] = _part_struct(part, nb, None, keep)
+    prm = make_params(keep=keep, **kw)
+    h = C.c_void_p()
+    _check(lib().nsp_build_batched(len(mats), csrs, parts, C.byref(prm), C.byref(h)),
+           "nsp_build_batched")
+    hd = Handle(h, prm, keep)
+    hd.batch = len(mats)
+    return hd
+
+
 def nsp_analyze(A, part, nblocks, perm=None):
     """Host-only validation and symbolic analysis; returns nsp_info as a dict."""
     keep = []
@@ -217,6 +238,7 @@ class Handle:
         self.prm = prm
         self._keep = keep
         self.dtype_name = "float64" if prm.precision == NSP_FP64 else "float32"
+        self.batch = 0
 
     def _handle(self):
         if self._h is None or not self._h.value:
@@ -249,6 +271,14 @@ class Handle:
             _check(st, "nsp_solve")
         return inf.as_dict()
 
+    def solve_batched(self, b, x, rtol=1e-8, maxit=500, allow_not_converged=False):
+        infos = (nsp_info * self.batch)()
+        st = lib().nsp_solve_batched(self._handle(), _ptr(b), _ptr(x), float(rtol), int(maxit),
+                                     infos)
+        if not (st == 0 or (allow_not_converged and st == 5)):
+            _check(st, "nsp_solve_batched")
+        return [infos[i].as_dict() for i in range(self.batch)]
+
     def schur_apply(self, X, Y):
         s = 1 if X.dim() == 1 else X.shape[1]
         _check(lib().nsp_schur_apply(self._handle(), _ptr(X), _ptr(Y), int(s)), "nsp_schur_apply")
@@ -270,6 +300,14 @@ class Handle:
     def get_basis(self):
         inf = self.info()
         nG, k = inf["n_gamma"], self.prm.k
+        if self.batch:
+            # batched handle: all k columns; Sigma per matrix (batch x k)
+            Z = np.zeros((nG, k))
+            S = np.zeros((self.batch, k))
+            r = C.c_int32()
+            _check(lib().nsp_get_basis(self._handle(), _ptr(Z), _ptr(S), C.byref(r)),
+                   "nsp_get_basis")
+            return Z, S
         Z = np.zeros((nG, k))
         S = np.zeros(k)
         r = C.c_int32()

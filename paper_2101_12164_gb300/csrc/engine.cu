@@ -404,6 +404,10 @@ struct EngineBase {
   virtual void apply_m2(const double *r, double *z) = 0;
   virtual void solve(const double *b, double *x, double rtol, int maxit, int form) = 0;
   virtual void schur_apply_user(const void *X, void *Y, int s) = 0;
+  virtual void setup_batch(const std::vector<int64_t> &mat_off) = 0;
+  virtual void construct_batched(const nsp_params &prm) = 0;
+  virtual void solve_batched(const double *b, double *x, double rtol, int maxit) = 0;
+  std::vector<nsp_info> binfo;     // per matrix of a batched handle
   virtual size_t schur_noalloc_bytes(int s) const = 0;
   virtual void schur_apply_noalloc(const void *X, void *Y, int s, unsigned char *scratch) = 0;
   virtual void factor_solve_user(int which, const void *B, void *X, int s) = 0;
@@ -738,6 +742,10 @@ struct Engine : EngineBase {
   // ---- M2 r = A_G^{-1} r + Z Sigma Z^T r (internal order, FP64 in/out)
   DBuf<double> zt_vec;
   void m2_apply_internal(const double *r, double *z) {
+    if (nseg > 1) {
+      m2_batched(r, z);
+      return;
+    }
     if (std::is_same<T, double>::value) {
       solve_G(reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), 1);
     } else {
@@ -900,6 +908,297 @@ struct Engine : EngineBase {
   }
   DBuf<double> pfull_t;
 
+  // ==== batches of independent matrices (one block-diagonal problem, per-matrix algebra)
+  struct Chunks {
+    SegChunks d;
+    DBuf<int64_t> row0, row1;
+    DBuf<int32_t> seg, seg_first;
+    void build(const std::vector<std::vector<std::pair<int64_t, int64_t>>> &ranges, int64_t len,
+               cudaStream_t st) {
+      std::vector<int64_t> a, b;
+      std::vector<int32_t> sg, first(ranges.size() + 1, 0);
+      for (size_t g = 0; g < ranges.size(); ++g) {
+        first[g] = (int32_t)a.size();
+        for (auto rg : ranges[g])
+          for (int64_t r = rg.first; r < rg.second; r += len) {
+            a.push_back(r);
+            b.push_back(std::min(rg.second, r + len));
+            sg.push_back((int32_t)g);
+          }
+      }
+      first[ranges.size()] = (int32_t)a.size();
+      row0.upload(a, st);
+      row1.upload(b, st);
+      seg.upload(sg, st);
+      seg_first.upload(first, st);
+      d = SegChunks{(int)a.size(), (int)ranges.size(), row0.p, row1.p, seg.p, seg_first.p};
+    }
+  };
+  int nseg = 1;
+  std::vector<int64_t> bmat_off;          // caller-order offsets of the matrices (nseg + 1)
+  Chunks chG, chF, chU;                   // Gamma rows, internal full rows, caller rows
+  DBuf<double> bwork, bscal, bK, bC, bSig;
+  DBuf<int32_t> bactive;
+  std::vector<int32_t> h_active;
+  std::vector<int64_t> seg_nG;            // interface size of every matrix
+
+  void setup_batch(const std::vector<int64_t> &mat_off) override {
+    nseg = (int)mat_off.size() - 1;
+    bmat_off = mat_off;
+    auto mat_of = [&](int64_t g) {
+      return (int)(std::upper_bound(mat_off.begin(), mat_off.end(), g) - mat_off.begin()) - 1;
+    };
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> rG(nseg), rF(nseg), rU(nseg);
+    auto ranges = [&](const std::vector<int64_t> &i2g, int64_t base,
+                      std::vector<std::vector<std::pair<int64_t, int64_t>>> &out) {
+      // maximal runs of one matrix in the internal order (a matrix may own several runs)
+      int64_t t = 0, n = (int64_t)i2g.size();
+      while (t < n) {
+        const int g = mat_of(i2g[t]);
+        int64_t e = t;
+        while (e < n && mat_of(i2g[e]) == g) ++e;
+        out[g].push_back({base + t, base + e});
+        t = e;
+      }
+    };
+    ranges(an.i2g_G, 0, rG);
+    ranges(an.i2g_I, 0, rF);
+    ranges(an.i2g_G, an.nI, rF);
+    for (int g = 0; g < nseg; ++g) rU[g].push_back({mat_off[g], mat_off[g + 1]});
+    seg_nG.assign(nseg, 0);
+    for (int g = 0; g < nseg; ++g)
+      for (auto rg : rG[g]) seg_nG[g] += rg.second - rg.first;
+    chG.build(rG, 1024, st);
+    chF.build(rF, 2048, st);
+    chU.build(rU, 2048, st);
+    binfo.assign(nseg, info);
+  }
+
+  void construct_batched(const nsp_params &prm) override {
+    auto t0 = Clock::now();
+    require(prm.k > 0 && prm.p >= 0, NSP_ERR_INVALID_ARG, "k > 0 and p >= 0 required");
+    s = prm.k + prm.p;
+    k = prm.k;
+    require(s <= 96, NSP_ERR_UNSUPPORTED, "batched handles support k + p <= 96");
+    for (int64_t ng : seg_nG)
+      require(s <= ng, NSP_ERR_INVALID_ARG, "k + p exceeds the interface size of a matrix");
+    require(prm.inner_form == NSP_FORM_SGAMMA, NSP_ERR_UNSUPPORTED, "inner form");
+    keep = prm.keep_intermediates != 0;
+    ensure_ws(s);
+    const size_t ns = (size_t)an.nG * s, ss = (size_t)s * s;
+    for (DBuf<T> *b : {&G, &Fh, &E, &R, &P, &Q, &Z, &W, &Y}) b->ensure(ns);
+    const int nch = std::max({chG.d.nchunk, chF.d.nchunk, chU.d.nchunk});
+    bwork.ensure((size_t)nch * std::max<size_t>(ss, (size_t)s * k) + 64);
+    for (DBuf<double> *b : {&Cg, &alpha, &beta, &Rinv, &bK, &bC}) b->ensure(nseg * ss);
+    Lwork.ensure(nseg * core_work_size(s));
+    nys_work.ensure(nseg * nystrom_work_size(s));
+    colsq.ensure((size_t)nseg * s);
+    bnorm.ensure((size_t)nseg * s);
+    ratio.ensure(nseg);
+    Mix.ensure((size_t)nseg * s * k);
+    bSig.ensure((size_t)nseg * k);
+    mask.ensure((size_t)nseg * s);
+    nkept.ensure(nseg);
+    drank.ensure(nseg);
+    bactive.ensure(nseg);
+    bscal.ensure(16 * (size_t)nseg);
+    NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
+    g64.ensure(ns);
+    if (prm.sketch) {
+      NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+      launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
+    }
+    launch_gather_rows<double, T>(i2u_G.p, an.nG, g64.p, G.p, s, st);
+    // block PCG for every matrix at once (per-matrix scalars, one sweep per operator)
+    schur_apply(G.p, Fh.p, s, false);
+    launch_seg_colsq<T>(Fh.p, s, chG.d, colsq.p, bwork.p, st);
+    launch_sqrt_vec(colsq.p, nseg * s, bnorm.p, st);
+    NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
+    NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    solve_G(R.p, W.p, s);
+    h_active.assign(nseg, 1);
+    std::vector<int32_t> its(nseg, 0), act_cols(nseg, s);
+    std::vector<double> rat(nseg, 1.0);
+    NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    std::vector<double> hr(nseg);
+    std::vector<int32_t> hk(nseg);
+    for (int it = 0; it < prm.max_inner_it; ++it) {
+      schur_apply(W.p, Z.p, s, true);
+      launch_seg_gram<T, T>(W.p, Z.p, s, s, chG.d, Cg.p, bwork.p, st);
+      launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st, nseg);
+      launch_seg_block_update<T>(W.p, Rinv.p, s, s, T(1), nullptr, T(0), P.p, chG.d, bactive.p, st);
+      launch_seg_block_update<T>(Z.p, Rinv.p, s, s, T(1), nullptr, T(0), Q.p, chG.d, bactive.p, st);
+      launch_seg_gram<T, T>(P.p, R.p, s, s, chG.d, alpha.p, bwork.p, st);
+      launch_seg_block_update<T>(P.p, alpha.p, s, s, T(1), E.p, T(1), E.p, chG.d, bactive.p, st);
+      launch_seg_block_update<T>(Q.p, alpha.p, s, s, T(-1), R.p, T(1), R.p, chG.d, bactive.p, st);
+      launch_seg_colsq<T>(R.p, s, chG.d, colsq.p, bwork.p, st);
+      launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st, nseg);
+      NSP_CUDA(cudaMemcpyAsync(hr.data(), ratio.p, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+      NSP_CUDA(cudaMemcpyAsync(hk.data(), nkept.p, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      sync();
+      int any = 0;
+      for (int g = 0; g < nseg; ++g) {
+        if (!h_active[g]) continue;
+        if (hk[g] == 0) { h_active[g] = 0; act_cols[g] = 0; continue; }
+        its[g] += 1;
+        rat[g] = hr[g];
+        act_cols[g] = hk[g];
+        if (!(hr[g] > prm.eps_inner)) h_active[g] = 0;
+        any |= h_active[g];
+      }
+      if (!any) break;
+      NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      solve_G(R.p, Z.p, s);
+      launch_seg_gram<T, T>(Q.p, Z.p, s, s, chG.d, beta.p, bwork.p, st);
+      launch_seg_block_update<T>(P.p, beta.p, s, s, T(-1), Z.p, T(1), W.p, chG.d, bactive.p, st);
+    }
+    check_status();
+    auto t1 = Clock::now();
+    launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
+    launch_seg_gram<T, double>(Y.p, Y.p, s, s, chG.d, bK.p, bwork.p, st);
+    launch_seg_gram<T, double>(G.p, Y.p, s, s, chG.d, bC.p, bwork.p, st);
+    launch_nystrom_core(bK.p, bC.p, s, k, prm.eps_trunc_rel, 1e-14, Mix.p, bSig.p, drank.p,
+                        nys_work.p, st, nseg);
+    U.ensure((size_t)an.nG * k);
+    Zt.ensure((size_t)an.nG * k);
+    Zs.ensure((size_t)an.nG * k);
+    launch_seg_block_update<T>(Y.p, Mix.p, s, k, T(1), nullptr, T(0), U.p, chG.d, nullptr, st);
+    solve_G(U.p, Zt.p, k);
+    launch_seg_scale_sqrt<T>(Zt.p, k, bSig.p, chG.d, Zs.p, st);
+    std::vector<int32_t> rk(nseg);
+    NSP_CUDA(cudaMemcpyAsync(rk.data(), drank.p, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    sync();
+    const double ms_in = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    rank = 0;
+    for (int g = 0; g < nseg; ++g) {
+      binfo[g] = info;
+      binfo[g].it_inner = its[g];
+      binfo[g].inner_residual = rat[g];
+      binfo[g].inner_active_cols = act_cols[g];
+      binfo[g].rank = rk[g];
+      binfo[g].ms_inner = ms_in;
+      binfo[g].ms_core = ms_since(t1);
+      rank = std::max(rank, rk[g]);
+    }
+    info.ms_inner = ms_in;
+    info.ms_core = ms_since(t1);
+  }
+
+  // M2 of every matrix on the interface part of a full internal vector (FP64)
+  DBuf<double> bt;
+  void m2_batched(const double *rG, double *zG) {
+    if (std::is_same<T, double>::value) {
+      solve_G(reinterpret_cast<const T *>(rG), reinterpret_cast<T *>(zG), 1);
+    } else {
+      sT.ensure(std::max(an.nI, an.nG));
+      sT2.ensure(std::max(an.nI, an.nG));
+      launch_gather_rows<double, T>(nullptr, an.nG, rG, sT.p, 1, st);
+      solve_G(sT.p, sT2.p, 1);
+      launch_gather_rows<T, double>(nullptr, an.nG, sT2.p, zG, 1, st);
+    }
+    bt.ensure((size_t)nseg * k);
+    launch_seg_gram<double, double>(Zs.p, rG, k, 1, chG.d, bt.p, bwork.p, st);
+    launch_seg_block_update<double>(Zs.p, bt.p, k, 1, 1.0, zG, 1.0, zG, chG.d, nullptr, st);
+  }
+
+  void solve_batched(const double *b_user, double *x_user, double rtol, int maxit) override {
+    auto t0 = Clock::now();
+    const int64_t n = an.n, nI = an.nI, nG = an.nG;
+    vb.ensure(n); vx.ensure(n); vt.ensure(n); vu.ensure(n); vf.ensure(n);
+    vr.ensure(n); vz.ensure(n); vp.ensure(n); vq.ensure(n); pfull_t.ensure(n);
+    ensure_ws(1);
+    double *sc = bscal.p;  // per matrix: rz, pq, alpha, beta, rr, rznew, ff, bb (8 x nseg)
+    double *d_rz = sc, *d_pq = sc + nseg, *d_al = sc + 2 * nseg, *d_be = sc + 3 * nseg,
+           *d_rr = sc + 4 * nseg, *d_rzn = sc + 5 * nseg, *d_ff = sc + 6 * nseg, *d_bb = sc + 7 * nseg;
+    double *bI = vb.p, *bG = vb.p + nI;
+    launch_gather_rows<double, double>(i2g_I.p, nI, b_user, bI, 1, st);
+    launch_gather_rows<double, double>(i2g_G.p, nG, b_user, bG, 1, st);
+    auto Aop = [&](const double *v, double *o) {
+      launch_spmm<double>(A_I.d64(), v, o, 1, 1.0, nullptr, 0.0, st);
+      launch_spmm<double>(A_IG.d64(), v + nI, o, 1, 1.0, o, 1.0, st);
+      launch_spmm<double>(A_GI.d64(), v, o + nI, 1, 1.0, nullptr, 0.0, st);
+      launch_spmm<double>(A_G.d64(), v + nI, o + nI, 1, 1.0, o + nI, 1.0, st);
+    };
+    auto Mop = [&](const double *r, double *z) {
+      double *t = pfull_t.p;
+      solve_I64(r, t);
+      launch_spmm<double>(A_GI.d64(), t, t + nI, 1, -1.0, r + nI, 1.0, st);
+      m2_batched(t + nI, z + nI);
+      launch_spmm<double>(A_IG.d64(), z + nI, t, 1, -1.0, r, 1.0, st);
+      solve_I64(t, z);
+    };
+    double *x0 = vu.p;
+    solve_I64(bI, x0);
+    NSP_CUDA(cudaMemsetAsync(x0 + nI, 0, nG * sizeof(double), st));
+    Aop(x0, vf.p);
+    launch_axpby(n, nullptr, 1.0, vb.p, -1.0, vf.p, st);  // r0 = b - A x0
+    NSP_CUDA(cudaMemsetAsync(vx.p, 0, n * sizeof(double), st));
+    NSP_CUDA(cudaMemcpyAsync(vr.p, vf.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_seg_dot(vf.p, vf.p, chF.d, d_ff, bwork.p, st);
+    std::vector<double> fn(nseg), hr(nseg);
+    NSP_CUDA(cudaMemcpyAsync(fn.data(), d_ff, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    for (auto &v : fn) v = std::sqrt(v);
+    h_active.assign(nseg, 1);
+    std::vector<int32_t> its(nseg, 0);
+    std::vector<double> rel(nseg, 1.0);
+    for (int g = 0; g < nseg; ++g)
+      if (fn[g] == 0.0) { h_active[g] = 0; rel[g] = 0.0; }
+    NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    Mop(vr.p, vz.p);
+    NSP_CUDA(cudaMemcpyAsync(vp.p, vz.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_seg_dot(vr.p, vz.p, chF.d, d_rz, bwork.p, st);
+    for (int it = 0; it < maxit; ++it) {
+      Aop(vp.p, vq.p);
+      launch_seg_dot(vp.p, vq.p, chF.d, d_pq, bwork.p, st);
+      launch_seg_ratio(d_rz, d_pq, bactive.p, nseg, d_al, st);
+      launch_seg_axpby(chF.d, d_al, 1.0, vp.p, 1.0, vx.p, st);
+      launch_seg_axpby(chF.d, d_al, -1.0, vq.p, 1.0, vr.p, st);
+      launch_seg_dot(vr.p, vr.p, chF.d, d_rr, bwork.p, st);
+      NSP_CUDA(cudaMemcpyAsync(hr.data(), d_rr, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+      sync();
+      int any = 0;
+      for (int g = 0; g < nseg; ++g) {
+        if (!h_active[g]) continue;
+        its[g] += 1;
+        rel[g] = std::sqrt(std::max(hr[g], 0.0)) / fn[g];
+        if (!(rel[g] > rtol) || its[g] >= maxit) h_active[g] = 0;
+        any |= h_active[g];
+      }
+      if (!any) break;
+      NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      Mop(vr.p, vz.p);
+      launch_seg_dot(vr.p, vz.p, chF.d, d_rzn, bwork.p, st);
+      launch_seg_ratio(d_rzn, d_rz, bactive.p, nseg, d_be, st);
+      launch_seg_axpby(chF.d, d_be, 1.0, vp.p, 0.0, vp.p, st);  // p = beta p
+      launch_seg_axpby(chF.d, nullptr, 1.0, vz.p, 1.0, vp.p, st);  // p += z
+      NSP_CUDA(cudaMemcpyAsync(d_rz, d_rzn, nseg * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    }
+    launch_axpby(n, nullptr, 1.0, x0, 1.0, vx.p, st);
+    launch_scatter_rows<double, double>(i2g_I.p, nI, vx.p, x_user, 1, st);
+    launch_scatter_rows<double, double>(i2g_G.p, nG, vx.p + nI, x_user, 1, st);
+    CsrDev<double> Af{(int32_t)n, (int32_t)n, an.nnz, full_rowptr.p, full_col.p, Aval.p};
+    launch_spmm<double>(Af, x_user, vt.p, 1, -1.0, b_user, 1.0, st);
+    launch_seg_dot(vt.p, vt.p, chU.d, d_rr, bwork.p, st);
+    launch_seg_dot(b_user, b_user, chU.d, d_bb, bwork.p, st);
+    std::vector<double> rr(nseg), bb(nseg);
+    NSP_CUDA(cudaMemcpyAsync(rr.data(), d_rr, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NSP_CUDA(cudaMemcpyAsync(bb.data(), d_bb, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    check_status();
+    bool ok = true;
+    for (int g = 0; g < nseg; ++g) {
+      binfo[g].it_pcg = its[g];
+      binfo[g].pcg_residual = rel[g];
+      binfo[g].final_residual = bb[g] > 0 ? std::sqrt(rr[g] / bb[g]) : 0.0;
+      binfo[g].ms_solve = ms_since(t0);
+      ok &= !(rel[g] > rtol);
+    }
+    info.ms_solve = ms_since(t0);
+    if (!ok) throw Error(NSP_ERR_NOT_CONVERGED, "outer PCG did not converge for every matrix");
+  }
+
   // ---- caller-order wrappers (asynchronous on the handle's stream, no allocation after
   // the first call with a given width)
   DBuf<T> io_a, io_b;
@@ -923,6 +1222,19 @@ struct Engine : EngineBase {
     launch_scatter_rows<T, T>(perm, nn, io_b.p, (T *)X, sc, st);
   }
   void get_basis(double *Zh, double *Sh, int32_t *rk) override {
+    if (nseg > 1) {  // batch: all k columns, Sigma per matrix (nseg x k, zero beyond its rank)
+      if (rk) *rk = k;
+      if (Sh) {
+        NSP_CUDA(cudaMemcpyAsync(Sh, bSig.p, (size_t)nseg * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+      }
+      if (Zh) {
+        DBuf<double> zu((size_t)an.nG * k);
+        launch_scatter_rows<T, double>(i2u_G.p, an.nG, Zt.p, zu.p, k, st);
+        NSP_CUDA(cudaMemcpyAsync(Zh, zu.p, (size_t)an.nG * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+      }
+      sync();
+      return;
+    }
     if (rk) *rk = rank;
     if (rank <= 0) return;
     if (Sh) {
@@ -1001,6 +1313,7 @@ struct Engine : EngineBase {
 struct nsp_handle {
   std::unique_ptr<nsp::EngineBase> eng;
   nsp_params prm{};
+  int32_t batch = 0;   // number of matrices of a batched handle (0: single matrix)
 };
 
 static nsp_status guard(const std::function<void()> &f) {
@@ -1052,6 +1365,15 @@ const char *nsp_status_string(nsp_status s) {
   return "unknown status";
 }
 
+static bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 static nsp::EngineBase *make_engine(const nsp_csr *A, const int64_t *rp, const int32_t *ci,
                                     const nsp_partition *P, const nsp_params *prm) {
   cudaStream_t st = (cudaStream_t)prm->stream;
@@ -1089,6 +1411,102 @@ nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params 
   return s;
 }
 
+nsp_status nsp_build_batched(int32_t count, const nsp_csr *A, const nsp_partition *P,
+                             const nsp_params *prm, nsp_handle **out) {
+  if (!out || count < 1 || !A || !P || !prm) return NSP_ERR_INVALID_ARG;
+  *out = nullptr;
+  auto h = std::make_unique<nsp_handle>();
+  nsp_status s = guard([&] {
+    h->prm = *prm;
+    h->batch = count;
+    // block-diagonal concatenation: unknowns and interior blocks renumbered matrix by matrix
+    int64_t n = 0, nnz = 0;
+    int32_t nb = 0;
+    std::vector<int64_t> off(count + 1, 0);
+    for (int m = 0; m < count; ++m) {
+      nsp::validate_csr(&A[m]);
+      nsp::require(!A[m].on_device, NSP_ERR_INVALID_ARG, "batched build needs host CSR");
+      nsp::require(P[m].part && P[m].nblocks >= 1, NSP_ERR_INVALID_ARG, "partition");
+      off[m + 1] = off[m] + A[m].n;
+      nnz += A[m].rowptr[A[m].n];
+      nb += P[m].nblocks;
+    }
+    n = off[count];
+    std::vector<int64_t> rp(n + 1, 0), perm;
+    std::vector<int32_t> col, part(n);
+    std::vector<double> val;
+    col.reserve(nnz);
+    val.reserve(nnz);
+    bool any_perm = false, all_perm = true;
+    for (int m = 0; m < count; ++m) { any_perm |= P[m].perm != nullptr; all_perm &= P[m].perm != nullptr; }
+    nsp::require(any_perm == all_perm, NSP_ERR_INVALID_ARG, "batched: give perm for all matrices or none");
+    int32_t boff = 0;
+    for (int m = 0; m < count; ++m) {
+      const nsp_csr &a = A[m];
+      for (int64_t i = 0; i < a.n; ++i) {
+        for (int64_t e = a.rowptr[i]; e < a.rowptr[i + 1]; ++e) {
+          col.push_back((int32_t)(a.col[e] + off[m]));
+          val.push_back(a.val[e]);
+        }
+        rp[off[m] + i + 1] = (int64_t)col.size();
+        const int32_t pt = P[m].part[i];
+        part[off[m] + i] = pt < 0 ? -1 : pt + boff;
+      }
+      if (all_perm) {
+        int64_t ni = 0;
+        for (int64_t i = 0; i < a.n; ++i) ni += P[m].part[i] >= 0;
+        for (int64_t q = 0; q < ni; ++q) perm.push_back(P[m].perm[q] + off[m]);
+      }
+      boff += P[m].nblocks;
+    }
+    nsp_csr Asup{n, rp.data(), col.data(), val.data(), 0};
+    nsp_partition Psup{nb, part.data(), all_perm ? perm.data() : nullptr};
+    h->eng.reset(make_engine(&Asup, rp.data(), col.data(), &Psup, prm));
+    h->eng->setup_batch(off);
+    h->eng->factorize(val.data(), false);
+    h->eng->construct_batched(h->prm);
+  });
+  if (s == NSP_OK) *out = h.release();
+  return s;
+}
+
+nsp_status nsp_solve_batched(const nsp_handle *h, const double *b, double *x, double rtol,
+                             int32_t maxit, nsp_info *infos) {
+  if (!h || !h->eng || h->batch < 1 || !b || !x || !(rtol > 0) || maxit < 1)
+    return NSP_ERR_INVALID_ARG;
+  nsp_status s = guard([&] {
+    const int64_t n = h->eng->info.n;
+    cudaStream_t st = h->eng->st;
+    const bool bd = is_device_ptr(b), xd = is_device_ptr(x);
+    const double *bp = b;
+    double *xp = x;
+    if (!bd) {
+      h->eng->stage_b.ensure(n);
+      NSP_CUDA(cudaMemcpyAsync(h->eng->stage_b.p, b, n * sizeof(double), cudaMemcpyHostToDevice, st));
+      bp = h->eng->stage_b.p;
+    }
+    if (!xd) {
+      h->eng->stage_x.ensure(n);
+      xp = h->eng->stage_x.p;
+    }
+    nsp_status inner = NSP_OK;
+    try {
+      h->eng->solve_batched(bp, xp, rtol, maxit);
+    } catch (const nsp::Error &e) {
+      if (e.status != NSP_ERR_NOT_CONVERGED) throw;
+      inner = e.status;
+    }
+    if (!xd) {
+      NSP_CUDA(cudaMemcpyAsync(x, xp, n * sizeof(double), cudaMemcpyDeviceToHost, st));
+      NSP_CUDA(cudaStreamSynchronize(st));
+    }
+    if (inner != NSP_OK) throw nsp::Error(inner, "not converged");
+  });
+  if (infos)
+    for (int m = 0; m < h->batch && m < (int)h->eng->binfo.size(); ++m) infos[m] = h->eng->binfo[m];
+  return s;
+}
+
 nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device, const nsp_params *prm) {
   if (!h || !h->eng || !val) return NSP_ERR_INVALID_ARG;
   return guard([&] {
@@ -1099,7 +1517,10 @@ nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device, cons
       h->prm.stream = stream;
     }
     h->eng->factorize(val, on_device != 0);
-    h->eng->construct(h->prm);
+    if (h->batch > 0)
+      h->eng->construct_batched(h->prm);
+    else
+      h->eng->construct(h->prm);
   });
 }
 
@@ -1108,18 +1529,11 @@ nsp_status nsp_apply(const nsp_handle *h, const double *r, double *z) {
   return guard([&] { h->eng->apply_m2(r, z); });
 }
 
-static bool is_device_ptr(const void *p) {
-  cudaPointerAttributes a{};
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 nsp_status nsp_solve(const nsp_handle *h, const double *b, double *x, double rtol, int32_t maxit,
                      nsp_info *info) {
   if (!h || !h->eng || !b || !x || !(rtol > 0) || maxit < 1) return NSP_ERR_INVALID_ARG;
+  if (h->batch > 0) return NSP_ERR_INVALID_ARG;   // batched handles: nsp_solve_batched
   nsp_status s = guard([&] {
     const int64_t n = h->eng->info.n;
     cudaStream_t st = h->eng->st;

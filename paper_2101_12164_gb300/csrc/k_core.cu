@@ -48,10 +48,9 @@ __device__ void chol_threshold(double *L, const double *diag0, int s, double dro
       const double d = L[j * s + j];
       for (int i = j + 1 + tid; i < s; i += CT) L[i * s + j] /= d;
       __syncthreads();
-      const int rem = s - j - 1;
-      for (int idx = tid; idx < rem * rem; idx += CT) {
-        const int r = j + 1 + idx / rem, c = j + 1 + idx % rem;
-        if (r >= c) L[r * s + c] -= L[r * s + j] * L[c * s + j];
+      for (int r = j + 1 + (tid >> 5); r < s; r += CT / 32) {
+        const double lrj = L[r * s + j];
+        for (int c = j + 1 + (tid & 31); c <= r; c += 32) L[r * s + c] -= lrj * L[c * s + j];
       }
     } else {
       for (int i = j + tid; i < s; i += CT) L[i * s + j] = 0.0;
@@ -144,29 +143,32 @@ __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
         sn[k] = sv;
       }
       __syncthreads();
-      for (int idx = tid; idx < npair * s; idx += CT) {  // A <- A J, V <- V J
-        const int k = idx / s, i = idx % s;
+      const int lane = tid & 31, warp = tid >> 5;
+      for (int k = warp; k < npair; k += CT / 32) {  // A <- A J, V <- V J
         const F sv = sn[k];
         if (sv == F(0)) continue;
         const int p = pp[k], q = qq[k];
         const F c = cs[k];
-        const F ap = A[i * s + p], aq = A[i * s + q];
-        A[i * s + p] = c * ap - sv * aq;
-        A[i * s + q] = sv * ap + c * aq;
-        const F vp = V[i * s + p], vq = V[i * s + q];
-        V[i * s + p] = c * vp - sv * vq;
-        V[i * s + q] = sv * vp + c * vq;
+        for (int i = lane; i < s; i += 32) {
+          const F ap = A[i * s + p], aq = A[i * s + q];
+          A[i * s + p] = c * ap - sv * aq;
+          A[i * s + q] = sv * ap + c * aq;
+          const F vp = V[i * s + p], vq = V[i * s + q];
+          V[i * s + p] = c * vp - sv * vq;
+          V[i * s + q] = sv * vp + c * vq;
+        }
       }
       __syncthreads();
-      for (int idx = tid; idx < npair * s; idx += CT) {  // A <- J^T A
-        const int k = idx / s, j = idx % s;
+      for (int k = warp; k < npair; k += CT / 32) {  // A <- J^T A
         const F sv = sn[k];
         if (sv == F(0)) continue;
         const int p = pp[k], q = qq[k];
         const F c = cs[k];
-        const F ap = A[p * s + j], aq = A[q * s + j];
-        A[p * s + j] = c * ap - sv * aq;
-        A[q * s + j] = sv * ap + c * aq;
+        for (int j = lane; j < s; j += 32) {
+          const F ap = A[p * s + j], aq = A[q * s + j];
+          A[p * s + j] = c * ap - sv * aq;
+          A[q * s + j] = sv * ap + c * aq;
+        }
       }
       __syncthreads();
       if (tid == 0) {
@@ -179,6 +181,17 @@ __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
     if (!any) break;
     __syncthreads();
   }
+}
+
+// C = A B for s x s row-major operands (warps over rows, lanes over columns).
+__device__ void gemm_nn(const double *A, const double *B, double *Cm, int s) {  // C = A B
+  for (int i = threadIdx.x >> 5; i < s; i += CT / 32)
+    for (int j = threadIdx.x & 31; j < s; j += 32) {
+      double v = 0.0;
+      for (int t = 0; t < s; ++t) v += A[i * s + t] * B[t * s + j];
+      Cm[i * s + j] = v;
+    }
+  __syncthreads();
 }
 
 // Modified Gram-Schmidt on the columns of V (s x s row-major, FP64).
@@ -230,24 +243,17 @@ __device__ void eig_sym(double *Bm, int s, double *V, double *W1) {
   for (size_t i = tid; i < ss; i += CT) V[i] = (double)V32[i];
   __syncthreads();
   mgs_columns(V, s);
-  // W1 = C V ; Bm = V^T W1
-  for (size_t idx = tid; idx < ss; idx += CT) {
-    const int i = idx / s, j = idx % s;
-    double v = 0.0;
-    for (int t = 0; t < s; ++t) v += Bm[i * s + t] * V[t * s + j];
-    W1[idx] = v;
-  }
+  // W1 = C V ; Bm = V^T W1 (symmetric: upper triangle computed, mirrored)
+  gemm_nn(Bm, V, W1, s);
+  for (int i = tid >> 5; i < s; i += CT / 32)
+    for (int j = i + (tid & 31); j < s; j += 32) {
+      double v = 0.0;
+      for (int t = 0; t < s; ++t) v += V[t * s + i] * W1[t * s + j];
+      Bm[i * s + j] = v;
+      Bm[j * s + i] = v;
+    }
   __syncthreads();
-  for (size_t idx = tid; idx < ss; idx += CT) {
-    const int i = idx / s, j = idx % s;
-    if (j < i) continue;
-    double v = 0.0;
-    for (int t = 0; t < s; ++t) v += V[t * s + i] * W1[t * s + j];
-    Bm[i * s + j] = v;
-    Bm[j * s + i] = v;
-  }
-  __syncthreads();
-  jacobi<double>(Bm, V, s, 2, 1e-13, 1e-15);
+  jacobi<double>(Bm, V, s, 1, 1e-13, 1e-15);
 }
 
 struct Scratch {
@@ -269,9 +275,17 @@ __global__ void __launch_bounds__(CT) k_chol_drop(const double *C, int s, double
   __shared__ int nk;
   __shared__ double diag0[256];
   __shared__ int32_t msk[256];
-  const Scratch S = scratch(dsm, gwork, s, use_smem);
   const int tid = threadIdx.x;
   const size_t ss = (size_t)s * s;
+  {  // batch: block b works on the b-th s x s problem
+    const size_t b = blockIdx.x;
+    C += b * ss;
+    Rinv += b * ss;
+    mask += b * s;
+    nkept += b;
+    gwork += b * 3 * ss;
+  }
+  const Scratch S = scratch(dsm, gwork, s, use_smem);
   for (size_t i = tid; i < ss; i += CT) {
     S.b0[i] = C[i];
     S.b1[i] = (i / s == i % s) ? 1.0 : 0.0;
@@ -320,6 +334,9 @@ __global__ void __launch_bounds__(CT) k_spd_solve_masked(const double *A, const 
 
 __global__ void k_max_ratio(const double *colsq, const double *bnorm, int s, double *ratio) {
   __shared__ double red[256];
+  colsq += (size_t)blockIdx.x * s;
+  bnorm += (size_t)blockIdx.x * s;
+  ratio += blockIdx.x;
   double m = 0.0;
   for (int j = threadIdx.x; j < s; j += blockDim.x) {
     const double b = bnorm[j] > 0.0 ? bnorm[j] : 1.0;
@@ -348,15 +365,6 @@ __global__ void k_sqrt_vec(const double *in, int s, double *out) {
 //     columns and Sigma beyond kk are zero.
 // Three s x s buffers b0, b1, b2 (shared memory when s <= SMEM_S); gw (global) keeps L^{-1}
 // and R_full between phases (2 s x s) plus the fallback buffers (3 s x s).
-__device__ void gemm_nn(const double *A, const double *B, double *Cm, int s) {  // C = A B
-  for (size_t idx = threadIdx.x; idx < (size_t)s * s; idx += CT) {
-    const int i = idx / s, j = idx % s;
-    double v = 0.0;
-    for (int t = 0; t < s; ++t) v += A[i * s + t] * B[t * s + j];
-    Cm[idx] = v;
-  }
-  __syncthreads();
-}
 
 __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C, int s, int k,
                                                 double eps_rel, double drop_tol, double *Mix,
@@ -368,6 +376,15 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   __shared__ double diag0[256], dvals[256], evals[256];
   const int tid = threadIdx.x;
   const size_t ss = (size_t)s * s;
+  {  // batch: block b works on the b-th problem
+    const size_t b = blockIdx.x;
+    K += b * ss;
+    C += b * ss;
+    Mix += b * (size_t)s * k;
+    Sigma += b * (size_t)k;
+    rank += b;
+    gw += b * (5 * ss + 64);
+  }
   double *gLinv = gw, *gRf = gw + ss;
   const Scratch S = scratch(dsm, gw + 2 * ss, s, use_smem);
 
@@ -417,14 +434,13 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
     S.b0[idx] = keepc[j] ? S.b0[idx] / sqrt(dvals[j]) : 0.0;
   }
   __syncthreads();
-  for (size_t idx = tid; idx < ss; idx += CT) {  // b1 = T = RV RV^T
-    const int i = idx / s, j = idx % s;
-    if (j < i) continue;
-    double v = 0.0;
-    for (int t = 0; t < s; ++t) v += S.b0[i * s + t] * S.b0[j * s + t];
-    S.b1[i * s + j] = v;
-    S.b1[j * s + i] = v;
-  }
+  for (int i = tid >> 5; i < s; i += CT / 32)  // b1 = T = RV RV^T (symmetric)
+    for (int j = i + (tid & 31); j < s; j += 32) {
+      double v = 0.0;
+      for (int t = 0; t < s; ++t) v += S.b0[i * s + t] * S.b0[j * s + t];
+      S.b1[i * s + j] = v;
+      S.b1[j * s + i] = v;
+    }
   __syncthreads();
   for (size_t i = tid; i < ss; i += CT) S.b0[i] = S.b1[i];
   __syncthreads();
@@ -468,13 +484,13 @@ void set_smem(K kernel, size_t bytes) {
 
 }  // namespace
 
-size_t core_work_size(int s) { return 8 * (size_t)s * s + 64; }
+size_t core_work_size(int s) { return 3 * (size_t)s * s + 64; }
 
 void launch_chol_drop(const double *C, int s, double drop_tol, double *Rinv, int32_t *mask,
-                      int32_t *nkept, double *gwork, cudaStream_t stream) {
+                      int32_t *nkept, double *gwork, cudaStream_t stream, int batch) {
   const size_t sm = smem_for(s);
   set_smem(k_chol_drop, sm);
-  k_chol_drop<<<1, CT, sm, stream>>>(C, s, drop_tol, Rinv, mask, nkept, gwork, sm > 0);
+  k_chol_drop<<<batch, CT, sm, stream>>>(C, s, drop_tol, Rinv, mask, nkept, gwork, sm > 0);
   NSP_LAUNCH_CHECK();
 }
 
@@ -488,8 +504,8 @@ void launch_spd_solve_masked(const double *PtQ, const double *Rhs, int s, int r,
 }
 
 void launch_max_ratio(const double *colsq, const double *bnorm, int s, double *ratio,
-                      cudaStream_t stream) {
-  k_max_ratio<<<1, 256, 0, stream>>>(colsq, bnorm, s, ratio);
+                      cudaStream_t stream, int batch) {
+  k_max_ratio<<<batch, 256, 0, stream>>>(colsq, bnorm, s, ratio);
   NSP_LAUNCH_CHECK();
 }
 
@@ -502,10 +518,11 @@ size_t nystrom_work_size(int s) { return 5 * (size_t)s * s + 64; }
 
 void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
                          double drop_tol, double *Mix, double *Sigma, int32_t *rank,
-                         double *work, cudaStream_t stream) {
+                         double *work, cudaStream_t stream, int batch) {
   const size_t sm = smem_for(s);
   set_smem(k_nystrom, sm);
-  k_nystrom<<<1, CT, sm, stream>>>(K, C, s, k, eps_rel, drop_tol, Mix, Sigma, rank, work, sm > 0);
+  k_nystrom<<<batch, CT, sm, stream>>>(K, C, s, k, eps_rel, drop_tol, Mix, Sigma, rank, work,
+                                       sm > 0);
   NSP_LAUNCH_CHECK();
 }
 

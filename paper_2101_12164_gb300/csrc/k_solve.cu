@@ -212,12 +212,20 @@ __device__ void vec_fwd_small(const SweepCtx &c, const T *panel, const T *B, T *
   const T *P = panel + c.f.sn_panel[J];
   const T fk = lane < w ? front_rhs<T>(c, B, U, J, lane, 0, true) : T(0);
   T acc[3] = {T(0), T(0), T(0)};
-  for (int k = 0; k < w; ++k) {
-    const T f = __shfl_sync(0xffffffffu, fk, k);
+  for (int k0 = 0; k0 < w; k0 += 8) {  // 8 x 3 independent loads in flight per lane
+    T v[3][8];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int r = lane + 32 * q;
-      if (r < m) acc[q] += __ldg(&P[r + (size_t)k * ld]) * f;
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int r = lane + 32 * q;
+        v[q][u] = (k0 + u < w && r < m) ? __ldg(&P[r + (size_t)(k0 + u) * ld]) : T(0);
+      }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const T f = __shfl_sync(0xffffffffu, fk, (k0 + u) & 31);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) acc[q] += v[q][u] * f;
     }
   }
 #pragma unroll
@@ -243,8 +251,15 @@ __device__ void vec_bwd_small(const SweepCtx &c, const T *panel, const T *Y, T *
     T gk = T(0);
     if (k < w) gk = __ldcg(&Y[first + k]);
     else if (k < m) gk = -__ldcg(&X[c.f.rows[rp + k]]);
-    for (int col = 0; col < w; ++col)
-      tile[lane * 33 + col] = k < m ? __ldg(&P[k + (size_t)col * ld]) : T(0);
+    for (int c0 = 0; c0 < w; c0 += 8) {  // 8 independent loads in flight per lane
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = (k < m && c0 + u < w) ? __ldg(&P[k + (size_t)(c0 + u) * ld]) : T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (c0 + u < w) tile[lane * 33 + c0 + u] = v[u];
+    }
     __syncwarp();
     const int kn = min(32, m - kb);
     for (int kk = 0; kk < kn; ++kk) {
@@ -307,6 +322,32 @@ __device__ __forceinline__ T gather_sum(const SweepCtx &c, const GatherStage &g,
   return v;
 }
 
+// acc += As[0:kc, rows of this thread]^T Bs[0:kc, columns of this thread]; full chunks run
+// the fully unrolled loop, the last partial chunk a runtime-bounded one.
+template <typename T, int TC, int CM, int RM>
+__device__ __forceinline__ void mac_chunk(const T *As, const T *Bs, int tc, int tr, int kc,
+                                          T (&acc)[RM][CM]) {
+  using C = Cfg<TC, CM, RM>;
+  constexpr int TM = C::TM, NCP = C::NCP;
+  auto step = [&](int k) {
+    T a[RM], b[CM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i) a[i] = As[k * (TM + 1) + tr * RM + i];
+#pragma unroll
+    for (int j = 0; j < CM; ++j) b[j] = Bs[k * NCP + tc + TC * j];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+      for (int j = 0; j < CM; ++j) acc[i][j] += a[i] * b[j];
+  };
+  if (kc == TK) {
+#pragma unroll
+    for (int k = 0; k < TK; ++k) step(k);
+  } else {
+    for (int k = 0; k < kc; ++k) step(k);
+  }
+}
+
 template <typename T, int TC, int CM, int RM>
 __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *B, T *Y,
                              T *U, int J, int r0, T *sm) {
@@ -331,12 +372,14 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
   for (int k0 = 0; k0 < kmax; k0 += TK) {
     const int kc = min(TK, kmax - k0);
     stage_sources(c, J, k0, kc, gs);
+#pragma unroll
     for (int i = tid; i < TK * TM; i += ST) {
       const int r = i % TM, k = i / TM;
       T v = T(0);
       if (r0 + r < m && k < kc) v = __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]);
       As[k * (TM + 1) + r] = v;
     }
+#pragma unroll
     for (int i = tid; i < TK * NCP; i += ST) {
       const int col = i % NCP, k = i / NCP;
       T v = T(0);
@@ -347,18 +390,7 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
       Bs[k * NCP + col] = v;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < TK; ++k) {
-      T a[RM], b[CM];
-#pragma unroll
-      for (int i = 0; i < RM; ++i) a[i] = As[k * (TM + 1) + tr * RM + i];
-#pragma unroll
-      for (int j = 0; j < CM; ++j) b[j] = Bs[k * NCP + tc + TC * j];
-#pragma unroll
-      for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < CM; ++j) acc[i][j] += a[i] * b[j];
-    }
+    if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
     __syncthreads();
   }
   // epilogue: y rows, or update rows u = f_bot - P_bot f_top
@@ -408,6 +440,7 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
   for (int k0 = r0; k0 < m; k0 += TK) {
     for (int i = tid; i < TK; i += ST) rows_s[i] = (k0 + i < m) ? c.f.rows[rp + k0 + i] : 0;
+#pragma unroll
     for (int i = tid; i < TK * TM; i += ST) {
       const int k = i % TK, r = i / TK;
       T v = T(0);
@@ -415,6 +448,7 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
       As[k * (TM + 1) + r] = v;
     }
     __syncthreads();
+#pragma unroll
     for (int i = tid; i < TK * NCP; i += ST) {
       const int col = i % NCP, k = i / NCP;
       const int kk = k0 + k;
@@ -426,18 +460,8 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
       Bs[k * NCP + col] = v;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < TK; ++k) {
-      T a[RM], b[CM];
-#pragma unroll
-      for (int i = 0; i < RM; ++i) a[i] = As[k * (TM + 1) + tr * RM + i];
-#pragma unroll
-      for (int j = 0; j < CM; ++j) b[j] = Bs[k * NCP + tc + TC * j];
-#pragma unroll
-      for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < CM; ++j) acc[i][j] += a[i] * b[j];
-    }
+    const int kc = min(TK, m - k0);
+    if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
     __syncthreads();
   }
 #pragma unroll

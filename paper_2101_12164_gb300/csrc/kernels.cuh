@@ -123,9 +123,10 @@ void launch_pcg_scalars(const double *rz_new, const double *rz_old, const double
 // ---- small dense FP64 core on one CTA (k_core.cu) ---------------------------------
 // Cholesky-QR with column drop: C (s x s) = W^T W; writes Rinv (s x s, zero outside the kept
 // columns) such that W Rinv has orthonormal kept columns, mask[j] = kept, *nkept.
+// batch > 1 factors `batch` independent s x s matrices stored consecutively (one CTA each).
 void launch_chol_drop(const double *C, int s, double drop_tol, double *Rinv, int32_t *mask,
-                      int32_t *nkept, double *gwork, cudaStream_t stream);
-// doubles of scratch for launch_chol_drop / launch_spd_solve_masked
+                      int32_t *nkept, double *gwork, cudaStream_t stream, int batch = 1);
+// doubles of scratch per problem for launch_chol_drop / launch_spd_solve_masked
 size_t core_work_size(int s);
 // out (s x r) = sign * PtQ^{-1} Rhs on the kept rows/cols (mask), zero elsewhere (r <= s).
 // Non-SPD PtQ -> DEV_BREAKDOWN.
@@ -134,13 +135,42 @@ void launch_spd_solve_masked(const double *PtQ, const double *Rhs, int s, int r,
                              DevStatus *st, cudaStream_t stream);
 // max_j sqrt(colsq[j]) / bnorm[j] -> *ratio
 void launch_max_ratio(const double *colsq, const double *bnorm, int s, double *ratio,
-                      cudaStream_t stream);
+                      cudaStream_t stream, int batch = 1);
 void launch_sqrt_vec(const double *in, int s, double *out, cudaStream_t stream);
 // Nyström core (Algorithm 2 steps 5-10) on K = Y^T Y and C = G^T Y (s x s FP64):
 // writes Mix (s x k, row-major) with U = Y Mix, Sigma (k), *rank. work >= nystrom_work(s).
 void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
                          double drop_tol, double *Mix, double *Sigma, int32_t *rank,
-                         double *work, cudaStream_t stream);
-size_t nystrom_work_size(int s);
+                         double *work, cudaStream_t stream, int batch = 1);
+size_t nystrom_work_size(int s);   // doubles of scratch per problem
+
+// ---- segmented kernels for batches of matrices (k_batch.cu) ------------------------
+// Chunks of rows [row0[c], row1[c]) of segment seg[c]; segment g owns chunks
+// [seg_first[g], seg_first[g+1]) in row order.
+struct SegChunks {
+  int nchunk = 0, nseg = 0;
+  const int64_t *row0 = nullptr, *row1 = nullptr;
+  const int32_t *seg = nullptr, *seg_first = nullptr;
+};
+// C[g] (s1 x s2) = X[rows of g]^T Y[rows of g]; work >= nchunk * s1 * s2 doubles
+template <typename T, typename AccT>
+void launch_seg_gram(const T *X, const T *Y, int s1, int s2, const SegChunks &ch, double *C,
+                     double *work, cudaStream_t st);
+template <typename T>
+void launch_seg_colsq(const T *X, int s, const SegChunks &ch, double *colsq, double *work,
+                      cudaStream_t st);
+void launch_seg_dot(const double *x, const double *y, const SegChunks &ch, double *out,
+                    double *work, cudaStream_t st);
+void launch_seg_axpby(const SegChunks &ch, const double *a, double sign, const double *x,
+                      double b, double *y, cudaStream_t st);
+void launch_seg_ratio(const double *num, const double *den, const int32_t *active, int nseg,
+                      double *out, cudaStream_t st);
+template <typename T>
+void launch_seg_scale_sqrt(const T *Zt, int k, const double *Sigma, const SegChunks &ch,
+                           double *Zs, cudaStream_t st);
+template <typename T>
+void launch_seg_block_update(const T *A, const double *M, int s1, int s2, T scale, const T *C,
+                             T beta, T *Out, const SegChunks &ch, const int32_t *active,
+                             cudaStream_t st);
 
 }  // namespace nsp
