@@ -97,7 +97,7 @@ typedef struct {
   int32_t max_inner_it;      /* inner block-PCG iteration cap (e.g. 500)                  */
   uint64_t seed;             /* Gaussian sketch seed (Philox4x32-10 + Box-Muller)          */
   const double *sketch;      /* optional caller sketch G: n_Gamma x s row-major, Gamma
-                                order, host memory; NULL = draw from seed                 */
+                                order, host or device memory; NULL = draw from seed       */
   int32_t precision;         /* nsp_precision of the factors and the inner block PCG      */
   int32_t outer_form;        /* nsp_outer_form                                            */
   int32_t inner_form;        /* nsp_inner_form                                            */
@@ -227,6 +227,66 @@ nsp_status nsp_get_basis(const nsp_handle *h, double *Z, double *Sigma, int32_t 
  * 1: E (block-PCG solution), 2: Y (= A_G E, step 4), 3: U (step 10, n_Gamma x rank). */
 nsp_status nsp_get_intermediate(const nsp_handle *h, int32_t which, double *out);
 
+/* ---- Learned sketch proposal --------------------------------------------------------
+ * The paper draws the sketch G of Algorithm 2 step 1 at random; its angle bound (§4.2,
+ * Proposition 4.1, eq. (tight_bound)) says the Nyström factor improves when range(G) is
+ * closer to the dominant eigenvectors. These calls train and run a small network phi that
+ * proposes G row by row from raw per-interface-node attributes a_i (d_raw doubles, the
+ * first n_coord of them coordinates in (0, 1)):
+ *   e_i = [sin(pi j a_ic), cos(pi j a_ic), c < n_coord, j = 1..n_freq] ++ a_i[n_coord:]
+ *   h1 = tanh(e W1 + b1), h2 = tanh(h1 W2 + b2), g_i = h2 W3 + b3   (s_out columns)
+ * Training minimises, for a target basis U (n x k, orthonormal columns),
+ *   L = ||U - G (G^T G)^{-1} G^T U||_F^2 + mu ||G^T G / n - I||_F^2.
+ * Parameters are one flat vector [W1, b1, W2, b2, W3, b3], weights row-major with the input
+ * dimension first (nsp_net_num_params entries). Arrays of attributes (n x d_raw), targets
+ * (n x k) and sketches (n x s_out) are row-major doubles, host or device (detected); the
+ * parameter arrays of nsp_net_create / set / get are host memory. Work runs on the stream
+ * given at creation. The paper has none of this; it is the learned-proposal extension. */
+typedef struct {
+  int32_t d_raw;       /* raw attributes per node                                        */
+  int32_t n_coord;     /* leading attributes that are coordinates in (0, 1)              */
+  int32_t n_freq;      /* Fourier frequencies per coordinate                             */
+  int32_t hidden;      /* width of both tanh layers, 1..256                              */
+  int32_t s_out;       /* sketch columns (k + p), 1..128                                 */
+  int32_t precision;   /* training arithmetic: NSP_FP32 or NSP_FP64                      */
+  double mu;           /* weight of the conditioning term, >= 0                          */
+} nsp_net_shape;
+typedef struct nsp_net nsp_net;
+
+/* Number of parameters of a network of this shape (-1 if the shape is invalid). */
+int64_t nsp_net_num_params(const nsp_net_shape *sh);
+/* Create a network with parameters theta0; stream is a cudaStream_t (NULL: default). */
+nsp_status nsp_net_create(const nsp_net_shape *sh, const double *theta0, void *stream,
+                          nsp_net **out);
+/* Replace the parameters; clears the gradient and the Adam state. */
+nsp_status nsp_net_set_params(nsp_net *net, const double *theta);
+/* Copy to host: what = 0 parameters, 1 accumulated gradient, 2 / 3 Adam first / second
+ * moments (nsp_net_num_params doubles). */
+nsp_status nsp_net_get(const nsp_net *net, int32_t what, double *out);
+/* G = phi(attrs) in the training precision (n x s_out). Synchronous. */
+nsp_status nsp_net_forward(const nsp_net *net, const double *attrs, int64_t n, double *G);
+/* Add dL/dtheta for one (attrs, U) pair to the accumulated gradient; *loss (host, may be
+ * NULL: no synchronization) receives L. Needs n >= s_out, 1 <= k <= 256. */
+nsp_status nsp_net_loss_grad(nsp_net *net, const double *attrs, int64_t n, const double *U,
+                             int32_t k, double *loss);
+nsp_status nsp_net_zero_grad(nsp_net *net);
+/* One Adam step (Kingma & Ba, bias-corrected) with the accumulated gradient, which is
+ * then cleared. */
+nsp_status nsp_net_adam_step(nsp_net *net, double lr, double beta1, double beta2, double eps);
+/* Inference for nsp_build's sketch: phi(attrs) with the embedding and hidden layers in
+ * BF16 weights and BF16-rounded activations (FP32 sums) and the output layer in FP32 (BF16
+ * there loses the small singular directions of the ill-conditioned proposed block), then
+ * orthonormalized by Cholesky-QR in FP64: G = phi L^{-T}, phi^T phi = L L^T. Algorithm 2 only
+ * depends on range(G) (G -> G R leaves the Nyström factor unchanged), and the orthonormal
+ * basis keeps the FP32 block PCG well conditioned. Written as doubles (n x s_out, Gamma
+ * order). *full_rank (may be NULL) is 1 when the Cholesky keeps every pivot above 1e-12
+ * times the largest diagonal entry; otherwise G is the raw output and callers fall back to
+ * the Gaussian sketch. With full_rank NULL no check and no orthonormalization is done.
+ * Synchronous. */
+nsp_status nsp_net_sketch(nsp_net *net, const double *attrs, int64_t n, double *G,
+                          int32_t *full_rank);
+nsp_status nsp_net_destroy(nsp_net *net);
+
 /* Dense lower Cholesky factor entries of one factor, for tests: block in [0, nblocks]
  * (nblocks = A_G). Writes the block's elimination order (n_b global indices of A) to
  * order and the factor L (n_b x n_b column-major, zeros above the diagonal and outside
@@ -242,6 +302,9 @@ nsp_status nsp_analyze(const nsp_csr *A, const nsp_partition *P, nsp_info *info)
 
 nsp_status nsp_get_info(const nsp_handle *h, nsp_info *info);
 nsp_status nsp_destroy(nsp_handle *h);
+/* Message of the last failed call made on the calling thread ("" if none); valid until
+ * the next failing call on that thread. */
+const char *nsp_last_error(void);
 const char *nsp_status_string(nsp_status s);
 
 /* Number of CUDA kernels this library has launched in the process so far (all handles).

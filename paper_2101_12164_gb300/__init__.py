@@ -23,9 +23,11 @@ STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_
           7: "NSP_ERR_CUDA", 8: "NSP_ERR_OOM", 9: "NSP_ERR_UNSUPPORTED"}
 EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_solve",
            "nsp_schur_apply", "nsp_factor_solve", "nsp_get_basis", "nsp_get_intermediate",
-           "nsp_get_factor", "nsp_get_info", "nsp_destroy", "nsp_status_string", "nsp_gaussian",
+           "nsp_get_factor", "nsp_get_info", "nsp_destroy", "nsp_status_string", "nsp_last_error", "nsp_gaussian",
            "nsp_analyze", "nsp_kernel_launches", "nsp_schur_apply_noalloc", "nsp_build_batched",
-           "nsp_solve_batched"]
+           "nsp_solve_batched", "nsp_net_num_params", "nsp_net_create", "nsp_net_set_params",
+           "nsp_net_get", "nsp_net_forward", "nsp_net_loss_grad", "nsp_net_zero_grad",
+           "nsp_net_adam_step", "nsp_net_sketch", "nsp_net_destroy"]
 
 
 class NspError(RuntimeError):
@@ -49,6 +51,12 @@ class nsp_params(C.Structure):
                 ("max_inner_it", C.c_int32), ("seed", C.c_uint64), ("sketch", C.c_void_p),
                 ("precision", C.c_int32), ("outer_form", C.c_int32), ("inner_form", C.c_int32),
                 ("keep_intermediates", C.c_int32), ("stream", C.c_void_p)]
+
+
+class nsp_net_shape(C.Structure):
+    _fields_ = [("d_raw", C.c_int32), ("n_coord", C.c_int32), ("n_freq", C.c_int32),
+                ("hidden", C.c_int32), ("s_out", C.c_int32), ("precision", C.c_int32),
+                ("mu", C.c_double)]
 
 
 class nsp_info(C.Structure):
@@ -92,6 +100,7 @@ def lib():
             "nsp_get_info": (C.c_int, [P, C.POINTER(nsp_info)]),
             "nsp_destroy": (C.c_int, [P]),
             "nsp_status_string": (C.c_char_p, [C.c_int]),
+            "nsp_last_error": (C.c_char_p, []),
             "nsp_gaussian": (C.c_int, [C.c_uint64, C.c_int64, P, P]),
             "nsp_analyze": (C.c_int, [C.POINTER(nsp_csr), C.POINTER(nsp_partition),
                                       C.POINTER(nsp_info)]),
@@ -100,6 +109,17 @@ def lib():
             "nsp_build_batched": (C.c_int, [C.c_int32, P, P, C.POINTER(nsp_params),
                                             C.POINTER(P)]),
             "nsp_solve_batched": (C.c_int, [P, P, P, C.c_double, C.c_int32, P]),
+            "nsp_net_num_params": (C.c_int64, [C.POINTER(nsp_net_shape)]),
+            "nsp_net_create": (C.c_int, [C.POINTER(nsp_net_shape), P, P, C.POINTER(P)]),
+            "nsp_net_set_params": (C.c_int, [P, P]),
+            "nsp_net_get": (C.c_int, [P, C.c_int32, P]),
+            "nsp_net_forward": (C.c_int, [P, P, C.c_int64, P]),
+            "nsp_net_loss_grad": (C.c_int, [P, P, C.c_int64, P, C.c_int32,
+                                            C.POINTER(C.c_double)]),
+            "nsp_net_zero_grad": (C.c_int, [P]),
+            "nsp_net_adam_step": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.c_double]),
+            "nsp_net_sketch": (C.c_int, [P, P, C.c_int64, P, C.POINTER(C.c_int32)]),
+            "nsp_net_destroy": (C.c_int, [P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -111,7 +131,8 @@ def lib():
 
 def _check(status, where):
     if status != 0:
-        raise NspError(status, where)
+        msg = lib().nsp_last_error()
+        raise NspError(status, where + (" (%s)" % msg.decode() if msg else ""))
 
 
 def _ptr(x):
@@ -175,7 +196,12 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                       "full": NSP_OUTER_FULL}[outer_form]
     prm.keep_intermediates = 1 if keep_intermediates else 0
     if sketch is not None:
-        sk = np.ascontiguousarray(sketch, dtype=np.float64)
+        if hasattr(sketch, "data_ptr"):   # device tensor: passed through (float64, contiguous)
+            if str(sketch.dtype) != "torch.float64" or not sketch.is_contiguous():
+                raise ValueError("a device sketch must be a contiguous float64 tensor")
+            sk = sketch
+        else:
+            sk = np.ascontiguousarray(sketch, dtype=np.float64)
         if keep is not None:
             keep.append(sk)
         prm.sketch = _ptr(sk)
@@ -209,6 +235,84 @@ def nsp_build_batched(mats, **kw):
     hd = Handle(h, prm, keep)
     hd.batch = len(mats)
     return hd
+
+
+class SketchNet:
+    """The learned sketch proposal (nsp_net_* calls): raw node attributes -> sketch rows."""
+
+    def __init__(self, theta0, d_raw, n_coord, n_freq, hidden, s_out, precision="fp32",
+                 mu=1e-2, stream=None):
+        self.shape = nsp_net_shape(int(d_raw), int(n_coord), int(n_freq), int(hidden), int(s_out),
+                                   NSP_FP64 if precision == "fp64" else NSP_FP32, float(mu))
+        self.num_params = int(lib().nsp_net_num_params(C.byref(self.shape)))
+        if self.num_params < 0:
+            raise NspError(1, "nsp_net_num_params")
+        th = np.ascontiguousarray(theta0, dtype=np.float64)
+        if th.size != self.num_params:
+            raise ValueError("theta0 has %d entries, the network %d" % (th.size, self.num_params))
+        if stream is None:
+            stream = _stream()
+        self._h = C.c_void_p()
+        _check(lib().nsp_net_create(C.byref(self.shape), _ptr(th), C.c_void_p(stream),
+                                    C.byref(self._h)), "nsp_net_create")
+
+    def _handle(self):
+        if not self._h:
+            raise RuntimeError("network destroyed")
+        return self._h
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        _check(lib().nsp_net_set_params(self._handle(), _ptr(th)), "nsp_net_set_params")
+
+    def get(self, what=0):
+        out = np.zeros(self.num_params)
+        _check(lib().nsp_net_get(self._handle(), int(what), _ptr(out)), "nsp_net_get")
+        return out
+
+    def params(self):
+        return self.get(0)
+
+    def grad(self):
+        return self.get(1)
+
+    def forward(self, attrs, G):
+        n = attrs.shape[0]
+        _check(lib().nsp_net_forward(self._handle(), _ptr(attrs), n, _ptr(G)), "nsp_net_forward")
+        return G
+
+    def loss_grad(self, attrs, U, want_loss=True):
+        loss = C.c_double(0.0)
+        _check(lib().nsp_net_loss_grad(self._handle(), _ptr(attrs), attrs.shape[0], _ptr(U),
+                                       U.shape[1], C.byref(loss) if want_loss else None),
+               "nsp_net_loss_grad")
+        return loss.value if want_loss else None
+
+    def zero_grad(self):
+        _check(lib().nsp_net_zero_grad(self._handle()), "nsp_net_zero_grad")
+
+    def adam_step(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(lib().nsp_net_adam_step(self._handle(), float(lr), float(beta1), float(beta2),
+                                       float(eps)), "nsp_net_adam_step")
+
+    def sketch(self, attrs, G, check=True):
+        """Inference into G (n x s_out doubles). With check, G is orthonormalized and the
+        return value says whether the proposal had full rank; without, G is the raw output."""
+        ok = C.c_int32(0)
+        _check(lib().nsp_net_sketch(self._handle(), _ptr(attrs), attrs.shape[0], _ptr(G),
+                                    C.byref(ok) if check else None), "nsp_net_sketch")
+        return bool(ok.value) if check else None
+
+    def destroy(self):
+        if self._h:
+            lib().nsp_net_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 def nsp_analyze(A, part, nblocks, perm=None):

@@ -19,23 +19,30 @@ struct Error : std::runtime_error {
   Error(nsp_status s, const std::string &msg) : std::runtime_error(msg), status(s) {}
 };
 
-#define NSP_CUDA(call)                                                                    \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess) {                                                              \
-      if (e_ == cudaErrorMemoryAllocation)                                                \
-        throw ::nsp::Error(NSP_ERR_OOM, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-      throw ::nsp::Error(NSP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
-    }                                                                                     \
+#define NSP_STR2_(x) #x
+#define NSP_STR_(x) NSP_STR2_(x)
+#define NSP_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) {                                                                \
+      const std::string m_ = std::string(#call " at " __FILE__ ":" NSP_STR_(__LINE__) ": ") + \
+                             cudaGetErrorString(e_);                                        \
+      throw ::nsp::Error(e_ == cudaErrorMemoryAllocation ? NSP_ERR_OOM : NSP_ERR_CUDA, m_);   \
+    }                                                                                       \
   } while (0)
 
 // Every kernel launch of the library passes through this check, which also counts it.
 int64_t count_launch();
+int64_t launches_counted();
+void add_launches(int64_t k);
 #define NSP_LAUNCH_CHECK()             \
   do {                                 \
     ::nsp::count_launch();             \
     NSP_CUDA(cudaGetLastError());      \
   } while (0)
+
+// Message of the last failed C call on this thread (nsp_last_error).
+void set_last_error(const char *msg);
 
 inline void require(bool ok, nsp_status s, const char *msg) {
   if (!ok) throw Error(s, msg);
@@ -92,5 +99,16 @@ struct DBuf {
 };
 
 inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Opt a kernel into `bytes` of dynamic shared memory when its static plus dynamic shared
+// memory exceed the default 48 KB window (the attribute only ever grows).
+template <typename K>
+inline void ensure_dyn_smem(K kernel, size_t bytes) {
+  if (bytes == 0) return;
+  cudaFuncAttributes fa{};
+  NSP_CUDA(cudaFuncGetAttributes(&fa, kernel));
+  if (fa.sharedSizeBytes + bytes > 48 * 1024 && (size_t)fa.maxDynamicSharedSizeBytes < bytes)
+    NSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
 
 }  // namespace nsp

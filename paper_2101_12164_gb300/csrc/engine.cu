@@ -31,6 +31,10 @@ namespace nsp {
 
 static std::atomic<int64_t> g_launches{0};
 int64_t count_launch() { return g_launches.fetch_add(1, std::memory_order_relaxed) + 1; }
+int64_t launches_counted() { return g_launches.load(); }
+// Launches recorded into a CUDA graph run at its replays: the capture removes them from the
+// count and each replay adds them back.
+void add_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 using Clock = std::chrono::steady_clock;
 static double ms_since(Clock::time_point t0) {
@@ -271,8 +275,9 @@ struct ForestData {
   struct Plan {
     SweepPlan d;
     DBuf<int32_t> item_a, item_b, group_sn, sn_parent, need_f, units_f, units_b;
-    DBuf<int32_t> counters;  // cnt_f, self_f, done_b (nsn each), claim, abort flag
-    int32_t epoch = 0, claim_base = 0, maxneed = 1;
+    DBuf<uint32_t> counters;  // cnt_f, self_f, done_b (nsn each), claim, abort, epoch, base
+    int32_t maxneed = 1;
+    std::map<int, int> tuned_grid;  // right-hand-side count -> persistent grid (autotuner)
   };
   std::unique_ptr<Plan> plans[2];  // 0: block (s > 1), 1: vector (s = 1)
   int vec_rows = 128;
@@ -324,7 +329,7 @@ struct ForestData {
     P.need_f.upload(need, st);
     P.units_f.upload(uf, st);
     P.units_b.upload(ub, st);
-    P.counters.alloc(3 * (size_t)nsn + 2);
+    P.counters.alloc(3 * (size_t)nsn + 4);
     NSP_CUDA(cudaMemsetAsync(P.counters.p, 0, P.counters.bytes(), st));
     int mm = 0;
     for (int J = 0; J < nsn; ++J) mm = std::max(mm, h.sn_m[J]);
@@ -344,6 +349,8 @@ struct ForestData {
     P.d.done_b = P.counters.p + 2 * (size_t)nsn;
     P.d.claim = P.counters.p + 3 * (size_t)nsn;
     P.d.abort_flag = P.counters.p + 3 * (size_t)nsn + 1;
+    P.d.epoch = P.counters.p + 3 * (size_t)nsn + 2;
+    P.d.claim_base = P.counters.p + 3 * (size_t)nsn + 3;
     return P;
   }
 
@@ -491,6 +498,10 @@ struct Engine : EngineBase {
     info.failed_block = -1;
   }
   ~Engine() override {
+    if (gstream) cudaStreamDestroy(gstream);
+    for (cudaEvent_t e : gev)
+      if (e) cudaEventDestroy(e);
+    if (h_any) cudaFreeHost(h_any);
     if (hstat) cudaFreeHost(hstat);
     if (hscal) cudaFreeHost(hscal);
     if (hint) cudaFreeHost(hint);
@@ -562,15 +573,61 @@ struct Engine : EngineBase {
   void solve_forest(ForestData &F, const T *panel, const T *B, T *Ywk, T *Uwk, T *X, int sc) {
     F.vec_rows = sweep_vector_rows((int)sizeof(T));
     auto &P = F.plan(sc == 1, st);
-    P.epoch += 1;
-    if ((int64_t)P.epoch * P.maxneed > (int64_t(1) << 30) || P.claim_base > (1 << 30)) {
-      NSP_CUDA(cudaMemsetAsync(P.counters.p, 0, P.counters.bytes(), st));
-      P.epoch = 1;
-      P.claim_base = 0;
+    int grid = 0;
+    auto it = P.tuned_grid.find(sc);
+    if (it != P.tuned_grid.end()) {
+      grid = it->second;
+    } else if (autotune_enabled() && !capturing()) {
+      grid = tune_sweep(F, P, panel, B, Ywk, Uwk, X, sc);
+      P.tuned_grid[sc] = grid;
     }
-    const int grid = launch_sweep<T>(F.dev, P.d, P.epoch, P.claim_base, panel, B, Ywk, Uwk, X,
-                                     sc, dstat.p, st);
-    P.claim_base += P.d.nitems + grid;
+    launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, grid);
+  }
+
+  // Autotuner of the persistent sweep: the grid (CTAs resident per SM, 1 to the occupancy
+  // limit) is timed on the handle's own forest and right-hand-side count with CUDA events,
+  // once per (forest, s); the fastest is kept. Every candidate computes the same result.
+  static bool autotune_enabled() {
+    const char *e = std::getenv("NSP_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }
+  bool capturing() {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NSP_CUDA(cudaStreamIsCapturing(st, &cs));
+    return cs != cudaStreamCaptureStatusNone;
+  }
+  std::vector<std::pair<int, float>> tune_log;
+  int tune_sweep(ForestData &F, ForestData::Plan &P, const T *panel, const T *B, T *Ywk, T *Uwk,
+                 T *X, int sc) {
+    int dev = 0, sms = 0;
+    NSP_CUDA(cudaGetDevice(&dev));
+    NSP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int gmax = launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, 0);
+    cudaEvent_t e0, e1;
+    NSP_CUDA(cudaEventCreate(&e0));
+    NSP_CUDA(cudaEventCreate(&e1));
+    int best = gmax;
+    float best_ms = 1e30f;
+    for (int g = sms; g <= gmax; g += sms) {
+      float tot = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        NSP_CUDA(cudaEventRecord(e0, st));
+        launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, g);
+        NSP_CUDA(cudaEventRecord(e1, st));
+        NSP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+      }
+      tune_log.push_back({g, tot / 2});
+      if (tot < best_ms) {
+        best_ms = tot;
+        best = g;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return best;
   }
   void solve_I(const T *B, T *X, int sc) {
     ensure_ws(sc);
@@ -659,7 +716,7 @@ struct Engine : EngineBase {
     {
       g64.ensure(ns);
       if (prm.sketch) {
-        NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+        NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyDefault, st));
       } else {
         launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
       }
@@ -1005,7 +1062,7 @@ struct Engine : EngineBase {
     NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
     g64.ensure(ns);
     if (prm.sketch) {
-      NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyHostToDevice, st));
+      NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyDefault, st));
     } else {
       launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
     }
@@ -1102,78 +1159,148 @@ struct Engine : EngineBase {
     launch_seg_block_update<double>(Zs.p, bt.p, k, 1, 1.0, zG, 1.0, zG, chG.d, nullptr, st);
   }
 
+  // Outer PCG of every matrix at once. The per-matrix bookkeeping (step counts, stopping
+  // test, masks) lives on the device, so an iteration is a fixed sequence of launches with no
+  // host decision; after one eager iteration (which allocates every workspace and builds the
+  // sweep plans) kGraphIters iterations are captured into a CUDA graph and replayed until no
+  // matrix is active. Matrices that stop early are masked (alpha = 0), so replayed
+  // iterations beyond their stop leave them unchanged.
+  static constexpr int kGraphIters = 4;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  DBuf<double> bfn, brel;
+  DBuf<int32_t> bits, bany;
+  int32_t *h_any = nullptr;
+  int64_t graph_replays = 0;
+
+  void pcg_batched_iteration(double rtol, int maxit) {
+    const int64_t n = an.n, nI = an.nI;
+    double *sc = bscal.p;
+    double *d_rz = sc, *d_pq = sc + nseg, *d_al = sc + 2 * nseg, *d_be = sc + 3 * nseg,
+           *d_rr = sc + 4 * nseg, *d_rzn = sc + 5 * nseg;
+    // q = A p
+    launch_spmm<double>(A_I.d64(), vp.p, vq.p, 1, 1.0, nullptr, 0.0, st);
+    launch_spmm<double>(A_IG.d64(), vp.p + nI, vq.p, 1, 1.0, vq.p, 1.0, st);
+    launch_spmm<double>(A_GI.d64(), vp.p, vq.p + nI, 1, 1.0, nullptr, 0.0, st);
+    launch_spmm<double>(A_G.d64(), vp.p + nI, vq.p + nI, 1, 1.0, vq.p + nI, 1.0, st);
+    launch_seg_dot(vp.p, vq.p, chF.d, d_pq, bwork.p, st);
+    launch_seg_ratio(d_rz, d_pq, bactive.p, nseg, d_al, st);
+    launch_seg_axpby(chF.d, d_al, 1.0, vp.p, 1.0, vx.p, st);
+    launch_seg_axpby(chF.d, d_al, -1.0, vq.p, 1.0, vr.p, st);
+    launch_seg_dot(vr.p, vr.p, chF.d, d_rr, bwork.p, st);
+    launch_seg_converge(d_rr, bfn.p, rtol, maxit, bactive.p, bits.p, brel.p, bany.p, nseg, st);
+    // z = M r (block-factorization preconditioner with M2 of every matrix)
+    double *t = pfull_t.p;
+    solve_I64(vr.p, t);
+    launch_spmm<double>(A_GI.d64(), t, t + nI, 1, -1.0, vr.p + nI, 1.0, st);
+    m2_batched(t + nI, vz.p + nI);
+    launch_spmm<double>(A_IG.d64(), vz.p + nI, t, 1, -1.0, vr.p, 1.0, st);
+    solve_I64(t, vz.p);
+    launch_seg_dot(vr.p, vz.p, chF.d, d_rzn, bwork.p, st);
+    launch_seg_ratio(d_rzn, d_rz, bactive.p, nseg, d_be, st);
+    launch_seg_axpby(chF.d, d_be, 1.0, vp.p, 0.0, vp.p, st);     // p = beta p
+    launch_seg_axpby(chF.d, nullptr, 1.0, vz.p, 1.0, vp.p, st);  // p += z
+    NSP_CUDA(cudaMemcpyAsync(d_rz, d_rzn, nseg * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    (void)n;
+  }
+
   void solve_batched(const double *b_user, double *x_user, double rtol, int maxit) override {
     auto t0 = Clock::now();
     const int64_t n = an.n, nI = an.nI, nG = an.nG;
     vb.ensure(n); vx.ensure(n); vt.ensure(n); vu.ensure(n); vf.ensure(n);
     vr.ensure(n); vz.ensure(n); vp.ensure(n); vq.ensure(n); pfull_t.ensure(n);
+    bfn.ensure(nseg); brel.ensure(nseg); bits.ensure(nseg); bany.ensure(1);
+    if (!h_any) NSP_CUDA(cudaMallocHost(&h_any, sizeof(int32_t)));
     ensure_ws(1);
     double *sc = bscal.p;  // per matrix: rz, pq, alpha, beta, rr, rznew, ff, bb (8 x nseg)
-    double *d_rz = sc, *d_pq = sc + nseg, *d_al = sc + 2 * nseg, *d_be = sc + 3 * nseg,
-           *d_rr = sc + 4 * nseg, *d_rzn = sc + 5 * nseg, *d_ff = sc + 6 * nseg, *d_bb = sc + 7 * nseg;
+    double *d_rz = sc, *d_rr = sc + 4 * nseg, *d_ff = sc + 6 * nseg, *d_bb = sc + 7 * nseg;
     double *bI = vb.p, *bG = vb.p + nI;
     launch_gather_rows<double, double>(i2g_I.p, nI, b_user, bI, 1, st);
     launch_gather_rows<double, double>(i2g_G.p, nG, b_user, bG, 1, st);
-    auto Aop = [&](const double *v, double *o) {
-      launch_spmm<double>(A_I.d64(), v, o, 1, 1.0, nullptr, 0.0, st);
-      launch_spmm<double>(A_IG.d64(), v + nI, o, 1, 1.0, o, 1.0, st);
-      launch_spmm<double>(A_GI.d64(), v, o + nI, 1, 1.0, nullptr, 0.0, st);
-      launch_spmm<double>(A_G.d64(), v + nI, o + nI, 1, 1.0, o + nI, 1.0, st);
-    };
-    auto Mop = [&](const double *r, double *z) {
-      double *t = pfull_t.p;
-      solve_I64(r, t);
-      launch_spmm<double>(A_GI.d64(), t, t + nI, 1, -1.0, r + nI, 1.0, st);
-      m2_batched(t + nI, z + nI);
-      launch_spmm<double>(A_IG.d64(), z + nI, t, 1, -1.0, r, 1.0, st);
-      solve_I64(t, z);
-    };
+    // x0 = (A_I^{-1} b_I, 0); r0 = b - A x0
     double *x0 = vu.p;
     solve_I64(bI, x0);
     NSP_CUDA(cudaMemsetAsync(x0 + nI, 0, nG * sizeof(double), st));
-    Aop(x0, vf.p);
-    launch_axpby(n, nullptr, 1.0, vb.p, -1.0, vf.p, st);  // r0 = b - A x0
+    launch_spmm<double>(A_I.d64(), x0, vf.p, 1, 1.0, nullptr, 0.0, st);
+    launch_spmm<double>(A_GI.d64(), x0, vf.p + nI, 1, 1.0, nullptr, 0.0, st);
+    launch_axpby(n, nullptr, 1.0, vb.p, -1.0, vf.p, st);
     NSP_CUDA(cudaMemsetAsync(vx.p, 0, n * sizeof(double), st));
     NSP_CUDA(cudaMemcpyAsync(vr.p, vf.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_seg_dot(vf.p, vf.p, chF.d, d_ff, bwork.p, st);
-    std::vector<double> fn(nseg), hr(nseg);
-    NSP_CUDA(cudaMemcpyAsync(fn.data(), d_ff, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
-    sync();
-    for (auto &v : fn) v = std::sqrt(v);
-    h_active.assign(nseg, 1);
-    std::vector<int32_t> its(nseg, 0);
-    std::vector<double> rel(nseg, 1.0);
-    for (int g = 0; g < nseg; ++g)
-      if (fn[g] == 0.0) { h_active[g] = 0; rel[g] = 0.0; }
-    NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    Mop(vr.p, vz.p);
+    launch_seg_pcg_init(d_ff, nseg, bfn.p, bactive.p, bits.p, brel.p, st);
+    // z0 = M r0, p0 = z0, rz = r0^T z0
+    {
+      double *t = pfull_t.p;
+      solve_I64(vr.p, t);
+      launch_spmm<double>(A_GI.d64(), t, t + nI, 1, -1.0, vr.p + nI, 1.0, st);
+      m2_batched(t + nI, vz.p + nI);
+      launch_spmm<double>(A_IG.d64(), vz.p + nI, t, 1, -1.0, vr.p, 1.0, st);
+      solve_I64(t, vz.p);
+    }
     NSP_CUDA(cudaMemcpyAsync(vp.p, vz.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_seg_dot(vr.p, vz.p, chF.d, d_rz, bwork.p, st);
-    for (int it = 0; it < maxit; ++it) {
-      Aop(vp.p, vq.p);
-      launch_seg_dot(vp.p, vq.p, chF.d, d_pq, bwork.p, st);
-      launch_seg_ratio(d_rz, d_pq, bactive.p, nseg, d_al, st);
-      launch_seg_axpby(chF.d, d_al, 1.0, vp.p, 1.0, vx.p, st);
-      launch_seg_axpby(chF.d, d_al, -1.0, vq.p, 1.0, vr.p, st);
-      launch_seg_dot(vr.p, vr.p, chF.d, d_rr, bwork.p, st);
-      NSP_CUDA(cudaMemcpyAsync(hr.data(), d_rr, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // one eager iteration, then graph replays of kGraphIters iterations
+    int done_its = 0;
+    auto any_active = [&]() {
+      NSP_CUDA(cudaMemcpyAsync(h_any, bany.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
       sync();
-      int any = 0;
-      for (int g = 0; g < nseg; ++g) {
-        if (!h_active[g]) continue;
-        its[g] += 1;
-        rel[g] = std::sqrt(std::max(hr[g], 0.0)) / fn[g];
-        if (!(rel[g] > rtol) || its[g] >= maxit) h_active[g] = 0;
-        any |= h_active[g];
+      return *h_any != 0;
+    };
+    pcg_batched_iteration(rtol, maxit);
+    done_its = 1;
+    bool more = any_active() && done_its < maxit;
+    // graphs are captured and replayed on the engine's own non-blocking stream (the caller's
+    // stream may be the legacy default stream, which cannot be captured), ordered after the
+    // caller's stream by an event and joined back at the end
+    cudaStream_t main_st = st;
+    if (more) {
+      if (!gstream) {
+        NSP_CUDA(cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking));
+        NSP_CUDA(cudaEventCreateWithFlags(&gev[0], cudaEventDisableTiming));
+        NSP_CUDA(cudaEventCreateWithFlags(&gev[1], cudaEventDisableTiming));
       }
-      if (!any) break;
-      NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-      Mop(vr.p, vz.p);
-      launch_seg_dot(vr.p, vz.p, chF.d, d_rzn, bwork.p, st);
-      launch_seg_ratio(d_rzn, d_rz, bactive.p, nseg, d_be, st);
-      launch_seg_axpby(chF.d, d_be, 1.0, vp.p, 0.0, vp.p, st);  // p = beta p
-      launch_seg_axpby(chF.d, nullptr, 1.0, vz.p, 1.0, vp.p, st);  // p += z
-      NSP_CUDA(cudaMemcpyAsync(d_rz, d_rzn, nseg * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      NSP_CUDA(cudaEventRecord(gev[0], main_st));
+      NSP_CUDA(cudaStreamWaitEvent(gstream, gev[0], 0));
+      st = gstream;
+    }
+    struct RestoreStream {
+      cudaStream_t &ref, saved;
+      ~RestoreStream() { ref = saved; }
+    } restore{st, main_st};
+    if (more) {
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      const int64_t l0 = launches_counted();
+      NSP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      try {
+        for (int q = 0; q < kGraphIters; ++q) pcg_batched_iteration(rtol, maxit);
+      } catch (...) {
+        cudaStreamEndCapture(st, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        throw;
+      }
+      NSP_CUDA(cudaStreamEndCapture(st, &graph));
+      const int64_t per_replay = launches_counted() - l0;
+      add_launches(-per_replay);  // counted when they run
+      NSP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+      try {
+        while (more) {
+          NSP_CUDA(cudaGraphLaunch(exec, st));
+          add_launches(per_replay);
+          ++graph_replays;
+          done_its += kGraphIters;
+          more = any_active() && done_its < maxit;
+        }
+      } catch (...) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        throw;
+      }
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      NSP_CUDA(cudaEventRecord(gev[1], gstream));
+      NSP_CUDA(cudaStreamWaitEvent(main_st, gev[1], 0));
+      st = main_st;
     }
     launch_axpby(n, nullptr, 1.0, x0, 1.0, vx.p, st);
     launch_scatter_rows<double, double>(i2g_I.p, nI, vx.p, x_user, 1, st);
@@ -1182,9 +1309,12 @@ struct Engine : EngineBase {
     launch_spmm<double>(Af, x_user, vt.p, 1, -1.0, b_user, 1.0, st);
     launch_seg_dot(vt.p, vt.p, chU.d, d_rr, bwork.p, st);
     launch_seg_dot(b_user, b_user, chU.d, d_bb, bwork.p, st);
-    std::vector<double> rr(nseg), bb(nseg);
+    std::vector<double> rr(nseg), bb(nseg), rel(nseg);
+    std::vector<int32_t> its(nseg);
     NSP_CUDA(cudaMemcpyAsync(rr.data(), d_rr, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
     NSP_CUDA(cudaMemcpyAsync(bb.data(), d_bb, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NSP_CUDA(cudaMemcpyAsync(rel.data(), brel.p, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    NSP_CUDA(cudaMemcpyAsync(its.data(), bits.p, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     sync();
     check_status();
     bool ok = true;
@@ -1316,15 +1446,26 @@ struct nsp_handle {
   int32_t batch = 0;   // number of matrices of a batched handle (0: single matrix)
 };
 
+namespace nsp {
+static thread_local std::string g_last_error;
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+}  // namespace nsp
+
 static nsp_status guard(const std::function<void()> &f) {
   try {
     f();
     return NSP_OK;
   } catch (const nsp::Error &e) {
+    nsp::set_last_error(e.what());
     return e.status;
   } catch (const std::bad_alloc &) {
+    nsp::set_last_error("host allocation failed");
     return NSP_ERR_OOM;
+  } catch (const std::exception &e) {
+    nsp::set_last_error(e.what());
+    return NSP_ERR_INVALID_ARG;
   } catch (...) {
+    nsp::set_last_error("unknown exception");
     return NSP_ERR_INVALID_ARG;
   }
 }
@@ -1348,6 +1489,8 @@ void nsp_default_params(nsp_params *prm) {
   prm->keep_intermediates = 0;
   prm->stream = nullptr;
 }
+
+const char *nsp_last_error(void) { return nsp::g_last_error.c_str(); }
 
 const char *nsp_status_string(nsp_status s) {
   switch (s) {

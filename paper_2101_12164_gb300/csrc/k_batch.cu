@@ -159,6 +159,36 @@ __global__ void __launch_bounds__(BT) k_seg_block_update(const T *__restrict__ A
   }
 }
 
+__global__ void k_seg_pcg_init(const double *ff, int nseg, double *fn, int32_t *active,
+                               int32_t *its, double *rel) {
+  for (int g = threadIdx.x; g < nseg; g += blockDim.x) {
+    const double f = sqrt(fmax(ff[g], 0.0));
+    fn[g] = f;
+    active[g] = f > 0.0;
+    its[g] = 0;
+    rel[g] = f > 0.0 ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_seg_converge(const double *rr, const double *fn, double rtol, int maxit,
+                               int32_t *active, int32_t *its, double *rel, int32_t *any, int nseg) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < nseg; g += blockDim.x) {
+    if (!active[g]) continue;
+    const int it = its[g] + 1;
+    its[g] = it;
+    const double r = sqrt(fmax(rr[g], 0.0)) / fn[g];
+    rel[g] = r;
+    const int still = (r > rtol) && (it < maxit);
+    active[g] = still;
+    if (still) s_any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *any = s_any;
+}
+
 // Zs[i][j] = (double) Zt[i][j] * sqrt(Sigma[seg][j]) over chunks
 template <typename T>
 __global__ void k_seg_scale_sqrt(const T *Zt, int k, const double *Sigma, SegChunks ch, double *Zs) {
@@ -237,6 +267,19 @@ void launch_seg_block_update(const T *A, const double *M, int s1, int s2, T scal
     attr = true;
   }
   k_seg_block_update<T><<<ch.nchunk, BT, sm, st>>>(A, M, s1, s2, scale, C, beta, Out, ch, active);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_seg_pcg_init(const double *ff, int nseg, double *fn, int32_t *active, int32_t *its,
+                         double *rel, cudaStream_t st) {
+  k_seg_pcg_init<<<1, 1024, 0, st>>>(ff, nseg, fn, active, its, rel);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_seg_converge(const double *rr, const double *fn, double rtol, int maxit,
+                         int32_t *active, int32_t *its, double *rel, int32_t *any, int nseg,
+                         cudaStream_t st) {
+  k_seg_converge<<<1, 1024, 0, st>>>(rr, fn, rtol, maxit, active, its, rel, any, nseg);
   NSP_LAUNCH_CHECK();
 }
 

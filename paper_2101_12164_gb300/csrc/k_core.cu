@@ -405,35 +405,80 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   gemm_nn(S.b1, S.b2, S.b0, s);  // R_full = L^{-1} K (rows of dropped columns are zero)
   for (size_t i = tid; i < ss; i += CT) gRf[i] = S.b0[i];
   // step 6: symmetric C into b0
+  __shared__ int c_ok;
+  __shared__ double red2[CT];
   for (size_t idx = tid; idx < ss; idx += CT) {
     const int i = idx / s, j = idx % s;
     S.b0[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
   }
+  for (int i = tid; i < s; i += CT) diag0[i] = 0.5 * (C[i * s + i] + C[i * s + i]);
   __syncthreads();
-  // step 7: EVD of C: eigenvalues on b0's diagonal, V in b1
-  eig_sym(S.b0, s, S.b1, S.b2);
-  if (tid == 0) {
-    double dmax = 0.0;
-    for (int j = 0; j < s; ++j) dmax = fmax(dmax, S.b0[j * s + j]);
-    int r = 0;
-    for (int j = 0; j < s; ++j) {
-      const double d = S.b0[j * s + j];
-      dvals[j] = d;
-      keepc[j] = (d > 0.0 && d >= eps_rel * dmax) ? 1 : 0;
-      r += keepc[j];
+  // steps 7-8 when C is provably well conditioned: with C = L_C L_C^T and
+  // lambda_min(C) >= 1 / ||L_C^{-1}||_F^2 >= eps_rel trace(C) >= eps_rel lambda_max(C), the
+  // eigenvalue threshold of step 7 keeps every eigenvalue, so V1 D1^{-1} V1^T = C^{-1} and
+  // R V1 D1^{-1/2} may be replaced by R L_C^{-T} (same T = R C^{-1} R^T); no EVD of C.
+  chol_threshold(S.b0, diag0, s, 0.0, keepc, &r_keep);
+  for (size_t i = tid; i < ss; i += CT) S.b1[i] = (i / s == i % s) ? 1.0 : 0.0;
+  __syncthreads();
+  trsm_masked(S.b0, s, keepc, S.b1, s, false, true);  // b1 = L_C^{-1}
+  {
+    double a = 0.0;
+    for (size_t i = tid; i < ss; i += CT) a += S.b1[i] * S.b1[i];
+    red2[tid] = a;
+    __syncthreads();
+    for (int h = CT / 2; h > 0; h >>= 1) {
+      if (tid < h) red2[tid] += red2[tid + h];
+      __syncthreads();
     }
-    r_keep = r;
+    if (tid == 0) {
+      double tr = 0.0;
+      for (int i = 0; i < s; ++i) tr += diag0[i];
+      c_ok = r_keep == s && tr > 0.0 && 1.0 / red2[0] >= eps_rel * tr;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // step 8: b0 = RV = R_full V1 D1^{-1/2}; b2 = R_full
-  for (size_t i = tid; i < ss; i += CT) S.b2[i] = gRf[i];
-  __syncthreads();
-  gemm_nn(S.b2, S.b1, S.b0, s);
-  for (size_t idx = tid; idx < ss; idx += CT) {
-    const int j = idx % s;
-    S.b0[idx] = keepc[j] ? S.b0[idx] / sqrt(dvals[j]) : 0.0;
+  if (c_ok) {
+    // b0 = RV = R_full L_C^{-T}
+    for (size_t i = tid; i < ss; i += CT) S.b2[i] = gRf[i];
+    __syncthreads();
+    for (int i = tid >> 5; i < s; i += CT / 32)
+      for (int j = tid & 31; j < s; j += 32) {
+        double v = 0.0;
+        for (int t = 0; t <= j; ++t) v += S.b2[i * s + t] * S.b1[j * s + t];
+        S.b0[i * s + j] = v;
+      }
+    __syncthreads();
+  } else {
+    // step 7: EVD of C: eigenvalues on b0's diagonal, V in b1
+    for (size_t idx = tid; idx < ss; idx += CT) {
+      const int i = idx / s, j = idx % s;
+      S.b0[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
+    }
+    __syncthreads();
+    eig_sym(S.b0, s, S.b1, S.b2);
+    if (tid == 0) {
+      double dmax = 0.0;
+      for (int j = 0; j < s; ++j) dmax = fmax(dmax, S.b0[j * s + j]);
+      int r = 0;
+      for (int j = 0; j < s; ++j) {
+        const double d = S.b0[j * s + j];
+        dvals[j] = d;
+        keepc[j] = (d > 0.0 && d >= eps_rel * dmax) ? 1 : 0;
+        r += keepc[j];
+      }
+      r_keep = r;
+    }
+    __syncthreads();
+    // step 8: b0 = RV = R_full V1 D1^{-1/2}; b2 = R_full
+    for (size_t i = tid; i < ss; i += CT) S.b2[i] = gRf[i];
+    __syncthreads();
+    gemm_nn(S.b2, S.b1, S.b0, s);
+    for (size_t idx = tid; idx < ss; idx += CT) {
+      const int j = idx % s;
+      S.b0[idx] = keepc[j] ? S.b0[idx] / sqrt(dvals[j]) : 0.0;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   for (int i = tid >> 5; i < s; i += CT / 32)  // b1 = T = RV RV^T (symmetric)
     for (int j = i + (tid & 31); j < s; j += 32) {
       double v = 0.0;
@@ -478,8 +523,7 @@ size_t smem_for(int s) { return s <= SMEM_S ? 3 * (size_t)s * s * sizeof(double)
 
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
-  if (bytes > 48 * 1024)
-    NSP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  ensure_dyn_smem(kernel, bytes);
 }
 
 }  // namespace

@@ -14,7 +14,9 @@
 //   backward item of J  : after every backward item of J's parent (after J's own forward
 //                         items for a root).
 // A CTA only waits for items claimed before its own, so the schedule cannot deadlock.
-// Counters grow monotonically; launch e waits for e x (units per supernode).
+// Counters grow monotonically (unsigned, compared modulo 2^32); launch e waits for
+// e x (units per supernode). The epoch e and the claim base are read from device memory,
+// where k_sweep_begin advances them before every launch.
 // Item kinds:
 //   vector (s = 1): 16-byte vector loads of the panel, 8 warps split the K dimension
 //                   (forward) or a warp per panel column (backward); supernodes with
@@ -30,32 +32,41 @@ constexpr int TK = 32;       // K chunk of the block product
 constexpr int MAX_SPINS = 1 << 22;
 
 // ---------------------------------------------------------------- synchronization
-__device__ __forceinline__ int ld_acquire(const int32_t *p) {
-  int v;
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
-  int v;
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
+  uint32_t v;
   asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
-// Thread 0 waits until *p >= target. Returns false (and sets the abort flag) on timeout or
-// when another CTA has aborted.
-__device__ bool wait_geq(const int32_t *p, int32_t target, int32_t *abort_flag, DevStatus *st,
+// Thread 0 waits until *p >= target (modulo 2^32). Returns false (and sets the abort flag)
+// on timeout or when another CTA has aborted.
+__device__ bool wait_geq(const uint32_t *p, uint32_t target, uint32_t *abort_flag, DevStatus *st,
                          int32_t where) {
   int spins = 0;
-  while (ld_acquire(p) < target) {
+  while ((int32_t)(ld_acquire(p) - target) < 0) {
     if (ld_relaxed(abort_flag)) return false;
     if (++spins > MAX_SPINS) {
-      atomicExch(abort_flag, 1);
+      atomicExch(abort_flag, 1u);
       dev_fail(st, DEV_TIMEOUT, where);
       return false;
     }
     __nanosleep(64);
   }
   return true;
+}
+
+// Before every sweep: next epoch; items of this launch are numbered from the claim counter's
+// current value (every earlier launch on the plan has finished, stream order).
+__global__ void k_sweep_begin(SweepPlan p) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *p.epoch += 1u;
+    *p.claim_base = *p.claim;
+  }
 }
 
 template <typename T>
@@ -78,8 +89,6 @@ struct Vec<double> {
 struct SweepCtx {
   ForestDev f;
   SweepPlan p;
-  int32_t epoch;
-  int32_t claim_base;
   int s;
   DevStatus *st;
 };
@@ -485,9 +494,16 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   __shared__ int s_item, s_ok;
+  __shared__ uint32_t s_epoch, s_base;
   const SweepPlan &p = c.p;
+  if (threadIdx.x == 0) {
+    s_epoch = *(volatile uint32_t *)p.epoch;
+    s_base = *(volatile uint32_t *)p.claim_base;
+  }
+  __syncthreads();
+  const uint32_t epoch = s_epoch;
   while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(p.claim, 1) - c.claim_base;
+    if (threadIdx.x == 0) s_item = (int)(atomicAdd(p.claim, 1u) - s_base);
     __syncthreads();
     const int it = s_item;
     if (it >= p.nitems) break;
@@ -500,11 +516,12 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
       for (int q = 0; q < nmem && ok; ++q) {
         const int J = b < 0 ? p.group_sn[a + q] : a;
         if (fwd) {
-          ok = wait_geq(&p.cnt_f[J], c.epoch * p.need_f[J], p.abort_flag, c.st, J);
+          ok = wait_geq(&p.cnt_f[J], epoch * (uint32_t)p.need_f[J], p.abort_flag, c.st, J);
         } else {
           const int par = p.sn_parent[J];
-          ok = par >= 0 ? wait_geq(&p.done_b[par], c.epoch * p.units_b[par], p.abort_flag, c.st, J)
-                        : wait_geq(&p.self_f[J], c.epoch * p.units_f[J], p.abort_flag, c.st, J);
+          ok = par >= 0
+                   ? wait_geq(&p.done_b[par], epoch * (uint32_t)p.units_b[par], p.abort_flag, c.st, J)
+                   : wait_geq(&p.self_f[J], epoch * (uint32_t)p.units_f[J], p.abort_flag, c.st, J);
         }
       }
       s_ok = ok;
@@ -532,11 +549,11 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
       for (int q = 0; q < nmem; ++q) {
         const int J = b < 0 ? p.group_sn[a + q] : a;
         if (fwd) {
-          atomicAdd(&p.self_f[J], 1);
+          atomicAdd(&p.self_f[J], 1u);
           const int par = p.sn_parent[J];
-          if (par >= 0) atomicAdd(&p.cnt_f[par], 1);
+          if (par >= 0) atomicAdd(&p.cnt_f[par], 1u);
         } else {
-          atomicAdd(&p.done_b[J], 1);
+          atomicAdd(&p.done_b[J], 1u);
         }
       }
     }
@@ -547,9 +564,8 @@ template <typename T, int TC, int CM, int RM, bool VECTOR>
 void run_sweep(const SweepCtx &c, int grid, size_t smem, const T *panel, const T *B, T *Y,
                T *U, T *X, cudaStream_t st) {
   static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    NSP_CUDA(cudaFuncSetAttribute(k_sweep<T, TC, CM, RM, VECTOR>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (smem > attr) {
+    ensure_dyn_smem(k_sweep<T, TC, CM, RM, VECTOR>, smem);
     attr = smem;
   }
   k_sweep<T, TC, CM, RM, VECTOR><<<grid, ST, smem, st>>>(c, panel, B, Y, U, X);
@@ -570,9 +586,7 @@ int sweep_grid(size_t smem) {
     int dev = 0, sms = 0, per = 0;
     NSP_CUDA(cudaGetDevice(&dev));
     NSP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (smem > 48 * 1024)
-      NSP_CUDA(cudaFuncSetAttribute(k_sweep<T, TC, CM, RM, VECTOR>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ensure_dyn_smem(k_sweep<T, TC, CM, RM, VECTOR>, smem);
     NSP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sweep<T, TC, CM, RM, VECTOR>,
                                                            ST, smem));
     grid = sms * std::max(1, std::min(per, 4));
@@ -584,7 +598,8 @@ int sweep_grid(size_t smem) {
 template <typename T, int TC, int CM, int RM, bool VECTOR>
 void dispatch(SweepCtx c, size_t smem, const T *panel, const T *B, T *Y, T *U, T *X,
               cudaStream_t st, int *grid_out) {
-  const int grid = sweep_grid<T, TC, CM, RM, VECTOR>(smem);
+  const int gmax = sweep_grid<T, TC, CM, RM, VECTOR>(smem);
+  const int grid = *grid_out > 0 ? std::min(*grid_out, gmax) : gmax;
   *grid_out = grid;
   run_sweep<T, TC, CM, RM, VECTOR>(c, grid, smem, panel, B, Y, U, X, st);
 }
@@ -594,11 +609,12 @@ void dispatch(SweepCtx c, size_t smem, const T *panel, const T *B, T *Y, T *U, T
 int sweep_vector_rows(int elem_bytes) { return 16 * (16 / elem_bytes); }
 
 template <typename T>
-int launch_sweep(const ForestDev &f, const SweepPlan &p, int32_t epoch, int32_t claim_base,
-                 const T *panel, const T *B, T *Y, T *U, T *X, int s, DevStatus *st,
-                 cudaStream_t stream) {
-  SweepCtx c{f, p, epoch, claim_base, s, st};
-  int grid = 0;
+int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y, T *U,
+                 T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req) {
+  SweepCtx c{f, p, s, st};
+  int grid = grid_req;
+  k_sweep_begin<<<1, 32, 0, stream>>>(p);
+  NSP_LAUNCH_CHECK();
   if (s == 1) {
     require(p.vector, NSP_ERR_INVALID_ARG, "vector plan needed for one right-hand side");
     const size_t ldmax = (size_t)((p.max_m + 3) & ~3) + 8;
@@ -623,11 +639,11 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, int32_t epoch, int32_t 
   return grid;
 }
 
-template int launch_sweep<float>(const ForestDev &, const SweepPlan &, int32_t, int32_t,
-                                 const float *, const float *, float *, float *, float *, int,
-                                 DevStatus *, cudaStream_t);
-template int launch_sweep<double>(const ForestDev &, const SweepPlan &, int32_t, int32_t,
-                                  const double *, const double *, double *, double *, double *,
-                                  int, DevStatus *, cudaStream_t);
+template int launch_sweep<float>(const ForestDev &, const SweepPlan &, const float *,
+                                 const float *, float *, float *, float *, int, DevStatus *,
+                                 cudaStream_t, int);
+template int launch_sweep<double>(const ForestDev &, const SweepPlan &, const double *,
+                                  const double *, double *, double *, double *, int, DevStatus *,
+                                  cudaStream_t, int);
 
 }  // namespace nsp

@@ -32,14 +32,17 @@ struct CsrDev {
 // Work list of one persistent solve (see k_solve.cu): nfwd forward items, then backward
 // items. Item i is a tile of supernode item_a[i] starting at row/column item_b[i], or, when
 // item_b[i] < 0, a group of -item_b[i] small supernodes group_sn[item_a[i] ...]. Counters
-// grow across launches; launch number `epoch` waits for epoch x (units per supernode).
+// grow across launches (unsigned, compared modulo 2^32); launch number `epoch` waits for
+// epoch x (units per supernode). The epoch and the claim base live in device memory and are
+// advanced by a one-thread kernel before every sweep, so that sweeps can be captured in a
+// CUDA graph and replayed.
 struct SweepPlan {
   int32_t nitems = 0, nfwd = 0, max_m = 0;
   bool vector = false;
   const int32_t *item_a = nullptr, *item_b = nullptr, *group_sn = nullptr;
   const int32_t *sn_parent = nullptr, *need_f = nullptr, *units_f = nullptr, *units_b = nullptr;
-  int32_t *cnt_f = nullptr, *self_f = nullptr, *done_b = nullptr;
-  int32_t *claim = nullptr, *abort_flag = nullptr;
+  uint32_t *cnt_f = nullptr, *self_f = nullptr, *done_b = nullptr;
+  uint32_t *claim = nullptr, *abort_flag = nullptr, *epoch = nullptr, *claim_base = nullptr;
 };
 
 // ---- numeric factorization (k_factor.cu) -----------------------------------------
@@ -59,10 +62,11 @@ constexpr int kBigFront = 192;   // fronts with m >= kBigFront use the cluster k
 // the forest's internal order; Y (n x s) and U (update rows x s) are workspaces. claim_base
 // is the claim counter's value before the launch; returns the grid size used (the counter
 // advances by nitems + grid).
+// Returns the grid used: grid_req CTAs (rounded to the SM count, capped by occupancy) or,
+// when grid_req <= 0, the occupancy maximum (at most 4 CTAs per SM).
 template <typename T>
-int launch_sweep(const ForestDev &f, const SweepPlan &p, int32_t epoch, int32_t claim_base,
-                 const T *panel, const T *B, T *Y, T *U, T *X, int s, DevStatus *st,
-                 cudaStream_t stream);
+int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y, T *U,
+                 T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req = 0);
 // rows of a forward tile in vector mode for elements of elem_bytes
 int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
@@ -172,5 +176,13 @@ template <typename T>
 void launch_seg_block_update(const T *A, const double *M, int s1, int s2, T scale, const T *C,
                              T beta, T *Out, const SegChunks &ch, const int32_t *active,
                              cudaStream_t st);
+// Per-matrix outer-PCG bookkeeping on the device: fn = sqrt(ff), active = fn > 0, its = 0;
+// then after each step: for active matrices its += 1, rel = ||r|| / fn, active stays on while
+// rel > rtol and its < maxit; any = 1 if some matrix is still active.
+void launch_seg_pcg_init(const double *ff, int nseg, double *fn, int32_t *active, int32_t *its,
+                         double *rel, cudaStream_t st);
+void launch_seg_converge(const double *rr, const double *fn, double rtol, int maxit,
+                         int32_t *active, int32_t *its, double *rel, int32_t *any, int nseg,
+                         cudaStream_t st);
 
 }  // namespace nsp

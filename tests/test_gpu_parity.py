@@ -185,3 +185,26 @@ def test_not_spd_block_reported(N):
     with pytest.raises(N.NspError) as e:
         N.nsp_build(B.tocsr(), part, nsub, k=4, p=2, precision="fp64")
     assert e.value.status == 3
+
+
+def test_singular_c_matches_oracle(N):
+    # A separator three nodes thick: its middle column touches no interior node, so A_IG has
+    # zero columns, rank(A_GI S_I^{-1} A_IG) <= 18 < s = 24 and C = G^T Y is singular: step 7
+    # must drop eigenvalues (the EVD path of the Nyström core, not the Cholesky shortcut).
+    shape = (21, 9)
+    A = F.diffusion_matrix(shape)
+    ix = np.arange(A.shape[0]) % shape[0]          # x fastest
+    part = np.where(ix < 9, 0, np.where(ix > 11, 1, -1)).astype(np.int32)
+    D = O.DBBD(A, part, 2)
+    k, p = 12, 12
+    G = np.random.default_rng(21).standard_normal((D.n_G, k + p))
+    M, info = O.build_m2(D, G, k, 0.1, form="S_gamma", drop_tol=1e-12)
+    assert info["rank_C"] < k + p
+    h = N.nsp_build(A, part, 2, k=k, p=p, precision="fp64", sketch=G, drop_tol=1e-12)
+    gi = h.info()
+    assert gi["it_inner"] == info["it_inner"]
+    assert gi["rank"] == len(info["eig_T"][:k])
+    Z, S = h.get_basis()
+    assert np.allclose(S, info["eig_T"][:gi["rank"]], rtol=1e-8)
+    assert _rel((Z * S) @ Z.T, (M.Z * M.Sigma) @ M.Z.T) < 1e-7
+    h.destroy()
