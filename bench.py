@@ -128,6 +128,18 @@ def schur_apply_bytes(info, s, wbytes, nnz_sub):
             + 2 * info["n_gamma"] * s * wbytes + nnz_sub * (wbytes + 4))
 
 
+def sweep_algorithmic_bytes(info, s, wbytes):
+    """Algorithmic bytes of one interior sweep X = A_I^{-1} B (n_I x s): the panels read by
+    the forward and the backward pass, B read, X written, and one round trip of the n_I x s
+    intermediate between the two passes."""
+    return 2 * info["nnz_L_interior"] * wbytes + 4 * info["n_interior"] * s * wbytes
+
+
+# DRAM bytes (read + write) of one interior-sweep launch from an ncu capture of the bench
+# workload, keyed by (configuration, s); None until captured for the current kernel.
+SWEEP_TRAFFIC = {}
+
+
 def sub_nnz(P):
     part = P.part
     coo = P.A.tocoo()
@@ -277,6 +289,14 @@ def main():
         h.schur_apply(X, Y)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
+        Bi = torch.randn(info0["n_interior"], P.s, device=dev, dtype=X.dtype)
+        Xi = torch.empty_like(Bi)
+        h.factor_solve(0, Bi, Xi)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("interior_sweep")
+        h.factor_solve(0, Bi, Xi)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         h.destroy()
         return
 
@@ -329,6 +349,19 @@ def main():
     hbm, peak_kind = peaks()
     achieved = nbytes / (apply_ms * 1e-3) / 1e9
     flops = 4.0 * info0["nnz_L_interior"] * s
+    # dominant kernel of the apply: the persistent interior sweep A_I^{-1} (n_I x s), alone
+    Bi = torch.randn(info0["n_interior"], s, dtype=dt, device=dev)
+    Xi = torch.empty_like(Bi)
+    h.factor_solve(0, Bi, Xi)
+    torch.cuda.synchronize()
+    a0.record(stream)
+    for _ in range(args.apply_reps):
+        h.factor_solve(0, Bi, Xi)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = a0.elapsed_time(a1) / args.apply_reps
+    sweep_bytes = sweep_algorithmic_bytes(info0, s, wbytes)
+    sweep_gbs = sweep_bytes / (sweep_ms * 1e-3) / 1e9
 
     # ---- e2e: same step through the public calls from pinned host buffers
     val_h = torch.tensor(P.A.data, dtype=torch.float64).pin_memory()
@@ -382,13 +415,18 @@ def main():
                            step_ms_min=float(np.min(step_ms)),
                            phase_ms={"factor": last["ms_factor"], "inner": last["ms_inner"],
                                      "core": last["ms_core"], "solve": last["ms_solve"]}),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "kernel": "S_Gamma block apply (s=%d, %s): A_IG SpMM + supernodal "
-                                   "forward/backward sweeps + A_G/A_GI SpMM" % (s, args.precision),
-                         "apply_ms": apply_ms, "algorithmic_bytes": nbytes,
+            "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": sweep_gbs / hbm, "traffic": SWEEP_TRAFFIC.get((args.config, s)),
+                         "kernel": "k_sweep (s=%d, %s): persistent forward+backward supernodal "
+                                   "sweep of every interior block, the dominant kernel of the "
+                                   "S_Gamma block apply" % (s, args.precision),
+                         "launch_ms": sweep_ms, "algorithmic_bytes": sweep_bytes,
                          "peak_kind": peak_kind,
-                         "flops": flops, "tflops": flops / (apply_ms * 1e-3) / 1e12},
+                         "flops": flops, "tflops": flops / (sweep_ms * 1e-3) / 1e12},
+            "schur_apply": {"achieved": achieved, "unit": "GB/s", "frac": achieved / hbm,
+                            "apply_ms": apply_ms, "algorithmic_bytes": nbytes,
+                            "what": "S_Gamma X: A_IG SpMM + interior sweep + A_G/A_GI SpMM "
+                                    "(s=%d, %s)" % (s, args.precision)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),
