@@ -288,49 +288,6 @@ struct Cfg {
   static constexpr int NCP = TC * CM;
 };
 
-// Sources of the extend-add gather for front positions [p0, p0 + cnt) of supernode J staged
-// in shared memory: off[i] = first source of position p0 + i relative to off[0],
-// src[j] = update row (valid when off[cnt] <= kSrcCap; otherwise read from global memory).
-constexpr int kSrcCap = 4 * 64;
-struct GatherStage {
-  int32_t off[257];
-  int32_t src[kSrcCap];
-  int64_t base;
-  int total;
-};
-
-__device__ void stage_sources(const SweepCtx &c, int J, int p0, int cnt, GatherStage &g) {
-  const int64_t rp = c.f.sn_rowptr[J];
-  const int64_t b0 = c.f.gptr[rp + p0];
-  for (int i = threadIdx.x; i <= cnt; i += ST) g.off[i] = (int32_t)(c.f.gptr[rp + p0 + i] - b0);
-  if (threadIdx.x == 0) g.base = b0;
-  __syncthreads();
-  g.total = g.off[cnt];
-  if (g.total <= kSrcCap)
-    for (int i = threadIdx.x; i < g.total; i += ST) g.src[i] = (int32_t)c.f.gsrc[b0 + i];
-  __syncthreads();
-}
-
-// sum of the update rows landing on staged position i, column col
-template <typename T>
-__device__ __forceinline__ T gather_sum(const SweepCtx &c, const GatherStage &g, const T *U, int i,
-                                        int col) {
-  const int e0 = g.off[i], e1 = g.off[i + 1];
-  const int s = c.s;
-  T v = T(0);
-  if (g.total <= kSrcCap) {
-    T t[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) t[q] = (e0 + q < e1) ? __ldcg(&U[(size_t)g.src[e0 + q] * s + col]) : T(0);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v += t[q];
-    for (int e = e0 + 4; e < e1; ++e) v += __ldcg(&U[(size_t)g.src[e] * s + col]);
-  } else {
-    for (int e = e0; e < e1; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[g.base + e] * s + col]);
-  }
-  return v;
-}
-
 // acc += As[0:kc, rows of this thread]^T Bs[0:kc, columns of this thread]; full chunks run
 // the fully unrolled loop, the last partial chunk a runtime-bounded one.
 template <typename T, int TC, int CM, int RM>
@@ -357,22 +314,27 @@ __device__ __forceinline__ void mac_chunk(const T *As, const T *Bs, int tc, int 
   }
 }
 
+// Forward tile: rows [r0, r0 + TM) of supernode J, all s columns, K = panel columns.
+// The gathered front right-hand side f (b + children's update rows) is staged a warp per
+// front position (uniform index loads, lanes over columns); the panel tile is staged along
+// its contiguous rows. Two block barriers per K chunk.
 template <typename T, int TC, int CM, int RM>
 __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *B, T *Y,
                              T *U, int J, int r0, T *sm) {
   using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP;
-  static_assert(TK <= 256 && TM <= 256, "gather staging holds 256 positions");
-  __shared__ GatherStage gs;
+  constexpr int TM = C::TM, NCP = C::NCP, NW = ST / 32;
+  static_assert((TM & (TM - 1)) == 0, "tile rows must be a power of two");
   T *As = sm;                  // [TK][TM + 1]
   T *Bs = As + TK * (TM + 1);  // [TK][NCP]
   const int s = c.s;
   const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
   const int first = c.f.sn_first[J];
+  const int64_t rp = c.f.sn_rowptr[J];
   const T *P = panel + c.f.sn_panel[J];
   const int r1 = min(r0 + TM, m);
   const int kmax = (r1 <= w) ? r1 : w;
   const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
+  const int lane = tid & 31, wid = tid >> 5;
   T acc[RM][CM];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
@@ -380,23 +342,21 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
   for (int k0 = 0; k0 < kmax; k0 += TK) {
     const int kc = min(TK, kmax - k0);
-    stage_sources(c, J, k0, kc, gs);
-#pragma unroll
-    for (int i = tid; i < TK * TM; i += ST) {
+    for (int i = tid; i < kc * TM; i += ST) {
       const int r = i % TM, k = i / TM;
-      T v = T(0);
-      if (r0 + r < m && k < kc) v = __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]);
-      As[k * (TM + 1) + r] = v;
+      As[k * (TM + 1) + r] = (r0 + r < m) ? __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]) : T(0);
     }
-#pragma unroll
-    for (int i = tid; i < TK * NCP; i += ST) {
-      const int col = i % NCP, k = i / NCP;
-      T v = T(0);
-      if (k < kc && col < s) {
-        if (B) v = B[(size_t)(first + k0 + k) * s + col];
-        v += gather_sum<T>(c, gs, U, k, col);
+    for (int k = wid; k < kc; k += NW) {
+      const int64_t e0 = c.f.gptr[rp + k0 + k], e1 = c.f.gptr[rp + k0 + k + 1];
+      const size_t brow = (size_t)(first + k0 + k) * s;
+      for (int col = lane; col < NCP; col += 32) {
+        T v = T(0);
+        if (col < s) {
+          if (B) v = B[brow + col];
+          for (int64_t e = e0; e < e1; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[e] * s + col]);
+        }
+        Bs[k * NCP + col] = v;
       }
-      Bs[k * NCP + col] = v;
     }
     __syncthreads();
     if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
@@ -404,8 +364,6 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
   }
   // epilogue: y rows, or update rows u = f_bot - P_bot f_top
   const int64_t upd = c.f.sn_upd[J];
-  const int rb = max(r0, w);
-  if (r1 > rb) stage_sources(c, J, rb, r1 - rb, gs);
 #pragma unroll
   for (int i = 0; i < RM; ++i) {
     const int r = r0 + tr * RM + i;
@@ -417,22 +375,27 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
         if (col < s) Y[(size_t)(first + r) * s + col] = acc[i][j];
       }
     } else {
+      const int64_t e0 = c.f.gptr[rp + r], e1 = c.f.gptr[rp + r + 1];
 #pragma unroll
       for (int j = 0; j < CM; ++j) {
         const int col = tc + TC * j;
-        if (col < s)
-          U[(size_t)(upd + r - w) * s + col] = gather_sum<T>(c, gs, U, r - rb, col) - acc[i][j];
+        if (col < s) {
+          T v = T(0);
+          for (int64_t e = e0; e < e1; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[e] * s + col]);
+          U[(size_t)(upd + r - w) * s + col] = v - acc[i][j];
+        }
       }
     }
   }
 }
 
+// Backward tile: x rows [r0, r0 + TM) of supernode J (rows of its own columns), all s
+// columns, K over the m front positions: g = [y_top; -x_bot] staged a warp per position.
 template <typename T, int TC, int CM, int RM>
 __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *Y, T *X,
                              int J, int r0, T *sm) {
   using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP;
-  __shared__ int32_t rows_s[TK];
+  constexpr int TM = C::TM, NCP = C::NCP, NW = ST / 32;
   T *As = sm;
   T *Bs = As + TK * (TM + 1);
   const int s = c.s;
@@ -442,34 +405,27 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
   const T *P = panel + c.f.sn_panel[J];
   const int r1 = min(r0 + TM, w);
   const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
+  const int lane = tid & 31, wid = tid >> 5;
   T acc[RM][CM];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
 #pragma unroll
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
   for (int k0 = r0; k0 < m; k0 += TK) {
-    for (int i = tid; i < TK; i += ST) rows_s[i] = (k0 + i < m) ? c.f.rows[rp + k0 + i] : 0;
-#pragma unroll
+    const int kc = min(TK, m - k0);
     for (int i = tid; i < TK * TM; i += ST) {
       const int k = i % TK, r = i / TK;
-      T v = T(0);
-      if (r0 + r < r1 && k0 + k < m) v = __ldg(&P[(size_t)(k0 + k) + (size_t)(r0 + r) * ld]);
-      As[k * (TM + 1) + r] = v;
+      if (k < kc)
+        As[k * (TM + 1) + r] = (r0 + r < r1) ? __ldg(&P[(size_t)(k0 + k) + (size_t)(r0 + r) * ld]) : T(0);
     }
-    __syncthreads();
-#pragma unroll
-    for (int i = tid; i < TK * NCP; i += ST) {
-      const int col = i % NCP, k = i / NCP;
+    for (int k = wid; k < kc; k += NW) {
       const int kk = k0 + k;
-      T v = T(0);
-      if (kk < m && col < s) {
-        if (kk < w) v = __ldcg(&Y[(size_t)(first + kk) * s + col]);
-        else v = -__ldcg(&X[(size_t)rows_s[k] * s + col]);
-      }
-      Bs[k * NCP + col] = v;
+      const T *src = kk < w ? Y + (size_t)(first + kk) * s : X + (size_t)c.f.rows[rp + kk] * s;
+      const T sg = kk < w ? T(1) : T(-1);
+      for (int col = lane; col < NCP; col += 32)
+        Bs[k * NCP + col] = col < s ? sg * __ldcg(&src[col]) : T(0);
     }
     __syncthreads();
-    const int kc = min(TK, m - k0);
     if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
     __syncthreads();
   }
