@@ -104,6 +104,33 @@ __device__ __forceinline__ T front_rhs(const SweepCtx &c, const T *B, const T *U
   return v;
 }
 
+// v[i] += the update rows landing on front position pos[i] of the supernode whose rows start
+// at rp (pos[i] < 0: none), column col: the NR positions advance together so that their
+// dependent index and value loads are in flight at the same time.
+template <typename T, int NR>
+__device__ __forceinline__ void gather_rows(const SweepCtx &c, const T *U, int64_t rp,
+                                            const int (&pos)[NR], T (&v)[NR], int col) {
+  int64_t e[NR], ee[NR];
+#pragma unroll
+  for (int i = 0; i < NR; ++i) {
+    e[i] = pos[i] >= 0 ? c.f.gptr[rp + pos[i]] : 0;
+    ee[i] = pos[i] >= 0 ? c.f.gptr[rp + pos[i] + 1] : 0;
+  }
+  bool more = true;
+  while (more) {
+    int64_t src[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) src[i] = e[i] < ee[i] ? c.f.gsrc[e[i]] : -1;
+    more = false;
+#pragma unroll
+    for (int i = 0; i < NR; ++i)
+      if (src[i] >= 0) {
+        v[i] += __ldcg(&U[(size_t)src[i] * c.s + col]);
+        more |= ++e[i] < ee[i];
+      }
+  }
+}
+
 // ---------------------------------------------------------------- vector items (s = 1)
 // Forward tile: 16 row groups of VN rows x 16 K groups; each thread keeps 8 vector loads in
 // flight. Rows of the tile: 16 VN (64 floats / 32 doubles).
@@ -119,8 +146,16 @@ __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y
   const int kmax = (r1 <= w) ? r1 : w;
   T *fs = sm;                      // [kmax]
   T *red = sm + ((ld + 3) & ~3);   // [16][TMV]
+  T *gb = red + 16 * TMV;          // [TMV] update-row gathers of the tile's rows
   const int tid = threadIdx.x;
   for (int k = tid; k < kmax; k += ST) fs[k] = front_rhs<T>(c, B, U, J, k, 0, true);
+  if (kmax <= ST - TMV && tid >= ST - TMV) {  // otherwise idle threads gather concurrently
+    const int i = tid - (ST - TMV), r = r0 + i;
+    int pos[1] = {(r >= w && r < r1) ? r : -1};
+    T v[1] = {T(0)};
+    gather_rows<T, 1>(c, U, c.f.sn_rowptr[J], pos, v, 0);
+    gb[i] = v[0];
+  }
   __syncthreads();
   const int rg = tid & 15, kg = tid >> 4;
   const int row = r0 + VN * rg;
@@ -159,7 +194,8 @@ __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y
       if (r < w) {
         Y[first + r] = v;
       } else {
-        U[c.f.sn_upd[J] + r - w] = front_rhs<T>(c, B, U, J, r, 0, false) - v;
+        const T g = kmax <= ST - TMV ? gb[tid] : front_rhs<T>(c, B, U, J, r, 0, false);
+        U[c.f.sn_upd[J] + r - w] = g - v;
       }
     }
   }
@@ -219,7 +255,17 @@ __device__ void vec_fwd_small(const SweepCtx &c, const T *panel, const T *B, T *
   const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
   const int first = c.f.sn_first[J];
   const T *P = panel + c.f.sn_panel[J];
-  const T fk = lane < w ? front_rhs<T>(c, B, U, J, lane, 0, true) : T(0);
+  // f_top entry of row lane (< w) and the update-row gathers of rows lane + 32 q (>= w)
+  int pos[3];
+  T gv[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const int r = lane + 32 * q;
+    pos[q] = r < m ? r : -1;
+    gv[q] = (r < w && B) ? B[first + r] : T(0);
+  }
+  gather_rows<T, 3>(c, U, c.f.sn_rowptr[J], pos, gv, 0);
+  const T fk = lane < w ? gv[0] : T(0);
   T acc[3] = {T(0), T(0), T(0)};
   for (int k0 = 0; k0 < w; k0 += 8) {  // 8 x 3 independent loads in flight per lane
     T v[3][8];
@@ -242,7 +288,7 @@ __device__ void vec_fwd_small(const SweepCtx &c, const T *panel, const T *B, T *
     const int r = lane + 32 * q;
     if (r >= m) continue;
     if (r < w) Y[first + r] = acc[q];
-    else U[c.f.sn_upd[J] + r - w] = front_rhs<T>(c, B, U, J, r, 0, false) - acc[q];
+    else U[c.f.sn_upd[J] + r - w] = gv[q] - acc[q];
   }
 }
 
@@ -288,8 +334,8 @@ struct Cfg {
   static constexpr int NCP = TC * CM;
 };
 
-// acc += As[0:kc, rows of this thread]^T Bs[0:kc, columns of this thread]; full chunks run
-// the fully unrolled loop, the last partial chunk a runtime-bounded one.
+// acc += As[0:kc, rows of this thread]^T Bs[0:kc, columns of this thread] (unrolled by 4:
+// full unrolling of every chunk made the kernel too large for the instruction cache).
 template <typename T, int TC, int CM, int RM>
 __device__ __forceinline__ void mac_chunk(const T *As, const T *Bs, int tc, int tr, int kc,
                                           T (&acc)[RM][CM]) {
@@ -306,12 +352,8 @@ __device__ __forceinline__ void mac_chunk(const T *As, const T *Bs, int tc, int 
 #pragma unroll
       for (int j = 0; j < CM; ++j) acc[i][j] += a[i] * b[j];
   };
-  if (kc == TK) {
-#pragma unroll
-    for (int k = 0; k < TK; ++k) step(k);
-  } else {
-    for (int k = 0; k < kc; ++k) step(k);
-  }
+#pragma unroll 4
+  for (int k = 0; k < kc; ++k) step(k);
 }
 
 // Forward tile: rows [r0, r0 + TM) of supernode J, all s columns, K = panel columns.
@@ -499,9 +541,11 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
         else blk_bwd_tile<T, TC, CM, RM>(c, panel, Y, X, a, b, sm);
       }
     }
-    __threadfence();
+    // the barrier orders every thread's writes before thread 0's device-scope fence, which
+    // publishes them before the completion counters move
     __syncthreads();
     if (threadIdx.x == 0 && s_ok) {
+      __threadfence();
       for (int q = 0; q < nmem; ++q) {
         const int J = b < 0 ? p.group_sn[a + q] : a;
         if (fwd) {
@@ -574,7 +618,7 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T
   if (s == 1) {
     require(p.vector, NSP_ERR_INVALID_ARG, "vector plan needed for one right-hand side");
     const size_t ldmax = (size_t)((p.max_m + 3) & ~3) + 8;
-    const size_t smem = sizeof(T) * std::max<size_t>(ldmax + 16 * 16 * (16 / sizeof(T)), 8 * 32 * 33);
+    const size_t smem = sizeof(T) * std::max<size_t>(ldmax + 17 * 16 * (16 / sizeof(T)), 8 * 32 * 33);
     dispatch<T, 1, 1, 1, true>(c, smem, panel, B, Y, U, X, stream, &grid);
     return grid;
   }
