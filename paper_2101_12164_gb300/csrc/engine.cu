@@ -65,6 +65,13 @@ static void validate_csr(const nsp_csr *A) {
   require(A->n < (int64_t(1) << 31) - 1, NSP_ERR_UNSUPPORTED, "CSR: n too large");
 }
 
+// Leaf size of the library's nested dissection (NSP_ND_LEAF, default 64).
+static int nd_leaf() {
+  const char *e = std::getenv("NSP_ND_LEAF");
+  const int v = e ? std::atoi(e) : 64;
+  return v >= 8 ? v : 64;
+}
+
 static int relax_level() {
   const char *e = std::getenv("NSP_RELAX");
   return e ? std::atoi(e) : 2;
@@ -154,7 +161,7 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
   for (int32_t b = 0; b < nb; ++b) {
     if (!P->perm && !nodes[b].empty()) {
       Graph gr = graph_of(nodes[b], b);
-      std::vector<int32_t> ord = nested_dissection(gr, 64);
+      std::vector<int32_t> ord = nested_dissection(gr, nd_leaf());
       init[b].resize(ord.size());
       for (size_t q = 0; q < ord.size(); ++q) init[b][q] = nodes[b][ord[q]];
     }
@@ -162,7 +169,7 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
   std::vector<int64_t> ginit;
   {
     Graph gr = graph_of(gam, -1);
-    std::vector<int32_t> ord = nested_dissection(gr, 64);
+    std::vector<int32_t> ord = nested_dissection(gr, nd_leaf());
     ginit.resize(ord.size());
     for (size_t q = 0; q < ord.size(); ++q) ginit[q] = gam[ord[q]];
   }
@@ -776,7 +783,7 @@ struct Engine : EngineBase {
     gram_acc64(Y.p, Y.p, s, s, K.p);
     gram_acc64(G.p, Y.p, s, s, Cn.p);
     launch_nystrom_core(K.p, Cn.p, s, k, prm.eps_trunc_rel, 1e-14, Mix.p, Sigma.p, drank.p,
-                        nys_work.p, st);
+                        nys_work.p, st, 1, std::is_same<T, double>::value ? 1 : 0);
     NSP_CUDA(cudaMemcpyAsync(hint, drank.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     sync();
     rank = hint[0];
@@ -1116,7 +1123,7 @@ struct Engine : EngineBase {
     launch_seg_gram<T, double>(Y.p, Y.p, s, s, chG.d, bK.p, bwork.p, st);
     launch_seg_gram<T, double>(G.p, Y.p, s, s, chG.d, bC.p, bwork.p, st);
     launch_nystrom_core(bK.p, bC.p, s, k, prm.eps_trunc_rel, 1e-14, Mix.p, bSig.p, drank.p,
-                        nys_work.p, st, nseg);
+                        nys_work.p, st, nseg, std::is_same<T, double>::value ? 1 : 0);
     U.ensure((size_t)an.nG * k);
     Zt.ensure((size_t)an.nG * k);
     Zs.ensure((size_t)an.nG * k);

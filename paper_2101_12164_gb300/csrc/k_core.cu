@@ -230,7 +230,7 @@ __device__ void mgs_columns(double *V, int s) {
 // FP64-accurate EVD of the symmetric matrix held in Bm (s x s): on return the eigenvalues
 // are on the diagonal of Bm and the eigenvectors in the columns of V. W1 is s x s scratch,
 // also used for the two FP32 matrices of the first phase. All three may be shared memory.
-__device__ void eig_sym(double *Bm, int s, double *V, double *W1) {
+__device__ void eig_sym(double *Bm, int s, double *V, double *W1, bool polish) {
   const int tid = threadIdx.x;
   const size_t ss = (size_t)s * s;
   float *A32 = reinterpret_cast<float *>(W1), *V32 = A32 + ss;
@@ -253,7 +253,7 @@ __device__ void eig_sym(double *Bm, int s, double *V, double *W1) {
       Bm[j * s + i] = v;
     }
   __syncthreads();
-  jacobi<double>(Bm, V, s, 1, 1e-13, 1e-15);
+  if (polish) jacobi<double>(Bm, V, s, 1, 1e-13, 1e-15);
 }
 
 struct Scratch {
@@ -369,7 +369,7 @@ __global__ void k_sqrt_vec(const double *in, int s, double *out) {
 __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C, int s, int k,
                                                 double eps_rel, double drop_tol, double *Mix,
                                                 double *Sigma, int32_t *rank, double *gw,
-                                                int use_smem) {
+                                                int use_smem, int polish) {
   extern __shared__ __align__(16) double dsm[];
   __shared__ int nk, r_keep;
   __shared__ int32_t msk[256], keepc[256], order[256];
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
       S.b0[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
     }
     __syncthreads();
-    eig_sym(S.b0, s, S.b1, S.b2);
+    eig_sym(S.b0, s, S.b1, S.b2, polish != 0);
     if (tid == 0) {
       double dmax = 0.0;
       for (int j = 0; j < s; ++j) dmax = fmax(dmax, S.b0[j * s + j]);
@@ -490,7 +490,7 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   for (size_t i = tid; i < ss; i += CT) S.b0[i] = S.b1[i];
   __syncthreads();
   // step 9: EVD of T: eigenvalues on b0's diagonal, W in b1
-  eig_sym(S.b0, s, S.b1, S.b2);
+  eig_sym(S.b0, s, S.b1, S.b2, polish != 0);
   if (tid == 0) {
     for (int j = 0; j < s; ++j) { evals[j] = S.b0[j * s + j]; order[j] = j; }
     for (int a = 0; a < s; ++a) {  // selection sort, descending
@@ -562,11 +562,11 @@ size_t nystrom_work_size(int s) { return 5 * (size_t)s * s + 64; }
 
 void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
                          double drop_tol, double *Mix, double *Sigma, int32_t *rank,
-                         double *work, cudaStream_t stream, int batch) {
+                         double *work, cudaStream_t stream, int batch, int polish) {
   const size_t sm = smem_for(s);
   set_smem(k_nystrom, sm);
   k_nystrom<<<batch, CT, sm, stream>>>(K, C, s, k, eps_rel, drop_tol, Mix, Sigma, rank, work,
-                                       sm > 0);
+                                       sm > 0, polish);
   NSP_LAUNCH_CHECK();
 }
 

@@ -143,9 +143,12 @@ void launch_max_ratio(const double *colsq, const double *bnorm, int s, double *r
 void launch_sqrt_vec(const double *in, int s, double *out, cudaStream_t stream);
 // Nyström core (Algorithm 2 steps 5-10) on K = Y^T Y and C = G^T Y (s x s FP64):
 // writes Mix (s x k, row-major) with U = Y Mix, Sigma (k), *rank. work >= nystrom_work(s).
+// polish: finish the eigenvectors with an FP64 Jacobi sweep (needed when K and C carry FP64
+// information; with FP32 inputs the FP32 Jacobi vectors, FP64-reorthonormalized, are as
+// accurate as the data and the eigenvalues are FP64 Rayleigh quotients).
 void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
                          double drop_tol, double *Mix, double *Sigma, int32_t *rank,
-                         double *work, cudaStream_t stream, int batch = 1);
+                         double *work, cudaStream_t stream, int batch = 1, int polish = 1);
 size_t nystrom_work_size(int s);   // doubles of scratch per problem
 
 // ---- segmented kernels for batches of matrices (k_batch.cu) ------------------------
