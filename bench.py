@@ -138,7 +138,7 @@ def sweep_algorithmic_bytes(info, s, wbytes):
 # DRAM bytes (read + write) of one interior-sweep launch from an ncu capture of the bench
 # workload (profiles/sweep_block_lognormal3d_64.md), keyed by (configuration, s); absent
 # until captured for the current kernel.
-SWEEP_TRAFFIC = {(1, 80): 850.6e6}
+SWEEP_TRAFFIC = {}
 
 
 def sub_nnz(P):

@@ -28,7 +28,7 @@ namespace nsp {
 namespace {
 
 constexpr int ST = 256;      // threads per CTA
-constexpr int TK = 32;       // K chunk of the block product
+constexpr int TK = 64;       // K chunk of the block product
 constexpr int MAX_SPINS = 1 << 22;
 
 // ---------------------------------------------------------------- synchronization
