@@ -50,6 +50,16 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(value, pg, device):
+    """The largest value over all ranks (a replicated job takes as long as its slowest rank)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -324,11 +334,7 @@ def main():
     if pg:
         pg.barrier()
     step_ms = [a.elapsed_time(bb) for a, bb in ev]
-    ms = float(np.mean(step_ms))
-    if pg:
-        t = torch.tensor([ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(step_ms)), pg, dev)
     res = float(np.linalg.norm(b - P.A @ x_d.cpu().numpy()) / np.linalg.norm(b))
 
     # ---- Schur block apply (s = k + p columns, the handle's precision): live timing

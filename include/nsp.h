@@ -302,6 +302,16 @@ nsp_status nsp_analyze(const nsp_csr *A, const nsp_partition *P, nsp_info *info)
 
 nsp_status nsp_get_info(const nsp_handle *h, nsp_info *info);
 nsp_status nsp_destroy(nsp_handle *h);
+/* Failure-detection check (no counterpart in the paper): runs one single-vector sweep of the
+ * handle's interior factor with every dependency made unreachable (its epoch moved 2^20
+ * launches ahead of the completion counters) and each wait bounded by max_spins polls
+ * (about 1 us each). The waits must run out: the sweep sets its abort flag, every CTA skips
+ * its remaining items, the kernel returns and records a device timeout. *observed receives
+ * the status the sweep reported (NSP_ERR_TIMEOUT when the path works). The plan's counters
+ * and the device status are reset afterwards, so the handle stays usable. No GPU fault, trap
+ * or hang is involved. */
+nsp_status nsp_check_timeout_path(const nsp_handle *h, int32_t max_spins, int32_t *observed);
+
 /* Message of the last failed call made on the calling thread ("" if none); valid until
  * the next failing call on that thread. */
 const char *nsp_last_error(void);

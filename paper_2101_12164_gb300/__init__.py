@@ -27,7 +27,7 @@ EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_s
            "nsp_analyze", "nsp_kernel_launches", "nsp_schur_apply_noalloc", "nsp_build_batched",
            "nsp_solve_batched", "nsp_net_num_params", "nsp_net_create", "nsp_net_set_params",
            "nsp_net_get", "nsp_net_forward", "nsp_net_loss_grad", "nsp_net_zero_grad",
-           "nsp_net_adam_step", "nsp_net_sketch", "nsp_net_destroy"]
+           "nsp_net_adam_step", "nsp_net_sketch", "nsp_net_destroy", "nsp_check_timeout_path"]
 
 
 class NspError(RuntimeError):
@@ -120,6 +120,7 @@ def lib():
             "nsp_net_adam_step": (C.c_int, [P, C.c_double, C.c_double, C.c_double, C.c_double]),
             "nsp_net_sketch": (C.c_int, [P, P, C.c_int64, P, C.POINTER(C.c_int32)]),
             "nsp_net_destroy": (C.c_int, [P]),
+            "nsp_check_timeout_path": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -382,6 +383,13 @@ class Handle:
         if not (st == 0 or (allow_not_converged and st == 5)):
             _check(st, "nsp_solve_batched")
         return [infos[i].as_dict() for i in range(self.batch)]
+
+    def check_timeout_path(self, max_spins=1 << 14):
+        """Status a sweep with unreachable dependencies reports (see nsp_check_timeout_path)."""
+        obs = C.c_int32(-1)
+        _check(lib().nsp_check_timeout_path(self._handle(), int(max_spins), C.byref(obs)),
+               "nsp_check_timeout_path")
+        return obs.value
 
     def schur_apply(self, X, Y):
         s = 1 if X.dim() == 1 else X.shape[1]

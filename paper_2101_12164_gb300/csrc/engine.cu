@@ -423,6 +423,7 @@ struct EngineBase {
   virtual void solve_batched(const double *b, double *x, double rtol, int maxit) = 0;
   std::vector<nsp_info> binfo;     // per matrix of a batched handle
   virtual size_t schur_noalloc_bytes(int s) const = 0;
+  virtual nsp_status timeout_selftest(int max_spins) = 0;
   virtual void schur_apply_noalloc(const void *X, void *Y, int s, unsigned char *scratch) = 0;
   virtual void factor_solve_user(int which, const void *B, void *X, int s) = 0;
   virtual void get_basis(double *Z, double *Sigma, int32_t *rank) = 0;
@@ -1336,6 +1337,30 @@ struct Engine : EngineBase {
     if (!ok) throw Error(NSP_ERR_NOT_CONVERGED, "outer PCG did not converge for every matrix");
   }
 
+  // Failure-detection check of the sweeps, on the handle's own interior forest: the plan's
+  // epoch is moved 2^20 launches ahead of its counters, so every dependency wait of one sweep
+  // is unreachable; the bounded waits (max_spins polls) must run out, abort the launch and
+  // record DEV_TIMEOUT. The plan's counters and the status word are then reset, so the
+  // handle stays usable. Returns the status the sweep reported.
+  nsp_status timeout_selftest(int max_spins) override {
+    auto &P = FI.plan(true, st);
+    ensure_ws(1);
+    sT.ensure(std::max(an.nI, an.nG));
+    sT2.ensure(std::max(an.nI, an.nG));
+    NSP_CUDA(cudaMemsetAsync(sT.p, 0, an.nI * sizeof(T), st));
+    NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
+    const uint32_t far = 1u << 20;
+    NSP_CUDA(cudaMemcpyAsync(P.d.epoch, &far, sizeof(uint32_t), cudaMemcpyHostToDevice, st));
+    launch_sweep<T>(FI.dev, P.d, panelI.p, sT.p, Yw.p, Uw.p, sT2.p, 1, dstat.p, st, 0, max_spins);
+    NSP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+    sync();
+    const int32_t code = hstat->code;
+    NSP_CUDA(cudaMemsetAsync(P.counters.p, 0, P.counters.bytes(), st));
+    NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
+    sync();
+    return code == DEV_TIMEOUT ? NSP_ERR_TIMEOUT : code == DEV_OK ? NSP_OK : NSP_ERR_CUDA;
+  }
+
   // ---- caller-order wrappers (asynchronous on the handle's stream, no allocation after
   // the first call with a given width)
   DBuf<T> io_a, io_b;
@@ -1672,6 +1697,11 @@ nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device, cons
     else
       h->eng->construct(h->prm);
   });
+}
+
+nsp_status nsp_check_timeout_path(const nsp_handle *h, int32_t max_spins, int32_t *observed) {
+  if (!h || !h->eng || !observed || max_spins < 1) return NSP_ERR_INVALID_ARG;
+  return guard([&] { *observed = h->eng->timeout_selftest(max_spins); });
 }
 
 nsp_status nsp_apply(const nsp_handle *h, const double *r, double *z) {

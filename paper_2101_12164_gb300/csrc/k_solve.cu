@@ -29,7 +29,7 @@ namespace {
 
 constexpr int ST = 256;      // threads per CTA
 constexpr int TK = 64;       // K chunk of the block product
-constexpr int MAX_SPINS = 1 << 22;
+constexpr int MAX_SPINS = 1 << 22;  // default bound of a dependency wait (seconds at most)
 
 // ---------------------------------------------------------------- synchronization
 __device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
@@ -46,11 +46,11 @@ __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t *p) {
 // Thread 0 waits until *p >= target (modulo 2^32). Returns false (and sets the abort flag)
 // on timeout or when another CTA has aborted.
 __device__ bool wait_geq(const uint32_t *p, uint32_t target, uint32_t *abort_flag, DevStatus *st,
-                         int32_t where) {
+                         int32_t where, int max_spins) {
   int spins = 0;
   while ((int32_t)(ld_acquire(p) - target) < 0) {
     if (ld_relaxed(abort_flag)) return false;
-    if (++spins > MAX_SPINS) {
+    if (++spins > max_spins) {
       atomicExch(abort_flag, 1u);
       dev_fail(st, DEV_TIMEOUT, where);
       return false;
@@ -91,6 +91,7 @@ struct SweepCtx {
   SweepPlan p;
   int s;
   DevStatus *st;
+  int max_spins;
 };
 
 // f_top / f_bot entry k of supernode J (column b, s columns): B row + children's update rows
@@ -514,12 +515,15 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
       for (int q = 0; q < nmem && ok; ++q) {
         const int J = b < 0 ? p.group_sn[a + q] : a;
         if (fwd) {
-          ok = wait_geq(&p.cnt_f[J], epoch * (uint32_t)p.need_f[J], p.abort_flag, c.st, J);
+          ok = wait_geq(&p.cnt_f[J], epoch * (uint32_t)p.need_f[J], p.abort_flag, c.st, J,
+                        c.max_spins);
         } else {
           const int par = p.sn_parent[J];
           ok = par >= 0
-                   ? wait_geq(&p.done_b[par], epoch * (uint32_t)p.units_b[par], p.abort_flag, c.st, J)
-                   : wait_geq(&p.self_f[J], epoch * (uint32_t)p.units_f[J], p.abort_flag, c.st, J);
+                   ? wait_geq(&p.done_b[par], epoch * (uint32_t)p.units_b[par], p.abort_flag,
+                              c.st, J, c.max_spins)
+                   : wait_geq(&p.self_f[J], epoch * (uint32_t)p.units_f[J], p.abort_flag, c.st,
+                              J, c.max_spins);
         }
       }
       s_ok = ok;
@@ -610,8 +614,8 @@ int sweep_vector_rows(int elem_bytes) { return 16 * (16 / elem_bytes); }
 
 template <typename T>
 int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y, T *U,
-                 T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req) {
-  SweepCtx c{f, p, s, st};
+                 T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req, int max_spins) {
+  SweepCtx c{f, p, s, st, max_spins > 0 ? max_spins : MAX_SPINS};
   int grid = grid_req;
   k_sweep_begin<<<1, 32, 0, stream>>>(p);
   NSP_LAUNCH_CHECK();
@@ -641,9 +645,9 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T
 
 template int launch_sweep<float>(const ForestDev &, const SweepPlan &, const float *,
                                  const float *, float *, float *, float *, int, DevStatus *,
-                                 cudaStream_t, int);
+                                 cudaStream_t, int, int);
 template int launch_sweep<double>(const ForestDev &, const SweepPlan &, const double *,
                                   const double *, double *, double *, double *, int, DevStatus *,
-                                  cudaStream_t, int);
+                                  cudaStream_t, int, int);
 
 }  // namespace nsp

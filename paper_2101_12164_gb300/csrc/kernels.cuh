@@ -64,9 +64,13 @@ constexpr int kBigFront = 192;   // fronts with m >= kBigFront use the cluster k
 // advances by nitems + grid).
 // Returns the grid used: grid_req CTAs (rounded to the SM count, capped by occupancy) or,
 // when grid_req <= 0, the occupancy maximum (at most 4 CTAs per SM).
+// max_spins bounds every dependency wait (0: the default, a few seconds at most); a wait that
+// runs out sets the plan's abort flag (every CTA then skips its remaining items) and records
+// DEV_TIMEOUT.
 template <typename T>
 int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y, T *U,
-                 T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req = 0);
+                 T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req = 0,
+                 int max_spins = 0);
 // rows of a forward tile in vector mode for elements of elem_bytes
 int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
