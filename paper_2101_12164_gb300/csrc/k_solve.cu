@@ -357,15 +357,149 @@ __device__ __forceinline__ void mac_chunk(const T *As, const T *Bs, int tc, int 
   for (int k = 0; k < kc; ++k) step(k);
 }
 
+// Staging of one K chunk. In-order issue stalls a thread at the first use of a load, so
+// every staging step first issues all its independent loads into registers and only then
+// writes shared memory: the panel tile (NA values per thread), and the right-hand-side rows
+// of a warp (RB rows x CPW columns per lane; row indices, first gather sources, values in
+// three waves). Sums are formed in the same order as one row at a time would.
+template <typename T, int TM>
+__device__ __forceinline__ void stage_panel_fwd(const T *P, int ld, int m, int r0, int k0, int kc,
+                                                T *As) {
+  constexpr int NA = (TK * TM + ST - 1) / ST;
+  T av[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const int i = threadIdx.x + q * ST, r = i % TM, k = i / TM;
+    av[q] = (k < kc && r0 + r < m) ? __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]) : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const int i = threadIdx.x + q * ST, r = i % TM, k = i / TM;
+    if (k < kc) As[k * (TM + 1) + r] = av[q];
+  }
+}
+
+template <typename T, int TM>
+__device__ __forceinline__ void stage_panel_bwd(const T *P, int ld, int r0, int r1, int k0, int kc,
+                                                T *As) {
+  constexpr int NA = (TK * TM + ST - 1) / ST;
+  T av[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const int i = threadIdx.x + q * ST, k = i % TK, r = i / TK;
+    av[q] = (k < kc && r0 + r < r1) ? __ldg(&P[(size_t)(k0 + k) + (size_t)(r0 + r) * ld]) : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    const int i = threadIdx.x + q * ST, k = i % TK, r = i / TK;
+    if (k < kc) As[k * (TM + 1) + r] = av[q];
+  }
+}
+
+// f rows k0 + [0, kc) of supernode J: b + the children's update rows landing there
+template <typename T, int NCP>
+__device__ __forceinline__ void stage_f(const SweepCtx &c, const T *B, const T *U, int64_t rp,
+                                        int first, int k0, int kc, T *Bs) {
+  constexpr int NW = ST / 32, CPW = (NCP + 31) / 32, RB = CPW >= 8 ? 2 : 24 / CPW;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int s = c.s;
+  for (int kb = wid; kb < kc; kb += NW * RB) {
+    int32_t e0[RB], e1[RB];
+    T v[RB][CPW];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int k = kb + q * NW;
+      const bool on = k < kc;
+      e0[q] = on ? (int32_t)c.f.gptr[rp + k0 + k] : 0;
+      e1[q] = on ? (int32_t)c.f.gptr[rp + k0 + k + 1] : 0;
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        const int col = lane + 32 * j;
+        v[q][j] = (on && B && col < s) ? B[(size_t)(first + k0 + k) * s + col] : T(0);
+      }
+    }
+    int64_t src[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) src[q] = e0[q] < e1[q] ? c.f.gsrc[e0[q]] : -1;
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      if (src[q] >= 0) {
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          const int col = lane + 32 * j;
+          if (col < s) v[q][j] += __ldcg(&U[(size_t)src[q] * s + col]);
+        }
+      }
+#pragma unroll
+    for (int q = 0; q < RB; ++q)
+      for (int e = e0[q] + 1; e < e1[q]; ++e) {
+        const int64_t sr = c.f.gsrc[e];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          const int col = lane + 32 * j;
+          if (col < s) v[q][j] += __ldcg(&U[(size_t)sr * s + col]);
+        }
+      }
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int k = kb + q * NW;
+      if (k < kc) {
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          const int col = lane + 32 * j;
+          if (col < NCP) Bs[k * NCP + col] = v[q][j];
+        }
+      }
+    }
+  }
+}
+
+// g rows k0 + [0, kc) of supernode J for the backward sweep: y of its own rows, -x below
+template <typename T, int NCP>
+__device__ __forceinline__ void stage_g(const SweepCtx &c, const T *Y, const T *X, int64_t rp,
+                                        int first, int w, int k0, int kc, T *Bs) {
+  constexpr int NW = ST / 32, CPW = (NCP + 31) / 32, RB = CPW >= 8 ? 2 : 24 / CPW;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int s = c.s;
+  for (int kb = wid; kb < kc; kb += NW * RB) {
+    int64_t row[RB];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int k = kb + q * NW, kk = k0 + k;
+      row[q] = k >= kc ? -1 : kk < w ? (int64_t)(first + kk) : (int64_t)c.f.rows[rp + kk];
+    }
+    T v[RB][CPW];
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int kk = k0 + kb + q * NW;
+      const T *src = kk < w ? Y : X;
+#pragma unroll
+      for (int j = 0; j < CPW; ++j) {
+        const int col = lane + 32 * j;
+        v[q][j] = (row[q] >= 0 && col < s) ? __ldcg(&src[(size_t)row[q] * s + col]) : T(0);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RB; ++q) {
+      const int k = kb + q * NW;
+      if (k < kc) {
+        const T sg = k0 + k < w ? T(1) : T(-1);
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+          const int col = lane + 32 * j;
+          if (col < NCP) Bs[k * NCP + col] = sg * v[q][j];
+        }
+      }
+    }
+  }
+}
+
 // Forward tile: rows [r0, r0 + TM) of supernode J, all s columns, K = panel columns.
-// The gathered front right-hand side f (b + children's update rows) is staged a warp per
-// front position (uniform index loads, lanes over columns); the panel tile is staged along
-// its contiguous rows. Two block barriers per K chunk.
 template <typename T, int TC, int CM, int RM>
 __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *B, T *Y,
                              T *U, int J, int r0, T *sm) {
   using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP, NW = ST / 32;
+  constexpr int TM = C::TM, NCP = C::NCP;
   static_assert((TM & (TM - 1)) == 0, "tile rows must be a power of two");
   T *As = sm;                  // [TK][TM + 1]
   T *Bs = As + TK * (TM + 1);  // [TK][NCP]
@@ -377,7 +511,6 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
   const int r1 = min(r0 + TM, m);
   const int kmax = (r1 <= w) ? r1 : w;
   const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
-  const int lane = tid & 31, wid = tid >> 5;
   T acc[RM][CM];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
@@ -385,28 +518,26 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
   for (int k0 = 0; k0 < kmax; k0 += TK) {
     const int kc = min(TK, kmax - k0);
-    for (int i = tid; i < kc * TM; i += ST) {
-      const int r = i % TM, k = i / TM;
-      As[k * (TM + 1) + r] = (r0 + r < m) ? __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]) : T(0);
-    }
-    for (int k = wid; k < kc; k += NW) {
-      const int64_t e0 = c.f.gptr[rp + k0 + k], e1 = c.f.gptr[rp + k0 + k + 1];
-      const size_t brow = (size_t)(first + k0 + k) * s;
-      for (int col = lane; col < NCP; col += 32) {
-        T v = T(0);
-        if (col < s) {
-          if (B) v = B[brow + col];
-          for (int64_t e = e0; e < e1; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[e] * s + col]);
-        }
-        Bs[k * NCP + col] = v;
-      }
-    }
+    stage_panel_fwd<T, TM>(P, ld, m, r0, k0, kc, As);
+    stage_f<T, NCP>(c, B, U, rp, first, k0, kc, Bs);
     __syncthreads();
     if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
     __syncthreads();
   }
-  // epilogue: y rows, or update rows u = f_bot - P_bot f_top
+  // epilogue: y rows, or update rows u = f_bot - P_bot f_top (gathers of the thread's rows
+  // issued together)
   const int64_t upd = c.f.sn_upd[J];
+  int32_t e0[RM], e1[RM];
+  int64_t src[RM];
+#pragma unroll
+  for (int i = 0; i < RM; ++i) {
+    const int r = r0 + tr * RM + i;
+    const bool bot = r < r1 && r >= w;
+    e0[i] = bot ? (int32_t)c.f.gptr[rp + r] : 0;
+    e1[i] = bot ? (int32_t)c.f.gptr[rp + r + 1] : 0;
+  }
+#pragma unroll
+  for (int i = 0; i < RM; ++i) src[i] = e0[i] < e1[i] ? c.f.gsrc[e0[i]] : -1;
 #pragma unroll
   for (int i = 0; i < RM; ++i) {
     const int r = r0 + tr * RM + i;
@@ -418,13 +549,12 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
         if (col < s) Y[(size_t)(first + r) * s + col] = acc[i][j];
       }
     } else {
-      const int64_t e0 = c.f.gptr[rp + r], e1 = c.f.gptr[rp + r + 1];
 #pragma unroll
       for (int j = 0; j < CM; ++j) {
         const int col = tc + TC * j;
         if (col < s) {
-          T v = T(0);
-          for (int64_t e = e0; e < e1; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[e] * s + col]);
+          T v = src[i] >= 0 ? __ldcg(&U[(size_t)src[i] * s + col]) : T(0);
+          for (int e = e0[i] + 1; e < e1[i]; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[e] * s + col]);
           U[(size_t)(upd + r - w) * s + col] = v - acc[i][j];
         }
       }
@@ -433,12 +563,12 @@ __device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
 }
 
 // Backward tile: x rows [r0, r0 + TM) of supernode J (rows of its own columns), all s
-// columns, K over the m front positions: g = [y_top; -x_bot] staged a warp per position.
+// columns, K over the m front positions.
 template <typename T, int TC, int CM, int RM>
 __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *Y, T *X,
                              int J, int r0, T *sm) {
   using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP, NW = ST / 32;
+  constexpr int TM = C::TM, NCP = C::NCP;
   T *As = sm;
   T *Bs = As + TK * (TM + 1);
   const int s = c.s;
@@ -448,7 +578,6 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
   const T *P = panel + c.f.sn_panel[J];
   const int r1 = min(r0 + TM, w);
   const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
-  const int lane = tid & 31, wid = tid >> 5;
   T acc[RM][CM];
 #pragma unroll
   for (int i = 0; i < RM; ++i)
@@ -456,18 +585,8 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
     for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
   for (int k0 = r0; k0 < m; k0 += TK) {
     const int kc = min(TK, m - k0);
-    for (int i = tid; i < TK * TM; i += ST) {
-      const int k = i % TK, r = i / TK;
-      if (k < kc)
-        As[k * (TM + 1) + r] = (r0 + r < r1) ? __ldg(&P[(size_t)(k0 + k) + (size_t)(r0 + r) * ld]) : T(0);
-    }
-    for (int k = wid; k < kc; k += NW) {
-      const int kk = k0 + k;
-      const T *src = kk < w ? Y + (size_t)(first + kk) * s : X + (size_t)c.f.rows[rp + kk] * s;
-      const T sg = kk < w ? T(1) : T(-1);
-      for (int col = lane; col < NCP; col += 32)
-        Bs[k * NCP + col] = col < s ? sg * __ldcg(&src[col]) : T(0);
-    }
+    stage_panel_bwd<T, TM>(P, ld, r0, r1, k0, kc, As);
+    stage_g<T, NCP>(c, Y, X, rp, first, w, k0, kc, Bs);
     __syncthreads();
     if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
     __syncthreads();

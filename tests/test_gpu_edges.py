@@ -51,9 +51,11 @@ def test_widest_sketch_block(N, torch):
     A, part, _ = tiny_problem((80, 80), 16, (3.0, 1.0), seed=2)
     h, D, M = _parity(N, torch, A, part, 16, 200, 56)
     Z, S = h.get_basis()
-    assert np.allclose(S, M.Sigma, rtol=1e-8)
-    # the tail of the 200 kept eigenvalues is clustered (relative gaps ~1e-2), so the kept
-    # eigenvectors carry rounding of order eps * cond / gap: agreement 1e-5 as an operator
+    # 256-column inner block PCG and Nyström core in FP64 on both sides, with different
+    # factor orderings and Cholesky-QR variants (equal in exact arithmetic): the eigenvalues
+    # agree to 1e-7; the tail of the 200 kept eigenvalues is clustered (relative gaps ~1e-2),
+    # so the eigenvectors carry rounding of order eps * cond / gap: 1e-5 as an operator
+    assert np.allclose(S, M.Sigma, rtol=1e-7)
     assert _rel((Z * S) @ Z.T, (M.Z * M.Sigma) @ M.Z.T) < 1e-5
     h.destroy()
 
