@@ -22,6 +22,12 @@ namespace nsp {
 namespace {
 
 constexpr int FT = 256;  // threads per CTA
+// resident CTAs per SM the register budget is sized for: the small FP32 fronts of the lower
+// tree levels are latency bound and gain from more CTAs per SM; FP64 keeps one
+template <typename T>
+struct FactorOcc {
+  static constexpr int value = sizeof(T) == 4 ? 3 : 1;
+};
 constexpr int NB = 32;   // column block of the blocked factorization
 constexpr int TT = 64;   // output tile of the trailing update / row tile of the inverse
 
@@ -75,6 +81,24 @@ __device__ void diag_block_cholesky(FactorSmem<T> &sm, int nb, int32_t blk, DevS
   }
 }
 
+// stage the lower triangle of the nb x nb diagonal block at (kb, kb) of F into D, all loads
+// in flight before the shared-memory writes
+template <typename T>
+__device__ __forceinline__ void stage_diag(const T *F, int m, int kb, int nb, FactorSmem<T> &sm) {
+  constexpr int NQ = NB * NB / FT;
+  T v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = threadIdx.x + q * FT, r = i % NB, c = i / NB;
+    v[q] = (r < nb && c < nb && r >= c) ? F[(size_t)(kb + r) + (size_t)(kb + c) * m] : T(0);
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int i = threadIdx.x + q * FT;
+    sm.D[i % NB][i / NB] = v[q];
+  }
+}
+
 // Right-looking blocked partial Cholesky of the first w columns of F (m x m).
 template <typename T, int NC>
 __device__ void partial_cholesky(T *F, int m, int w, int32_t blk, DevStatus *st,
@@ -83,10 +107,7 @@ __device__ void partial_cholesky(T *F, int m, int w, int32_t blk, DevStatus *st,
   const int rank = front_rank<NC>();
   for (int kb = 0; kb < w; kb += NB) {
     const int nb = min(NB, w - kb);
-    for (int i = tid; i < NB * NB; i += FT) {
-      const int r = i % NB, c = i / NB;
-      sm.D[r][c] = (r < nb && c < nb && r >= c) ? F[(size_t)(kb + r) + (size_t)(kb + c) * m] : T(0);
-    }
+    stage_diag(F, m, kb, nb, sm);
     __syncthreads();
     diag_block_cholesky(sm, nb, blk, st, rank == 0);
     // rows below the diagonal block: L[r, kb:kb+nb] = F[r, kb:kb+nb] Ld^{-T}
@@ -126,15 +147,21 @@ __device__ void partial_cholesky(T *F, int m, int w, int32_t blk, DevStatus *st,
         while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
         const int tj = tile - ti * (ti + 1) / 2;
         const int rb = c0 + ti * TT, cb = c0 + tj * TT;
-        for (int i = tid; i < TT * NB; i += FT) {
-          const int rr = i % TT, t = i / TT;
-          T a = T(0), b = T(0);
-          if (t < nb) {
-            if (rb + rr < m) a = F[(size_t)(rb + rr) + (size_t)(kb + t) * m];
-            if (cb + rr < m) b = F[(size_t)(cb + rr) + (size_t)(kb + t) * m];
+        {
+          constexpr int NQ = TT * NB / FT;  // every load of the two tiles in flight together
+          T a[NQ], b[NQ];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int i = tid + q * FT, rr = i % TT, t = i / TT;
+            a[q] = (t < nb && rb + rr < m) ? F[(size_t)(rb + rr) + (size_t)(kb + t) * m] : T(0);
+            b[q] = (t < nb && cb + rr < m) ? F[(size_t)(cb + rr) + (size_t)(kb + t) * m] : T(0);
           }
-          sm.Lr[rr][t] = a;
-          sm.Lc[rr][t] = b;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int i = tid + q * FT, rr = i % TT, t = i / TT;
+            sm.Lr[rr][t] = a[q];
+            sm.Lc[rr][t] = b[q];
+          }
         }
         __syncthreads();
         T acc[4][4];
@@ -153,12 +180,22 @@ __device__ void partial_cholesky(T *F, int m, int w, int32_t blk, DevStatus *st,
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
         }
+        // read-modify-write of the 16 entries: every read issued before the first write (the
+        // compiler cannot reorder loads past stores into the same array by itself)
+        T cur[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             const int r = rb + tx + 16 * i, c = cb + ty + 16 * j;
-            if (r < m && c < m && r >= c) F[(size_t)r + (size_t)c * m] -= acc[i][j];
+            cur[i][j] = (r < m && c < m && r >= c) ? F[(size_t)r + (size_t)c * m] : T(0);
+          }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int r = rb + tx + 16 * i, c = cb + ty + 16 * j;
+            if (r < m && c < m && r >= c) F[(size_t)r + (size_t)c * m] = cur[i][j] - acc[i][j];
           }
         __syncthreads();
       }
@@ -190,10 +227,7 @@ __device__ void inverse_panel(const T *F, T *P, int m, int w, FactorSmem<T> &sm)
     const int jb = bi * NB;
     const int nb = min(NB, w - jb);
     __syncthreads();
-    for (int i = tid; i < NB * NB; i += FT) {
-      const int r = i % NB, c = i / NB;
-      sm.D[r][c] = (r < nb && c < nb && r >= c) ? F[(size_t)(jb + r) + (size_t)(jb + c) * m] : T(0);
-    }
+    stage_diag(F, m, jb, nb, sm);
     __syncthreads();
     const int tfirst = jb / TT;  // rows < jb of these columns are zero (upper triangle)
     for (int t = tfirst; t < ntile; ++t) {
@@ -213,14 +247,29 @@ __device__ void inverse_panel(const T *F, T *P, int m, int w, FactorSmem<T> &sm)
       for (int cc = jb + nb; cc < w; cc += NB) {
         const int cn = min(NB, w - cc);
         __syncthreads();
-        for (int i = tid; i < TT * NB; i += FT) {
-          const int rr = i % TT, k = i / TT;
-          const int r = r0 + rr;
-          sm.Lr[rr][k] = (k < cn && r < m) ? P[(size_t)r + (size_t)(cc + k) * ld] : T(0);
-        }
-        for (int i = tid; i < NB * NB; i += FT) {
-          const int k = i % NB, c = i / NB;
-          sm.Lc[k][c] = (k < cn && c < nb) ? F[(size_t)(cc + k) + (size_t)(jb + c) * m] : T(0);
+        {
+          constexpr int NQ = TT * NB / FT, NQ2 = NB * NB / FT;
+          T a[NQ], b[NQ2];
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int i = tid + q * FT, rr = i % TT, k = i / TT, r = r0 + rr;
+            a[q] = (k < cn && r < m) ? P[(size_t)r + (size_t)(cc + k) * ld] : T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < NQ2; ++q) {
+            const int i = tid + q * FT, k = i % NB, c = i / NB;
+            b[q] = (k < cn && c < nb) ? F[(size_t)(cc + k) + (size_t)(jb + c) * m] : T(0);
+          }
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            const int i = tid + q * FT;
+            sm.Lr[i % TT][i / TT] = a[q];
+          }
+#pragma unroll
+          for (int q = 0; q < NQ2; ++q) {
+            const int i = tid + q * FT;
+            sm.Lc[i % NB][i / NB] = b[q];
+          }
         }
         __syncthreads();
         for (int k = 0; k < cn; ++k) {
@@ -275,17 +324,42 @@ __device__ void factor_front(const ForestDev &f, int J, const double *Aval, T *f
   const int gt = rank * FT + tid;
   for (size_t i = gt; i < (size_t)m * m; i += NC * FT) F[i] = T(0);
   front_sync<NC>();
-  for (int64_t e = f.asm_ptr[J] + gt; e < f.asm_ptr[J + 1]; e += NC * FT)
-    F[f.asm_dst[e]] = (T)Aval[f.asm_src[e]];
+  {  // A's entries of J's columns, four per thread in flight
+    const int64_t a0 = f.asm_ptr[J], a1 = f.asm_ptr[J + 1];
+    for (int64_t e = a0 + gt; e < a1; e += 4 * NC * FT) {
+      int64_t dst[4];
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t ee = e + (int64_t)u * NC * FT;
+        dst[u] = ee < a1 ? f.asm_dst[ee] : -1;
+        v[u] = ee < a1 ? Aval[f.asm_src[ee]] : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (dst[u] >= 0) F[dst[u]] = (T)v[u];
+    }
+  }
   for (int ci = f.ch_ptr[J]; ci < f.ch_ptr[J + 1]; ++ci) {
     front_sync<NC>();
     const int C = f.ch_list[ci];
     const int wc = f.sn_w[C], mc = f.sn_m[C], mu = mc - wc;
     const T *FC = front + f.sn_front[C];
     const int32_t *rm = f.relmap + f.sn_upd[C];
-    for (int idx = gt; idx < mu * mu; idx += NC * FT) {
-      const int a = idx % mu, b = idx / mu;
-      if (a >= b) F[(size_t)rm[a] + (size_t)rm[b] * m] += FC[(size_t)(wc + a) + (size_t)(wc + b) * mc];
+    for (int idx0 = gt; idx0 < mu * mu; idx0 += 4 * NC * FT) {  // four entries in flight
+      int64_t dst[4];
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = idx0 + u * NC * FT;
+        const int a = idx % mu, b = idx / mu;
+        const bool on = idx < mu * mu && a >= b;
+        dst[u] = on ? (int64_t)rm[a] + (int64_t)rm[b] * m : -1;
+        v[u] = on ? FC[(size_t)(wc + a) + (size_t)(wc + b) * mc] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (dst[u] >= 0) F[dst[u]] += v[u];
     }
   }
   front_sync<NC>();
@@ -294,7 +368,7 @@ __device__ void factor_front(const ForestDev &f, int J, const double *Aval, T *f
 }
 
 template <typename T>
-__global__ void __launch_bounds__(FT) k_factor(ForestDev f, const int32_t *level_sn,
+__global__ void __launch_bounds__(FT, FactorOcc<T>::value) k_factor(ForestDev f, const int32_t *level_sn,
                                                const double *Aval, T *front, T *panel,
                                                DevStatus *st) {
   __shared__ FactorSmem<T> sm;
@@ -304,7 +378,7 @@ __global__ void __launch_bounds__(FT) k_factor(ForestDev f, const int32_t *level
 constexpr int CLUSTER = 8;
 
 template <typename T>
-__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(FT)
+__global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(FT, FactorOcc<T>::value)
     k_factor_cluster(ForestDev f, const int32_t *level_sn, const double *Aval, T *front,
                      T *panel, DevStatus *st) {
   __shared__ FactorSmem<T> sm;

@@ -149,7 +149,20 @@ __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y
   T *red = sm + ((ld + 3) & ~3);   // [16][TMV]
   T *gb = red + 16 * TMV;          // [TMV] update-row gathers of the tile's rows
   const int tid = threadIdx.x;
-  for (int k = tid; k < kmax; k += ST) fs[k] = front_rhs<T>(c, B, U, J, k, 0, true);
+  for (int kb = tid; kb < kmax; kb += 3 * ST) {  // three positions' gathers in flight
+    int pos[3];
+    T v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int k = kb + q * ST;
+      pos[q] = k < kmax ? k : -1;
+      v[q] = (k < kmax && B) ? B[first + k] : T(0);
+    }
+    gather_rows<T, 3>(c, U, c.f.sn_rowptr[J], pos, v, 0);
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (kb + q * ST < kmax) fs[kb + q * ST] = v[q];
+  }
   if (kmax <= ST - TMV && tid >= ST - TMV) {  // otherwise idle threads gather concurrently
     const int i = tid - (ST - TMV), r = r0 + i;
     int pos[1] = {(r >= w && r < r1) ? r : -1};
@@ -216,11 +229,22 @@ __device__ void vec_bwd_tile(const SweepCtx &c, const T *panel, const T *Y, T *X
   const int kbeg = c0 & ~(VN - 1);
   T *g = sm;  // [ld]
   const int tid = threadIdx.x;
-  for (int k = kbeg + tid; k < ld; k += ST) {
-    T v = T(0);
-    if (k < w) v = __ldcg(&Y[first + k]);
-    else if (k < m) v = -__ldcg(&X[c.f.rows[rp + k]]);
-    g[k] = v;
+  for (int kb = kbeg + tid; kb < ld; kb += 3 * ST) {  // indices, then values, in flight
+    int64_t row[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int k = kb + q * ST;
+      row[q] = k < w ? (int64_t)(first + k) : k < m ? (int64_t)c.f.rows[rp + k] : -1;
+    }
+    T v[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int k = kb + q * ST;
+      v[q] = row[q] < 0 ? T(0) : k < w ? __ldcg(&Y[row[q]]) : -__ldcg(&X[row[q]]);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      if (kb + q * ST < ld) g[kb + q * ST] = v[q];
   }
   __syncthreads();
   const int lane = tid & 31, wid = tid >> 5;
