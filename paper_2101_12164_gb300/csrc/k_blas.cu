@@ -82,12 +82,22 @@ __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
   for (int i = 0; i < RT; ++i)
 #pragma unroll
     for (int j = 0; j < RT; ++j) acc[i][j] = AccT(0);
+  static_assert((GR * TS) % BT == 0, "staging tile must split evenly over the threads");
+  constexpr int NQ = GR * TS / BT;
   for (int64_t ib = i0; ib < i1; ib += GR) {
-    for (int q = tid; q < GR * TS; q += BT) {
-      const int r = q / TS, c = q % TS;
+    T xv[NQ], yv[NQ];  // every load of the two tiles in flight before the shared stores
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int q = tid + u * BT, r = q / TS, c = q % TS;
       const int64_t row = ib + r;
-      Xs[r][c] = (row < i1 && a0 + c < s1) ? X[(size_t)row * s1 + a0 + c] : T(0);
-      Ys[r][c] = (row < i1 && b0 + c < s2) ? Y[(size_t)row * s2 + b0 + c] : T(0);
+      xv[u] = (row < i1 && a0 + c < s1) ? X[(size_t)row * s1 + a0 + c] : T(0);
+      yv[u] = (row < i1 && b0 + c < s2) ? Y[(size_t)row * s2 + b0 + c] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int q = tid + u * BT;
+      Xs[q / TS][q % TS] = xv[u];
+      Ys[q / TS][q % TS] = yv[u];
     }
     __syncthreads();
 #pragma unroll 4
@@ -192,13 +202,30 @@ __global__ void __launch_bounds__(BT) k_block_update(const T *__restrict__ A,
 #pragma unroll
     for (int j = 0; j < MAXJ; ++j) acc[i][j] = T(0);
   for (int kc = 0; kc < s1; kc += UK) {
-    for (int q = tid; q < UR * UK; q += BT) {
-      const int r = q / UK, k = q % UK;
-      As[r * (UK + 1) + k] = (i0 + r < n && kc + k < s1) ? A[(size_t)(i0 + r) * s1 + kc + k] : T(0);
+    {  // loads of the A tile in flight together, then the M rows four at a time
+      constexpr int NQ = UR * UK / BT;
+      T av[NQ];
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) {
+        const int q = tid + u * BT, r = q / UK, k = q % UK;
+        av[u] = (i0 + r < n && kc + k < s1) ? A[(size_t)(i0 + r) * s1 + kc + k] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < NQ; ++u) {
+        const int q = tid + u * BT;
+        As[(q / UK) * (UK + 1) + q % UK] = av[u];
+      }
     }
-    for (int q = tid; q < UK * s2; q += BT) {
-      const int k = q / s2, c = q % s2;
-      Ms[q] = (kc + k < s1) ? (T)M[(size_t)(kc + k) * s2 + c] : T(0);
+    for (int q0 = tid; q0 < UK * s2; q0 += 4 * BT) {
+      T mv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int q = q0 + u * BT, k = q / s2, c = q % s2;
+        mv[u] = (q < UK * s2 && kc + k < s1) ? (T)M[(size_t)(kc + k) * s2 + c] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (q0 + u * BT < UK * s2) Ms[q0 + u * BT] = mv[u];
     }
     __syncthreads();
     for (int k = 0; k < UK; ++k) {
