@@ -156,30 +156,14 @@ __global__ void __launch_bounds__(BT) k_seg_block_update(const T *__restrict__ A
   const double *Mg = M + (size_t)seg * s1 * s2;
   for (int q = threadIdx.x; q < s1 * s2; q += BT) Ms[q] = on ? (T)Mg[q] : T(0);
   __syncthreads();
-  // a warp per row: the row of A is read once (lanes over k, s1 <= 96) and broadcast by
-  // shuffles; lanes own output columns
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int64_t i = ch.row0[c] + ty; i < ch.row1[c]; i += 8) {
-    T a[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) a[q] = tx + 32 * q < s1 ? A[(size_t)i * s1 + tx + 32 * q] : T(0);
-    for (int col = tx; col - tx < s2; col += 32) {
+    for (int col = tx; col < s2; col += 32) {
       T acc = T(0);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (32 * q >= s1) break;
-#pragma unroll 8
-        for (int kk = 0; kk < 32; ++kk) {
-          const T ak = __shfl_sync(0xffffffffu, a[q], kk);
-          const int k = 32 * q + kk;
-          if (k < s1 && col < s2) acc += ak * Ms[k * s2 + col];
-        }
-      }
-      if (col < s2) {
-        T v = scale * acc;
-        if (C) v += beta * C[(size_t)i * s2 + col];
-        Out[(size_t)i * s2 + col] = v;
-      }
+      for (int k = 0; k < s1; ++k) acc += A[(size_t)i * s1 + k] * Ms[k * s2 + col];
+      T v = scale * acc;
+      if (C) v += beta * C[(size_t)i * s2 + col];
+      Out[(size_t)i * s2 + col] = v;
     }
   }
 }
