@@ -76,7 +76,16 @@ __global__ void k_seg_reduce(const double *work, SegChunks ch, int64_t entries, 
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= entries) return;
   double acc = 0.0;
-  for (int c = ch.seg_first[seg]; c < ch.seg_first[seg + 1]; ++c) acc += work[(size_t)c * entries + e];
+  const int c1 = ch.seg_first[seg + 1];
+  int c = ch.seg_first[seg];
+  for (; c + 8 <= c1; c += 8) {  // eight partials in flight, summed in chunk order
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = work[(size_t)(c + u) * entries + e];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc += v[u];
+  }
+  for (; c < c1; ++c) acc += work[(size_t)c * entries + e];
   out[(size_t)seg * entries + e] = acc;
 }
 

@@ -126,8 +126,17 @@ __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
 __global__ void k_gram_reduce(const double *work, int nchunks, int64_t entries, double *C) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= entries) return;
+  // sixteen partials in flight per round, summed in chunk order (same result as one by one)
   double acc = 0.0;
-  for (int c = 0; c < nchunks; ++c) acc += work[(size_t)c * entries + e];
+  int c = 0;
+  for (; c + 16 <= nchunks; c += 16) {
+    double v[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v[u] = work[(size_t)(c + u) * entries + e];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) acc += v[u];
+  }
+  for (; c < nchunks; ++c) acc += work[(size_t)c * entries + e];
   C[e] = acc;
 }
 

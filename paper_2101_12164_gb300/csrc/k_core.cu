@@ -98,7 +98,7 @@ __device__ void trsm_masked(const double *L, int s, const int32_t *mask, double 
 template <typename F>
 __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
   __shared__ F cs[128], sn[128];
-  __shared__ int pp[128], qq[128], ring[258];
+  __shared__ int pp[128], qq[128];
   __shared__ int any;
   __shared__ F fro_sh;
   __shared__ float red[CT];
@@ -118,13 +118,18 @@ __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
   const F floor_abs = floor_rel * fro_sh;
   const int se = s + (s & 1);
   const int npair = se / 2;
+  // round-robin pairing in closed form: the ring that fixes position 0 and rotates the other
+  // se - 1 positions by one per round holds, after t rounds, 1 + ((j - 1 - t) mod (se - 1))
+  // at position j >= 1
+  auto ring_at = [se](int j, int t) {
+    return j == 0 ? 0 : 1 + (((j - 1 - t) % (se - 1)) + (se - 1)) % (se - 1);
+  };
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) any = 0;
-    for (int i = tid; i < se; i += CT) ring[i] = i;
     __syncthreads();
     for (int round = 0; round < se - 1; ++round) {
       for (int k = tid; k < npair; k += CT) {
-        int p = ring[k], q = ring[se - 1 - k];
+        int p = ring_at(k, round), q = ring_at(se - 1 - k, round);
         if (p > q) { const int x = p; p = q; q = x; }
         pp[k] = p;
         qq[k] = q;
@@ -169,12 +174,6 @@ __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
           A[p * s + j] = c * ap - sv * aq;
           A[q * s + j] = sv * ap + c * aq;
         }
-      }
-      __syncthreads();
-      if (tid == 0) {
-        const int last = ring[se - 1];
-        for (int i = se - 1; i > 1; --i) ring[i] = ring[i - 1];
-        ring[1] = last;
       }
       __syncthreads();
     }
