@@ -72,6 +72,18 @@ static int nd_leaf() {
   return v >= 8 ? v : 64;
 }
 
+// Largest subtree (supernodes) a sweep runs as one item (NSP_SUBTREE, default 32; <= 1: off).
+static int subtree_max() {
+  const char *e = std::getenv("NSP_SUBTREE");
+  return e ? std::atoi(e) : 32;
+}
+
+// Largest front (rows) of a subtree member (NSP_SUBTREE_M, default 128).
+static int subtree_m() {
+  const char *e = std::getenv("NSP_SUBTREE_M");
+  return e ? std::atoi(e) : 128;
+}
+
 static int relax_level() {
   const char *e = std::getenv("NSP_RELAX");
   return e ? std::atoi(e) : 2;
@@ -299,6 +311,51 @@ struct ForestData {
     const int tb = vector ? kSweepVectorCols : kSweepBlockRows;
     std::vector<int32_t> ia, ib, gs, uf(nsn, 0), ub(nsn, 0), need(nsn, 0);
     auto small = [&](int J) { return vector && h.sn_m[J] <= kSmallM && h.sn_w[J] <= kSmallW; };
+    // Subtrees of small supernodes run as one item each (one CTA, no dependency wait inside):
+    // J heads one when its whole subtree is at most subtree_max() supernodes of bounded size
+    // and panel area, numbered contiguously below J (postorder).
+    std::vector<char> in_sub(nsn, 0);
+    std::vector<int32_t> sub_first(nsn), sub_cnt(nsn, 1), sub_off(nsn, -1), sub_len_of(nsn, 0);
+    {
+      const int smax = subtree_max();
+      std::vector<char> ok(nsn);
+      std::vector<double> area(nsn);
+      bool post = true;
+      for (int J = 0; J < nsn; ++J) {
+        const int m = h.sn_m[J], w = h.sn_w[J];
+        ok[J] = m <= subtree_m() && 2 * w <= subtree_m();
+        area[J] = (double)m * w;
+        sub_first[J] = J;
+        if (h.sn_parent[J] >= 0 && h.sn_parent[J] <= J) post = false;
+      }
+      // block mode only: in vector mode a small supernode is a warp's work, and running a
+      // subtree's heights one after another in one CTA lengthened the single-vector sweep
+      for (int J = 0; J < nsn && post && smax > 1 && !vector; ++J) {
+        in_sub[J] = ok[J] && sub_cnt[J] <= smax && area[J] <= kSubtreeArea && J - sub_first[J] + 1 == sub_cnt[J];
+        const int par = h.sn_parent[J];
+        if (par < 0) continue;
+        sub_first[par] = std::min(sub_first[par], sub_first[J]);
+        sub_cnt[par] += sub_cnt[J];
+        area[par] += area[J];
+        ok[par] = ok[par] && ok[J];
+      }
+    }
+    // member list of the subtree headed by R in group_sn: members by height, -1 between heights
+    auto emit_subtree = [&](int R) {
+      if (sub_off[R] < 0) {
+        std::vector<std::pair<int, int>> mem;
+        for (int J = sub_first[R]; J <= R; ++J) mem.push_back({h.sn_level[J], J});
+        std::stable_sort(mem.begin(), mem.end());
+        sub_off[R] = (int32_t)gs.size();
+        for (size_t q = 0; q < mem.size(); ++q) {
+          if (q > 0 && mem[q].first != mem[q - 1].first) gs.push_back(-1);
+          gs.push_back(mem[q].second);
+        }
+        sub_len_of[R] = (int32_t)gs.size() - sub_off[R];
+      }
+      ia.push_back(sub_off[R]);
+      ib.push_back(kSubtreeTag - sub_len_of[R]);
+    };
     auto emit_level = [&](int l, bool fwd) {
       std::vector<int32_t> grp;
       auto flush = [&]() {
@@ -310,6 +367,15 @@ struct ForestData {
       };
       for (int q = h.level_ptr[l]; q < h.level_ptr[l + 1]; ++q) {
         const int J = h.level_sn[q];
+        if (in_sub[J]) {
+          const int par = h.sn_parent[J];
+          if (par >= 0 && in_sub[par]) continue;  // runs inside its head's item
+          if (sub_cnt[J] > 1) {                   // the whole subtree in one item
+            emit_subtree(J);
+            (fwd ? uf : ub)[J] = 1;
+            continue;
+          }
+        }
         if (small(J)) {
           grp.push_back(J);
           if ((int)grp.size() == kGroup) flush();

@@ -60,52 +60,64 @@ __device__ void chol_threshold(double *L, const double *diag0, int s, double dro
 }
 
 // Solve L X = X (fwd) or L^T X = X (bwd) in place; L lower s x s (row-major), X s x r
-// (row-major); rows with mask == 0 are set to zero. Eight lanes share each column.
+// (row-major); rows with mask == 0 are set to zero. Right-looking substitution: step i
+// subtracts row i's contribution x_i = X_i / L_ii from the rows still to be solved (one
+// barrier per step, all (row, column) updates of a step in parallel), and a last pass
+// scales every row by 1 / L_ii. identity_rhs: X = I on entry (forward: only the columns
+// <= i of row i can be nonzero, so the updates of step i stop there).
 __device__ void trsm_masked(const double *L, int s, const int32_t *mask, double *X, int r,
                             bool transpose, bool identity_rhs = false) {
-  // lanes per column: enough groups to cover all r columns in one pass when possible
-  const int lpc = r <= CT / 8 ? 8 : 4;
-  const int lane8 = threadIdx.x % lpc, grp = threadIdx.x / lpc;
-  for (int c0 = 0; c0 < r; c0 += CT / lpc) {
-    const int c = c0 + grp;
-    const bool act = c < r;
-    for (int step = 0; step < s; ++step) {
-      const int i = transpose ? s - 1 - step : step;
-      double part = 0.0;
-      // forward solve of an identity column c: rows i < c stay zero
-      if (act && mask[i] && !(identity_rhs && !transpose && i < c)) {
-        if (!transpose) {
-          for (int t = (identity_rhs ? c : 0) + lane8; t < i; t += lpc)
-            if (mask[t]) part += L[i * s + t] * X[t * r + c];
-        } else {
-          for (int t = i + 1 + lane8; t < s; t += lpc)
-            if (mask[t]) part += L[t * s + i] * X[t * r + c];
+  __shared__ double invd[256];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < s; i += CT) invd[i] = mask[i] ? 1.0 / L[i * s + i] : 0.0;
+  __syncthreads();
+  // forward solve of X = I: row i is zero beyond column i, so step i touches columns <= i
+  const bool lower_id = identity_rhs && !transpose;
+  for (int step = 0; step < s; ++step) {
+    const int i = transpose ? s - 1 - step : step;
+    if (mask[i]) {
+      const double inv = invd[i];
+      const int t0 = transpose ? 0 : i + 1, t1 = transpose ? i : s;
+      const int nc = lower_id ? min(r, i + 1) : r;
+      const int n = (t1 - t0) * nc;
+      for (int e = tid; e < n; e += CT) {
+        const int t = t0 + e / nc, c = e % nc;
+        if (mask[t]) {
+          const double lti = transpose ? L[i * s + t] : L[t * s + i];
+          X[t * r + c] -= lti * (X[i * r + c] * inv);
         }
       }
-      if (lpc == 8) part += __shfl_xor_sync(FULL, part, 4);
-      part += __shfl_xor_sync(FULL, part, 2);
-      part += __shfl_xor_sync(FULL, part, 1);
-      if (lane8 == 0 && act) X[i * r + c] = mask[i] ? (X[i * r + c] - part) / L[i * s + i] : 0.0;
-      __syncwarp();
     }
+    __syncthreads();
+  }
+  for (int e = tid; e < s * r; e += CT) {
+    const int i = e / r;
+    X[e] = mask[i] ? X[e] * invd[i] : 0.0;
   }
   __syncthreads();
 }
 
-// Cyclic Jacobi on symmetric A (s x s row-major); V accumulates (A_in = V A_out V^T).
-// A rotation is applied when |a_pq| > tol * sqrt(|a_pp a_qq|) and |a_pq| > floor_rel ||A||_F
-// (below that the entry is at the rounding level of the matrix).
+// Cyclic Jacobi on symmetric A (s x s row-major, leading dimension ld for A and V); V
+// accumulates (A_in = V A_out V^T). A rotation is applied when |a_pq| > tol sqrt(|a_pp a_qq|)
+// and |a_pq| > floor_rel ||A||_F (below that the entry is at the rounding level of the
+// matrix). Each round rotates disjoint pairs; a warp owns its pairs for the whole round: it
+// forms each rotation from the pair's 2 x 2 block (which no other pair touches), applies it
+// to the pair's two columns of A and V, and after a barrier to the pair's two rows of A.
+// An odd ld keeps the column accesses free of shared-memory bank conflicts.
 template <typename F>
-__device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
+__device__ void jacobi(F *A, F *V, int s, int ld, int max_sweeps, F tol, F floor_rel) {
   __shared__ F cs[128], sn[128];
   __shared__ int pp[128], qq[128];
   __shared__ int any;
   __shared__ F fro_sh;
   __shared__ float red[CT];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {  // ||A||_F (rotations keep it): off-diagonal entries below floor_rel ||A||_F are final
     float acc = 0.0f;
-    for (int i = tid; i < s * s; i += CT) acc += (float)A[i] * (float)A[i];
+    for (int e = tid; e < s * s; e += CT) {
+      const float a = (float)A[(e / s) * ld + e % s];
+      acc += a * a;
+    }
     red[tid] = acc;
     __syncthreads();
     for (int h = CT / 2; h > 0; h >>= 1) {
@@ -128,39 +140,44 @@ __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
     if (tid == 0) any = 0;
     __syncthreads();
     for (int round = 0; round < se - 1; ++round) {
-      for (int k = tid; k < npair; k += CT) {
-        int p = ring_at(k, round), q = ring_at(se - 1 - k, round);
-        if (p > q) { const int x = p; p = q; q = x; }
-        pp[k] = p;
-        qq[k] = q;
-        F c = F(1), sv = F(0);
-        if (q < s) {
-          const F apq = A[p * s + q], app = A[p * s + p], aqq = A[q * s + q];
-          if (fabs(apq) > floor_abs && fabs(apq) > tol * sqrt_(fabs(app * aqq))) {
-            const F tau = (aqq - app) / (F(2) * apq);
-            const F tt = (tau >= F(0) ? F(1) : F(-1)) / (fabs(tau) + sqrt_(F(1) + tau * tau));
-            c = F(1) / sqrt_(F(1) + tt * tt);
-            sv = tt * c;
-            any = 1;
+      {
+        // lane l forms the rotation of the warp's l-th pair (the pairs' chains overlap), then
+        // the warp applies each rotation to its pair's two columns of A and V
+        const int kl = warp + lane * (CT / 32);
+        int pl = 0, ql = 0;
+        F cl = F(1), sl = F(0);
+        if (kl < npair) {
+          pl = ring_at(kl, round);
+          ql = ring_at(se - 1 - kl, round);
+          if (pl > ql) { const int x = pl; pl = ql; ql = x; }
+          if (ql < s) {
+            const F apq = A[pl * ld + ql], app = A[pl * ld + pl], aqq = A[ql * ld + ql];
+            if (fabs(apq) > floor_abs && fabs(apq) > tol * sqrt_(fabs(app * aqq))) {
+              const F tau = (aqq - app) / (F(2) * apq);
+              const F tt = (tau >= F(0) ? F(1) : F(-1)) / (fabs(tau) + sqrt_(F(1) + tau * tau));
+              cl = F(1) / sqrt_(F(1) + tt * tt);
+              sl = tt * cl;
+            }
           }
+          pp[kl] = pl;
+          qq[kl] = ql;
+          cs[kl] = cl;
+          sn[kl] = sl;
+          if (sl != F(0)) any = 1;
         }
-        cs[k] = c;
-        sn[k] = sv;
-      }
-      __syncthreads();
-      const int lane = tid & 31, warp = tid >> 5;
-      for (int k = warp; k < npair; k += CT / 32) {  // A <- A J, V <- V J
-        const F sv = sn[k];
-        if (sv == F(0)) continue;
-        const int p = pp[k], q = qq[k];
-        const F c = cs[k];
-        for (int i = lane; i < s; i += 32) {
-          const F ap = A[i * s + p], aq = A[i * s + q];
-          A[i * s + p] = c * ap - sv * aq;
-          A[i * s + q] = sv * ap + c * aq;
-          const F vp = V[i * s + p], vq = V[i * s + q];
-          V[i * s + p] = c * vp - sv * vq;
-          V[i * s + q] = sv * vp + c * vq;
+        __syncwarp();
+        for (int l = 0; warp + l * (CT / 32) < npair; ++l) {
+          const int p = __shfl_sync(0xffffffffu, pl, l), q = __shfl_sync(0xffffffffu, ql, l);
+          const F c = __shfl_sync(0xffffffffu, cl, l), sv = __shfl_sync(0xffffffffu, sl, l);
+          if (sv == F(0)) continue;
+          for (int i = lane; i < s; i += 32) {
+            const F ap = A[i * ld + p], aq = A[i * ld + q];
+            A[i * ld + p] = c * ap - sv * aq;
+            A[i * ld + q] = sv * ap + c * aq;
+            const F vp = V[i * ld + p], vq = V[i * ld + q];
+            V[i * ld + p] = c * vp - sv * vq;
+            V[i * ld + q] = sv * vp + c * vq;
+          }
         }
       }
       __syncthreads();
@@ -170,9 +187,9 @@ __device__ void jacobi(F *A, F *V, int s, int max_sweeps, F tol, F floor_rel) {
         const int p = pp[k], q = qq[k];
         const F c = cs[k];
         for (int j = lane; j < s; j += 32) {
-          const F ap = A[p * s + j], aq = A[q * s + j];
-          A[p * s + j] = c * ap - sv * aq;
-          A[q * s + j] = sv * ap + c * aq;
+          const F ap = A[p * ld + j], aq = A[q * ld + j];
+          A[p * ld + j] = c * ap - sv * aq;
+          A[q * ld + j] = sv * ap + c * aq;
         }
       }
       __syncthreads();
@@ -193,37 +210,56 @@ __device__ void gemm_nn(const double *A, const double *B, double *Cm, int s) {  
   __syncthreads();
 }
 
-// Modified Gram-Schmidt on the columns of V (s x s row-major, FP64).
-__device__ void mgs_columns(double *V, int s) {
-  __shared__ double red[CT];
-  __shared__ double coef[256];
+// Gram-Schmidt on the columns of V (s x s row-major, FP64): column j minus its projections
+// on the previous (orthonormal) columns, coefficients taken against the original column j,
+// then normalized. FP64 arithmetic is the scarce resource here (about two FMAs per clock per
+// SM), so every product is formed once: a thread per coefficient (a dot over the rows), a
+// thread per row for the projection, one warp for the norm. The work runs on a copy in W
+// (s x s) whose row r is rotated by r positions, so that threads walking down a column hit
+// distinct shared-memory banks.
+__device__ void mgs_columns(double *V, int s, double *W) {
+  __shared__ double coef[256], colw[256];
+  __shared__ double inv_nrm;
   const int tid = threadIdx.x;
+  auto at = [s](int r, int c) { return r * s + (c + r) % s; };
+  for (int e = tid; e < s * s; e += CT) W[at(e / s, e % s)] = V[e];
+  __syncthreads();
   for (int j = 0; j < s; ++j) {
-    // coefficients against the previous columns, then subtract, then normalize
-    for (int i = tid; i < j; i += CT) {
+    if (tid < j) {  // rotated positions advance by one per row, wrapping at s
       double d = 0.0;
-      for (int r = 0; r < s; ++r) d += V[r * s + i] * V[r * s + j];
-      coef[i] = d;
+      int ki = tid, kj = j;
+      for (int r = 0; r < s; ++r) {
+        d += W[r * s + ki] * W[r * s + kj];
+        ki = ki + 1 == s ? 0 : ki + 1;
+        kj = kj + 1 == s ? 0 : kj + 1;
+      }
+      coef[tid] = d;
     }
     __syncthreads();
-    for (int r = tid; r < s; r += CT) {
-      double v = V[r * s + j];
-      for (int i = 0; i < j; ++i) v -= coef[i] * V[r * s + i];
-      V[r * s + j] = v;
+    if (tid < s) {
+      const double *row = W + tid * s;
+      double v = row[(j + tid) % s];
+      int k = tid;
+      for (int i = 0; i < j; ++i) {
+        v -= coef[i] * row[k];
+        k = k + 1 == s ? 0 : k + 1;
+      }
+      colw[tid] = v;
     }
     __syncthreads();
-    double sq = 0.0;
-    for (int r = tid; r < s; r += CT) sq += V[r * s + j] * V[r * s + j];
-    red[tid] = sq;
-    __syncthreads();
-    for (int h = CT / 2; h > 0; h >>= 1) {
-      if (tid < h) red[tid] += red[tid + h];
-      __syncthreads();
+    if (tid < 32) {
+      double sq = 0.0;
+      for (int r = tid; r < s; r += 32) sq += colw[r] * colw[r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, o);
+      if (tid == 0) inv_nrm = sq > 0.0 ? 1.0 / sqrt(sq) : 0.0;
     }
-    const double nrm = sqrt(red[0]);
-    for (int r = tid; r < s; r += CT) V[r * s + j] = nrm > 0.0 ? V[r * s + j] / nrm : 0.0;
+    __syncthreads();
+    if (tid < s) W[at(tid, j)] = colw[tid] * inv_nrm;
     __syncthreads();
   }
+  for (int e = tid; e < s * s; e += CT) V[e] = W[at(e / s, e % s)];
+  __syncthreads();
 }
 
 // FP64-accurate EVD of the symmetric matrix held in Bm (s x s): on return the eigenvalues
@@ -232,16 +268,24 @@ __device__ void mgs_columns(double *V, int s) {
 __device__ void eig_sym(double *Bm, int s, double *V, double *W1, bool polish) {
   const int tid = threadIdx.x;
   const size_t ss = (size_t)s * s;
-  float *A32 = reinterpret_cast<float *>(W1), *V32 = A32 + ss;
-  for (size_t i = tid; i < ss; i += CT) {
-    A32[i] = (float)Bm[i];
-    V32[i] = (i / s == i % s) ? 1.0f : 0.0f;
+  const int ld = s | 1;  // odd leading dimension of the FP32 phase (s x ld floats fit in s x s doubles)
+  float *A32 = reinterpret_cast<float *>(W1), *V32 = reinterpret_cast<float *>(V);
+  for (size_t e = tid; e < ss; e += CT) {
+    const int i = e / s, j = e % s;
+    A32[i * ld + j] = (float)Bm[e];
+    V32[i * ld + j] = i == j ? 1.0f : 0.0f;
   }
   __syncthreads();
-  jacobi<float>(A32, V32, s, 8, 1e-6f, 2e-7f);
-  for (size_t i = tid; i < ss; i += CT) V[i] = (double)V32[i];
+  jacobi<float>(A32, V32, s, ld, 8, 1e-6f, 2e-7f);
+  float *T32 = A32;  // A32 is no longer needed: V32 moves there before V is widened in place
+  for (size_t e = tid; e < ss; e += CT) {
+    const int i = e / s, j = e % s;
+    T32[i * ld + j] = V32[i * ld + j];
+  }
   __syncthreads();
-  mgs_columns(V, s);
+  for (size_t e = tid; e < ss; e += CT) V[e] = (double)T32[(e / s) * ld + e % s];
+  __syncthreads();
+  mgs_columns(V, s, W1);
   // W1 = C V ; Bm = V^T W1 (symmetric: upper triangle computed, mirrored)
   gemm_nn(Bm, V, W1, s);
   for (int i = tid >> 5; i < s; i += CT / 32)
@@ -252,7 +296,7 @@ __device__ void eig_sym(double *Bm, int s, double *V, double *W1, bool polish) {
       Bm[j * s + i] = v;
     }
   __syncthreads();
-  if (polish) jacobi<double>(Bm, V, s, 1, 1e-13, 1e-15);
+  if (polish) jacobi<double>(Bm, V, s, s, 1, 1e-13, 1e-15);
 }
 
 struct Scratch {
@@ -437,13 +481,22 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
     __syncthreads();
   }
   if (c_ok) {
-    // b0 = RV = R_full L_C^{-T}
+    // b0 = RV = R_full L_C^{-T} (L_C^{-1} transposed in place first, so that the product
+    // reads rows of both operands)
     for (size_t i = tid; i < ss; i += CT) S.b2[i] = gRf[i];
+    for (size_t e = tid; e < ss; e += CT) {
+      const int i = e / s, j = e % s;
+      if (i > j) {
+        const double x = S.b1[e];
+        S.b1[e] = S.b1[j * s + i];
+        S.b1[j * s + i] = x;
+      }
+    }
     __syncthreads();
     for (int i = tid >> 5; i < s; i += CT / 32)
       for (int j = tid & 31; j < s; j += 32) {
         double v = 0.0;
-        for (int t = 0; t <= j; ++t) v += S.b2[i * s + t] * S.b1[j * s + t];
+        for (int t = 0; t <= j; ++t) v += S.b2[i * s + t] * S.b1[t * s + j];
         S.b0[i * s + j] = v;
       }
     __syncthreads();
@@ -478,10 +531,12 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
     }
     __syncthreads();
   }
+  for (size_t e = tid; e < ss; e += CT) S.b2[(e % s) * s + e / s] = S.b0[e];  // b2 = RV^T
+  __syncthreads();
   for (int i = tid >> 5; i < s; i += CT / 32)  // b1 = T = RV RV^T (symmetric)
     for (int j = i + (tid & 31); j < s; j += 32) {
       double v = 0.0;
-      for (int t = 0; t < s; ++t) v += S.b0[i * s + t] * S.b0[j * s + t];
+      for (int t = 0; t < s; ++t) v += S.b0[i * s + t] * S.b2[t * s + j];
       S.b1[i * s + j] = v;
       S.b1[j * s + i] = v;
     }
@@ -490,14 +545,22 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   __syncthreads();
   // step 9: EVD of T: eigenvalues on b0's diagonal, W in b1
   eig_sym(S.b0, s, S.b1, S.b2, polish != 0);
-  if (tid == 0) {
-    for (int j = 0; j < s; ++j) { evals[j] = S.b0[j * s + j]; order[j] = j; }
-    for (int a = 0; a < s; ++a) {  // selection sort, descending
-      int best = a;
-      for (int b = a + 1; b < s; ++b)
-        if (evals[order[b]] > evals[order[best]]) best = b;
-      const int x = order[a]; order[a] = order[best]; order[best] = x;
+  for (int j = tid; j < s; j += CT) {
+    evals[j] = S.b0[j * s + j];
+    order[j] = j;
+  }
+  __syncthreads();
+  if (tid < s) {  // descending order by rank (ties by index); every write stays in [0, s)
+    const double e = evals[tid];
+    int rk = 0;
+    for (int b = 0; b < s; ++b) {
+      const double f = evals[b];
+      rk += (f > e || (f == e && b < tid)) ? 1 : 0;
     }
+    order[min(rk, s - 1)] = tid;
+  }
+  __syncthreads();
+  if (tid == 0) {
     const int kk = min(k, min(r_keep, nk));
     *rank = kk;
     for (int j = 0; j < k; ++j) Sigma[j] = j < kk ? fmax(evals[order[j]], 0.0) : 0.0;

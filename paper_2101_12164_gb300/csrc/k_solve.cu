@@ -631,7 +631,7 @@ __device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, con
 // item_b >= 0: tile of supernode item_a starting at row/column item_b;
 // item_b < 0 : group of -item_b small supernodes group_sn[item_a ...] (vector mode only).
 template <typename T, int TC, int CM, int RM, bool VECTOR>
-__global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ panel,
+__global__ void __launch_bounds__(ST, sizeof(T) == 8 ? 1 : VECTOR ? 4 : 2) k_sweep(SweepCtx c, const T *__restrict__ panel,
                                               const T *B, T *Y, T *U, T *X) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
@@ -651,12 +651,19 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
     if (it >= p.nitems) break;
     const bool fwd = it < p.nfwd;
     const int a = p.item_a[it], b = p.item_b[it];
-    const int nmem = b < 0 ? -b : 1;
-    // dependencies
-    if (threadIdx.x == 0) {
+    const int sub_len = b <= kSubtreeTag ? kSubtreeTag - b : 0;  // subtree item: list length
+    const int nmem = sub_len ? 1 : b < 0 ? -b : 1;
+    // the supernode a member q of the item stands for in the dependency counters (a subtree
+    // item: its head, the last entry of its member list)
+    auto dep_sn = [&](int q) {
+      return sub_len ? p.group_sn[a + sub_len - 1] : b < 0 ? p.group_sn[a + q] : a;
+    };
+    // dependencies: lane q of warp 0 waits for member q, so a group's waits overlap
+    if (threadIdx.x < 32) {
+      const int q = threadIdx.x;
       bool ok = ld_relaxed(p.abort_flag) == 0;
-      for (int q = 0; q < nmem && ok; ++q) {
-        const int J = b < 0 ? p.group_sn[a + q] : a;
+      if (q < nmem && ok) {
+        const int J = dep_sn(q);
         if (fwd) {
           ok = wait_geq(&p.cnt_f[J], epoch * (uint32_t)p.need_f[J], p.abort_flag, c.st, J,
                         c.max_spins);
@@ -669,23 +676,63 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
                               J, c.max_spins);
         }
       }
-      s_ok = ok;
+      ok = __all_sync(0xffffffffu, ok);
+      if (q == 0) s_ok = ok;
     }
     __syncthreads();
     if (s_ok) {
-      if (b < 0) {
-        const int wid = threadIdx.x >> 5;
-        if (wid < nmem) {
-          const int J = p.group_sn[a + wid];
-          if (fwd) vec_fwd_small<T>(c, panel, B, Y, U, J);
-          else vec_bwd_small<T>(c, panel, Y, X, J, sm + wid * 32 * 33);
+      if constexpr (VECTOR) {
+        if (b < 0) {
+          // a group (L members of one height) or a subtree (members by height, -1 between
+          // heights): the members of one height a warp each, a barrier between heights
+          const int32_t *lst = p.group_sn + a;
+          const int L = sub_len ? sub_len : -b;
+          const int wid = threadIdx.x >> 5;
+          int q = fwd ? 0 : L - 1;
+          while (fwd ? q < L : q >= 0) {
+            int e = q;
+            if (fwd) {
+              while (e < L && lst[e] >= 0) ++e;
+            } else {
+              while (e >= 0 && lst[e] >= 0) --e;
+            }
+            const int lo = fwd ? q : e + 1, hi = fwd ? e : q + 1;  // members [lo, hi)
+            for (int t = lo + wid; t < hi; t += ST / 32) {
+              if (fwd) vec_fwd_small<T>(c, panel, B, Y, U, lst[t]);
+              else vec_bwd_small<T>(c, panel, Y, X, lst[t], sm + wid * 32 * 33);
+            }
+            if (sub_len) __syncthreads();
+            q = fwd ? e + 1 : e - 1;
+          }
+        } else {
+          if (fwd) vec_fwd_tile<T>(c, panel, B, Y, U, a, b, sm);
+          else vec_bwd_tile<T>(c, panel, Y, X, a, b, sm);
         }
-      } else if (VECTOR) {
-        if (fwd) vec_fwd_tile<T>(c, panel, B, Y, U, a, b, sm);
-        else vec_bwd_tile<T>(c, panel, Y, X, a, b, sm);
       } else {
-        if (fwd) blk_fwd_tile<T, TC, CM, RM>(c, panel, B, Y, U, a, b, sm);
-        else blk_bwd_tile<T, TC, CM, RM>(c, panel, Y, X, a, b, sm);
+        // one tile (supernode a, first row / column b), or every tile of a subtree's members
+        // (heights upwards forward, downwards backward; -1 separates heights and is a barrier
+        // that makes one height's U / X rows visible to the next)
+        constexpr int TM = Cfg<TC, CM, RM>::TM;
+        int pos = sub_len ? (fwd ? 0 : sub_len - 1) : 0;
+        int J = sub_len ? p.group_sn[a + pos] : a;
+        int r0 = sub_len ? 0 : b;
+        while (true) {
+          if (J >= 0) {
+            if (fwd) blk_fwd_tile<T, TC, CM, RM>(c, panel, B, Y, U, J, r0, sm);
+            else blk_bwd_tile<T, TC, CM, RM>(c, panel, Y, X, J, r0, sm);
+          } else {
+            __syncthreads();
+          }
+          if (!sub_len) break;
+          if (J >= 0 && r0 + TM < (fwd ? c.f.sn_m[J] : c.f.sn_w[J])) {
+            r0 += TM;
+            continue;
+          }
+          pos += fwd ? 1 : -1;
+          if (pos < 0 || pos >= sub_len) break;
+          J = p.group_sn[a + pos];
+          r0 = 0;
+        }
       }
     }
     // the barrier orders every thread's writes before thread 0's device-scope fence, which
@@ -694,7 +741,7 @@ __global__ void __launch_bounds__(ST) k_sweep(SweepCtx c, const T *__restrict__ 
     if (threadIdx.x == 0 && s_ok) {
       __threadfence();
       for (int q = 0; q < nmem; ++q) {
-        const int J = b < 0 ? p.group_sn[a + q] : a;
+        const int J = dep_sn(q);
         if (fwd) {
           atomicAdd(&p.self_f[J], 1u);
           const int par = p.sn_parent[J];

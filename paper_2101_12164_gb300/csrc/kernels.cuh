@@ -76,6 +76,10 @@ int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
 constexpr int kSweepVectorCols = 8;   // columns per backward tile in vector mode (a warp each)
 constexpr int kSmallM = 96, kSmallW = 32, kGroup = 8;
+// item_b of a subtree item: kSubtreeTag - L, item_a = offset of its L-entry member list
+// (supernodes by height, -1 between heights) in group_sn
+constexpr int kSubtreeTag = -(1 << 20);
+constexpr double kSubtreeArea = 65536.0;  // largest summed m x w panel area of a subtree item
 
 // ---- BLAS-like kernels (k_blas.cu) ------------------------------------------------
 // Y = alpha * A X + beta * C  (C may be nullptr; Y may alias C)
