@@ -148,7 +148,7 @@ def sweep_algorithmic_bytes(info, s, wbytes):
 # DRAM bytes (read + write) of one interior-sweep launch from an ncu capture of the bench
 # workload (profiles/sweep_block_lognormal3d_64.md), keyed by (configuration, s); absent
 # until captured for the current kernel.
-SWEEP_TRAFFIC = {(1, 80): 768.5e6}
+SWEEP_TRAFFIC = {(1, 80): 768.0e6}
 
 
 def sub_nnz(P):

@@ -84,6 +84,13 @@ static int subtree_m() {
   return e ? std::atoi(e) : 128;
 }
 
+// Columns per backward tile of a single-vector sweep (NSP_VEC_COLS, default 16).
+static int vec_cols() {
+  const char *e = std::getenv("NSP_VEC_COLS");
+  const int v = e ? std::atoi(e) : kSweepVectorCols;
+  return v >= 1 ? v : kSweepVectorCols;
+}
+
 static int relax_level() {
   const char *e = std::getenv("NSP_RELAX");
   return e ? std::atoi(e) : 2;
@@ -308,7 +315,7 @@ struct ForestData {
     Plan &P = *pp;
     const int nsn = h.nsn;
     const int tf = vector ? vec_rows : kSweepBlockRows;
-    const int tb = vector ? kSweepVectorCols : kSweepBlockRows;
+    const int tb = vector ? vec_cols() : kSweepBlockRows;
     std::vector<int32_t> ia, ib, gs, uf(nsn, 0), ub(nsn, 0), need(nsn, 0);
     auto small = [&](int J) { return vector && h.sn_m[J] <= kSmallM && h.sn_w[J] <= kSmallW; };
     // Subtrees of small supernodes run as one item each (one CTA, no dependency wait inside):
@@ -409,6 +416,7 @@ struct ForestData {
     P.d.nitems = (int32_t)ia.size();
     P.d.nfwd = nfwd;
     P.d.max_m = mm;
+    P.d.vec_cols = tb;
     P.d.vector = vector;
     P.d.item_a = P.item_a.p;
     P.d.item_b = P.item_b.p;

@@ -163,12 +163,23 @@ __global__ void __launch_bounds__(BT) k_seg_block_update(const T *__restrict__ A
   const int seg = ch.seg[c];
   const bool on = !active || active[seg];
   const double *Mg = M + (size_t)seg * s1 * s2;
-  for (int q = threadIdx.x; q < s1 * s2; q += BT) Ms[q] = on ? (T)Mg[q] : T(0);
+  for (int q0 = threadIdx.x; q0 < s1 * s2; q0 += 8 * BT) {  // eight loads in flight
+    double mv[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int q = q0 + u * BT;
+      mv[u] = (on && q < s1 * s2) ? Mg[q] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (q0 + u * BT < s1 * s2) Ms[q0 + u * BT] = (T)mv[u];
+  }
   __syncthreads();
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int64_t i = ch.row0[c] + ty; i < ch.row1[c]; i += 8) {
     for (int col = tx; col < s2; col += 32) {
       T acc = T(0);
+#pragma unroll 8
       for (int k = 0; k < s1; ++k) acc += A[(size_t)i * s1 + k] * Ms[k * s2 + col];
       T v = scale * acc;
       if (C) v += beta * C[(size_t)i * s2 + col];

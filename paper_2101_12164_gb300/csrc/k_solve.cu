@@ -19,8 +19,9 @@
 // where k_sweep_begin advances them before every launch.
 // Item kinds:
 //   vector (s = 1): 16-byte vector loads of the panel, 8 warps split the K dimension
-//                   (forward) or a warp per panel column (backward); supernodes with
-//                   m <= 96, w <= 32 are processed a warp each, up to 8 per item;
+//                   (forward) or a warp per panel column, vec_cols columns a tile
+//                   (backward); supernodes with m <= 96, w <= 32 are processed a warp
+//                   each, up to 8 per item;
 //   block (s > 1):  a register-blocked (TM x K) * (K x s) product per tile on CUDA cores.
 #include "kernels.cuh"
 
@@ -248,29 +249,30 @@ __device__ void vec_bwd_tile(const SweepCtx &c, const T *panel, const T *Y, T *X
   }
   __syncthreads();
   const int lane = tid & 31, wid = tid >> 5;
-  const int col = c0 + wid;
-  if (col >= w) return;
-  const T *Pc = P + (size_t)col * ld;
-  const int ks = col & ~(VN - 1);
-  T acc = T(0);
-  int k = ks + VN * lane;
-  for (; k + 3 * STEP < ld; k += 4 * STEP) {
-    typename VT::V v[4];
+  const int c1 = min(c0 + c.p.vec_cols, w);
+  for (int col = c0 + wid; col < c1; col += ST / 32) {  // the gathered g serves every column
+    const T *Pc = P + (size_t)col * ld;
+    const int ks = col & ~(VN - 1);
+    T acc = T(0);
+    int k = ks + VN * lane;
+    for (; k + 3 * STEP < ld; k += 4 * STEP) {
+      typename VT::V v[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) v[u] = VT::load(Pc + k + u * STEP);
+      for (int u = 0; u < 4; ++u) v[u] = VT::load(Pc + k + u * STEP);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < 4; ++u)
 #pragma unroll
-      for (int i = 0; i < VN; ++i) acc += VT::get(v[u], i) * g[k + u * STEP + i];
+        for (int i = 0; i < VN; ++i) acc += VT::get(v[u], i) * g[k + u * STEP + i];
+    }
+    for (; k < ld; k += STEP) {
+      typename VT::V v = VT::load(Pc + k);
+#pragma unroll
+      for (int i = 0; i < VN; ++i) acc += VT::get(v, i) * g[k + i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) X[first + col] = acc;
   }
-  for (; k < ld; k += STEP) {
-    typename VT::V v = VT::load(Pc + k);
-#pragma unroll
-    for (int i = 0; i < VN; ++i) acc += VT::get(v, i) * g[k + i];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) X[first + col] = acc;
 }
 
 // a warp processes one small supernode (m <= 96, w <= 32)

@@ -38,6 +38,7 @@ struct CsrDev {
 // CUDA graph and replayed.
 struct SweepPlan {
   int32_t nitems = 0, nfwd = 0, max_m = 0;
+  int32_t vec_cols = 0;  // columns per backward tile in vector mode (set by the plan)
   bool vector = false;
   const int32_t *item_a = nullptr, *item_b = nullptr, *group_sn = nullptr;
   const int32_t *sn_parent = nullptr, *need_f = nullptr, *units_f = nullptr, *units_b = nullptr;
@@ -74,7 +75,7 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T
 // rows of a forward tile in vector mode for elements of elem_bytes
 int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
-constexpr int kSweepVectorCols = 8;   // columns per backward tile in vector mode (a warp each)
+constexpr int kSweepVectorCols = 16;  // default columns per backward tile in vector mode
 constexpr int kSmallM = 96, kSmallW = 32, kGroup = 8;
 // item_b of a subtree item: kSubtreeTag - L, item_a = offset of its L-entry member list
 // (supernodes by height, -1 between heights) in group_sn
