@@ -134,21 +134,22 @@ __device__ __forceinline__ void gather_rows(const SweepCtx &c, const T *U, int64
 }
 
 // ---------------------------------------------------------------- vector items (s = 1)
-// Forward tile: 16 row groups of VN rows x 16 K groups; each thread keeps 8 vector loads in
-// flight. Rows of the tile: 16 VN (64 floats / 32 doubles).
+// Forward tile: kVecRG row groups of VN rows x ST / kVecRG K groups; each thread keeps 8
+// vector loads in flight. Rows of the tile: kVecRG VN.
+constexpr int kVecRG = 32;
 template <typename T>
 __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y, T *U, int J,
                              int r0, T *sm) {
   using VT = Vec<T>;
-  constexpr int VN = VT::N, TMV = 16 * VN;
+  constexpr int VN = VT::N, TMV = kVecRG * VN, KG = ST / kVecRG;
   const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
   const int first = c.f.sn_first[J];
   const T *P = panel + c.f.sn_panel[J];
   const int r1 = min(r0 + TMV, m);
   const int kmax = (r1 <= w) ? r1 : w;
   T *fs = sm;                      // [kmax]
-  T *red = sm + ((ld + 3) & ~3);   // [16][TMV]
-  T *gb = red + 16 * TMV;          // [TMV] update-row gathers of the tile's rows
+  T *red = sm + ((ld + 3) & ~3);   // [KG][TMV]
+  T *gb = red + KG * TMV;          // [TMV] update-row gathers of the tile's rows
   const int tid = threadIdx.x;
   for (int kb = tid; kb < kmax; kb += 3 * ST) {  // three positions' gathers in flight
     int pos[3];
@@ -172,25 +173,25 @@ __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y
     gb[i] = v[0];
   }
   __syncthreads();
-  const int rg = tid & 15, kg = tid >> 4;
+  const int rg = tid % kVecRG, kg = tid / kVecRG;
   const int row = r0 + VN * rg;
   T acc[VN];
 #pragma unroll
   for (int i = 0; i < VN; ++i) acc[i] = T(0);
   if (row < ld) {
     int k = kg;
-    for (; k + 112 < kmax; k += 128) {
+    for (; k + 7 * KG < kmax; k += 8 * KG) {
       typename VT::V v[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = VT::load(P + row + (size_t)(k + 16 * u) * ld);
+      for (int u = 0; u < 8; ++u) v[u] = VT::load(P + row + (size_t)(k + KG * u) * ld);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const T f = fs[k + 16 * u];
+        const T f = fs[k + KG * u];
 #pragma unroll
         for (int i = 0; i < VN; ++i) acc[i] += VT::get(v[u], i) * f;
       }
     }
-    for (; k < kmax; k += 16) {
+    for (; k < kmax; k += KG) {
       typename VT::V v0 = VT::load(P + row + (size_t)k * ld);
       const T f0 = fs[k];
 #pragma unroll
@@ -205,7 +206,7 @@ __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y
     if (r < r1) {
       T v = T(0);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) v += red[q * TMV + tid];
+      for (int q = 0; q < KG; ++q) v += red[q * TMV + tid];
       if (r < w) {
         Y[first + r] = v;
       } else {
@@ -216,8 +217,8 @@ __device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y
   }
 }
 
-// Backward tile: 8 consecutive panel columns, one warp each; a lane keeps up to 4 vector
-// loads of its column in flight.
+// Backward tile: vec_cols consecutive panel columns, a warp per column in turn, over one
+// gathered front vector; a lane keeps up to 4 vector loads of its column in flight.
 template <typename T>
 __device__ void vec_bwd_tile(const SweepCtx &c, const T *panel, const T *Y, T *X, int J, int c0,
                              T *sm) {
@@ -802,7 +803,7 @@ void dispatch(SweepCtx c, size_t smem, const T *panel, const T *B, T *Y, T *U, T
 
 }  // namespace
 
-int sweep_vector_rows(int elem_bytes) { return 16 * (16 / elem_bytes); }
+int sweep_vector_rows(int elem_bytes) { return kVecRG * (16 / elem_bytes); }
 
 template <typename T>
 int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y, T *U,
@@ -814,7 +815,8 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T
   if (s == 1) {
     require(p.vector, NSP_ERR_INVALID_ARG, "vector plan needed for one right-hand side");
     const size_t ldmax = (size_t)((p.max_m + 3) & ~3) + 8;
-    const size_t smem = sizeof(T) * std::max<size_t>(ldmax + 17 * 16 * (16 / sizeof(T)), 8 * 32 * 33);
+    const size_t smem = sizeof(T) * std::max<size_t>(
+        ldmax + (size_t)(ST / kVecRG + 1) * kVecRG * (16 / sizeof(T)), 8 * 32 * 33);
     dispatch<T, 1, 1, 1, true>(c, smem, panel, B, Y, U, X, stream, &grid);
     return grid;
   }
