@@ -15,6 +15,9 @@ Everything here is plain, slow and follows the paper step by step in float64:
 * ``nystrom_core``         : Algorithm 2 steps 5-10 (= Algorithm 1 steps 3-8).
 * ``build_m2``             : Algorithm 2, in the paper's S_I form (step 3) or the
                              equivalent S_Gamma correction form (SMW identity, §4.1 eq. (S-1)).
+* ``M2ADEF``               : the adapted-deflation variant M_{2A-DEF} of §4.3 (defined
+                             like eq. (deflation_comp_from_low_rank) and eq.
+                             (our_two_level_preconditioner), moved through Z = A_G^{-1} U).
 * ``pcg``                  : outer PCG on S_Gamma w = f (§2.3 eq. (Sx=b)) with M2 (§4.3 eq. (left_prec_mat)).
 * ``solve``                : block elimination of §2.3 eq. (A_LDLT) around the outer PCG.
 * ``solve_full_space``     : PCG on A with the block-factorization preconditioner of §2.3
@@ -225,9 +228,41 @@ class M2:
         return self.dbbd.solve_G(np.eye(n)) + (self.Z * self.Sigma) @ self.Z.T
 
 
+class M2ADEF:
+    """M_{2A-DEF}, the adapted-deflation variant of M2 (§4.3).
+
+    §4.3 defines, for a basis Ub of the R_G-transformed space, E = Ub^T R_G^{-T} S_G R_G^{-1} Ub,
+    Q = Ub E^{-1} Ub^T, the deflation operator I - Q R_G^{-T} S_G R_G^{-1} + Q (eq.
+    (deflation_comp_from_low_rank)) and the preconditioner R_G^{-1} (.) R_G^{-T} (eq.
+    (our_two_level_preconditioner)); M_{2A-DEF} is the same construction on the M2
+    approximation A_GI S_I^{-1} A_IG ~ U Sigma U^T, whose transformed basis is R_G^{-T} U.
+    With Zk = R_G^{-1} R_G^{-T} U = A_G^{-1} U (Algorithm 2 step 11) every R_G cancels:
+        E = Zk^T S_G Zk,   M = A_G^{-1} - Zk E^{-1} Zk^T S_G A_G^{-1} + Zk E^{-1} Zk^T.
+    Sigma does not enter (Q is invariant under a change of basis of span(Zk)).
+    """
+
+    def __init__(self, dbbd, Zk, Sigma=None):
+        self.dbbd, self.Z, self.Sigma = dbbd, np.asarray(Zk, dtype=np.float64), Sigma
+        self.E = self.Z.T @ dbbd.apply_S_gamma(self.Z)
+        self.E = 0.5 * (self.E + self.E.T)
+        self._Ec = sla.cho_factor(self.E, lower=True)
+
+    def apply(self, r):
+        r = np.asarray(r, dtype=np.float64)
+        y = self.dbbd.solve_G(r)                               # A_G^{-1} r
+        Sy = self.dbbd.apply_S_gamma(y)                        # S_G A_G^{-1} r
+        c = sla.cho_solve(self._Ec, self.Z.T @ r - self.Z.T @ Sy)
+        return y + self.Z @ c
+
+    def dense(self):
+        n = self.dbbd.n_G
+        return self.apply(np.eye(n))
+
+
 def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500,
-             drop_tol=1e-12):
-    """Algorithm 2. Returns (M2, info).
+             drop_tol=1e-12, variant="M2"):
+    """Algorithm 2. Returns (M2, info); variant="M2_ADEF" returns M_{2A-DEF} (class
+    M2ADEF) built from the same Z = A_G^{-1} U.
 
     form="S_I":     F = A_IG G (step 2); solve S_I X = F by block PCG preconditioned by
                     A_I (step 3, §5 setup); Y = A_GI X (step 4).
@@ -260,6 +295,10 @@ def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500
     U, Sigma, info = nystrom_core(G, Y, k, eps_rel)       # steps 5-10
     Z = dbbd.solve_G(U)                                   # step 11
     info.update(it_inner=it, inner_hist=hist, X=X, Y=Y, U=U)
+    if variant == "M2_ADEF":
+        return M2ADEF(dbbd, Z, Sigma), info
+    if variant != "M2":
+        raise ValueError(variant)
     return M2(dbbd, Z, Sigma), info
 
 

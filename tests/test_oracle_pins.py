@@ -281,3 +281,77 @@ def test_solve_and_full_space_form_on_config0():
     assert abs(it - it2) <= 1
     assert it < it1                                       # two-level beats S1
     assert np.allclose(x, spla.spsolve(sp.csc_matrix(P.A), b), rtol=1e-6, atol=1e-7)
+
+
+# ---------------------------------------------------------------- M_{2A-DEF} (§4.3)
+def _rgamma_definition(D, U):
+    # eq. (deflation_comp_from_low_rank) and eq. (our_two_level_preconditioner) written with
+    # the dense Cholesky factor A_G = R^T R and the transformed basis Ub = R^{-T} U
+    R = np.linalg.cholesky(D.A_G.toarray()).T
+    Ri = np.linalg.inv(R)
+    S = D.dense_S_gamma()
+    Sh = Ri.T @ S @ Ri
+    Ub = Ri.T @ U
+    E = Ub.T @ Sh @ Ub
+    Q = Ub @ np.linalg.solve(E, Ub.T)
+    Pdef = np.eye(D.n_G) - Q @ Sh + Q
+    return Ri @ Pdef @ Ri.T
+
+
+def test_m2adef_equals_rgamma_form_of_the_paper():
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=5)
+    D = O.DBBD(A, part)
+    G = np.random.default_rng(21).standard_normal((D.n_G, 9))
+    M, info = O.build_m2(D, G, k=6, eps_inner=0.1, variant="M2_ADEF")
+    ref = _rgamma_definition(D, info["U"])
+    assert np.allclose(M.dense(), ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
+
+
+def test_m2adef_deflation_identity():
+    # Z^T S_G M = Z^T for any basis Z: the correction is S_G-orthogonal to span(Z)
+    A, part = tiny((12, 12), 2, lognormal=(4.0, 1.0), seed=6)
+    D = O.DBBD(A, part)
+    Z = np.random.default_rng(22).standard_normal((D.n_G, 4))
+    M = O.M2ADEF(D, Z)
+    S = D.dense_S_gamma()
+    assert np.allclose(Z.T @ S @ M.dense(), Z.T, rtol=1e-9, atol=1e-9 * np.abs(Z).max())
+
+
+def test_m2adef_moves_deflated_eigenvalues_to_one():
+    # Z = k exact generalized eigenvectors of (S_G, A_G) for the smallest eigenvalues:
+    # Lambda(M S_G) = {1 (k times)} and the other n_G - k eigenvalues unchanged
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=7)
+    D = O.DBBD(A, part)
+    S = D.dense_S_gamma()
+    lam, V = sla.eigh(S, D.A_G.toarray())
+    k = 5
+    mu = np.sort(np.linalg.eigvals(O.M2ADEF(D, V[:, :k]).dense() @ S).real)
+    want = np.sort(np.concatenate([np.ones(k), lam[k:]]))
+    assert np.allclose(mu, want, rtol=1e-8, atol=1e-9)
+
+
+def test_m2adef_exact_when_rank_captured():
+    A, part, D = _small_problem()
+    s = D.n_G + 2
+    G = np.random.default_rng(23).standard_normal((D.n_G, s))
+    M, _ = O.build_m2(D, G, k=s, eps_inner=1e-14, eps_rel=1e-13, variant="M2_ADEF")
+    Sinv = np.linalg.inv(D.dense_S_gamma())
+    assert np.allclose(M.dense(), Sinv, rtol=1e-7, atol=1e-9 * np.abs(Sinv).max())
+    b = np.random.default_rng(24).standard_normal(D.n)
+    x, it, _ = O.solve(D, M.apply, b, rtol=1e-10)
+    assert it <= 2
+    assert O.relative_residual(A, x, b) < 1e-9
+
+
+def test_m2adef_iterations_close_to_m2_on_config0():
+    # Table (compare_variations): M2 and M_{2A-DEF} need nearly the same outer iterations
+    P = F.make_problem(0)
+    D = O.DBBD(P.A, P.part, P.nsub)
+    G = F.make_sketch(D.n_G, P.s, 0)
+    _, b = F.make_rhs(P, 0)
+    M2, _ = O.build_m2(D, G, P.k, P.eps_inner)
+    Ma, _ = O.build_m2(D, G, P.k, P.eps_inner, variant="M2_ADEF")
+    x2, it2, _ = O.solve(D, M2.apply, b, rtol=1e-8)
+    xa, ita, _ = O.solve(D, Ma.apply, b, rtol=1e-8)
+    assert O.relative_residual(P.A, xa, b) < 1e-7
+    assert abs(ita - it2) <= 2
