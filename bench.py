@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="nsp", choices=["nsp", "reference"])
     ap.add_argument("--config", type=int, default=1)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--variant", default="m2", choices=["m2", "m2_adef"],
+                    help="preconditioner of the timed step (§4.3: M2 or M_2A-DEF)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-reps", type=int, default=20)
     ap.add_argument("--profile", action="store_true",
@@ -275,7 +277,7 @@ def main():
 
     t0 = time.perf_counter()
     h = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
-                    precision=args.precision, seed=seed)
+                    precision=args.precision, seed=seed, variant=args.variant)
     torch.cuda.synchronize()
     build_first_ms = (time.perf_counter() - t0) * 1e3
     info0 = h.info()
@@ -387,11 +389,41 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h2 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
-                     precision=args.precision, seed=seed)
+                     precision=args.precision, seed=seed, variant=args.variant)
     h2.solve(b_h, x_h, rtol=P.rtol, maxit=500)
     torch.cuda.synchronize()
     full_ms = (time.perf_counter() - t0) * 1e3
     h2.destroy()
+
+    # ---- the other preconditioner of §4.3 on the same workload (device-timed like the step)
+    other = "m2_adef" if args.variant == "m2" else "m2"
+    h3 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                     precision=args.precision, seed=seed, variant=other)
+
+    def step3():
+        h3.rebuild(val_d, on_device=True)
+        return h3.solve(b_d, x_d, rtol=P.rtol, maxit=500)
+
+    for _ in range(2):
+        step3()
+    torch.cuda.synchronize()
+    v_ms, v_infos = [], []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        a0.record(stream)
+        v_infos.append(step3())
+        a1.record(stream)
+        torch.cuda.synchronize()
+        v_ms.append(a0.elapsed_time(a1))
+    v_res = float(np.linalg.norm(b - P.A @ x_d.cpu().numpy()) / np.linalg.norm(b))
+    variant_line = {"variant": other, "ms_per_step": float(np.mean(v_ms)),
+                    "it_inner": v_infos[-1]["it_inner"], "it_pcg": v_infos[-1]["it_pcg"],
+                    "final_residual": v_res,
+                    "phase_ms": {"factor": v_infos[-1]["ms_factor"],
+                                 "inner": v_infos[-1]["ms_inner"],
+                                 "core": v_infos[-1]["ms_core"],
+                                 "solve": v_infos[-1]["ms_solve"]}}
+    h3.destroy()
 
     out = None
     if rank == 0:
@@ -413,7 +445,7 @@ def main():
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": dict(workload_config(P, args),
+            "config": dict(workload_config(P, args), variant=args.variant,
                            analyze_ms=info0["ms_analyze"], first_build_ms=build_first_ms,
                            it_inner=last["it_inner"], it_pcg=last["it_pcg"],
                            rank=last["rank"], final_residual=res,
@@ -434,6 +466,7 @@ def main():
                             "apply_ms": apply_ms, "algorithmic_bytes": nbytes,
                             "what": "S_Gamma X: A_IG SpMM + interior sweep + A_G/A_GI SpMM "
                                     "(s=%d, %s)" % (s, args.precision)},
+            "other_variant": variant_line,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),

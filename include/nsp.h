@@ -66,6 +66,21 @@ typedef enum { NSP_OUTER_AUTO = 0, NSP_OUTER_SCHUR = 1, NSP_OUTER_FULL = 2 } nsp
  *                    (§4.1 eq. (S-1)) Y = A_GI S_I^{-1} A_IG G, the Y of Algorithm 2. */
 typedef enum { NSP_FORM_SGAMMA = 0 } nsp_inner_form;
 
+/* Preconditioner built from the Nyström factor (§4.3):
+ *  NSP_VARIANT_M2      : M2 = A_G^{-1} + Z Sigma Z^T, Z = A_G^{-1} U (eq. (left_prec_mat),
+ *                        Algorithm 2 step 12).
+ *  NSP_VARIANT_M2_ADEF : M_{2A-DEF}, the adapted-deflation form that §4.3 defines like
+ *                        eq. (deflation_comp_from_low_rank) / eq. (our_two_level_preconditioner)
+ *                        for M2's approximation. Written without R_G (Z = A_G^{-1} U,
+ *                        E = Z^T S_G Z, k x k):  M = (I - Z E^{-1} Z^T S_G) A_G^{-1} + Z E^{-1} Z^T.
+ *                        The build adds one S_G apply on k columns and a k x k Cholesky
+ *                        (columns of E whose pivot falls below drop_tol of their diagonal are
+ *                        left out of the deflation space); each application costs the A_G
+ *                        solve of M2 plus three length-n_G products with k columns. M is not
+ *                        symmetric; the outer PCG uses it as is, as §5 does. Single handles
+ *                        only: nsp_build_batched returns NSP_ERR_UNSUPPORTED for it. */
+typedef enum { NSP_VARIANT_M2 = 0, NSP_VARIANT_M2_ADEF = 1 } nsp_variant;
+
 /* Sparse matrix in CSR. Full symmetric pattern (both triangles) with sorted column
  * indices and no duplicates. rowptr has n+1 entries. Host pointers unless on_device. */
 typedef struct {
@@ -103,6 +118,8 @@ typedef struct {
   int32_t inner_form;        /* nsp_inner_form                                            */
   int32_t keep_intermediates;/* 1: keep E, Y, U of Algorithm 2 for nsp_get_intermediate  */
   void *stream;              /* cudaStream_t for all device work (NULL = default stream)  */
+  int32_t variant;           /* nsp_variant (default NSP_VARIANT_M2); other values:
+                                NSP_ERR_INVALID_ARG                                        */
 } nsp_params;
 
 typedef struct {
@@ -167,11 +184,12 @@ nsp_status nsp_solve_batched(const nsp_handle *h, const double *b, double *x, do
 
 /* Repeat the numeric part of nsp_build (factorization + Algorithm 2) for new values of A
  * with the same pattern (val has nnz entries in the CSR order given to nsp_build; device
- * memory if on_device). prm may change k, p, tolerances, seed, sketch (not precision). */
+ * memory if on_device). prm may change k, p, tolerances, seed, sketch, variant (not precision). */
 nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device,
                        const nsp_params *prm);
 
-/* z = M2 r = A_G^{-1} r + Z Sigma Z^T r (Algorithm 2 step 12). r, z: n_Gamma doubles in
+/* z = M2 r = A_G^{-1} r + Z Sigma Z^T r (Algorithm 2 step 12), or z = M_{2A-DEF} r when the
+ * handle was built with NSP_VARIANT_M2_ADEF (see nsp_variant). r, z: n_Gamma doubles in
  * Gamma order, device pointers, may not alias. */
 nsp_status nsp_apply(const nsp_handle *h, const double *r_gamma, double *z_gamma);
 

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libnsp.so")
 
 NSP_FP64, NSP_FP32 = 0, 1
 NSP_OUTER_AUTO, NSP_OUTER_SCHUR, NSP_OUTER_FULL = 0, 1, 2
+NSP_VARIANT_M2, NSP_VARIANT_M2_ADEF = 0, 1
 STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_ERR_NOT_SPD",
           4: "NSP_ERR_BREAKDOWN", 5: "NSP_ERR_NOT_CONVERGED", 6: "NSP_ERR_TIMEOUT",
           7: "NSP_ERR_CUDA", 8: "NSP_ERR_OOM", 9: "NSP_ERR_UNSUPPORTED"}
@@ -50,7 +51,8 @@ class nsp_params(C.Structure):
                 ("eps_trunc_rel", C.c_double), ("drop_tol", C.c_double),
                 ("max_inner_it", C.c_int32), ("seed", C.c_uint64), ("sketch", C.c_void_p),
                 ("precision", C.c_int32), ("outer_form", C.c_int32), ("inner_form", C.c_int32),
-                ("keep_intermediates", C.c_int32), ("stream", C.c_void_p)]
+                ("keep_intermediates", C.c_int32), ("stream", C.c_void_p),
+                ("variant", C.c_int32)]
 
 
 class nsp_net_shape(C.Structure):
@@ -184,7 +186,8 @@ def nsp_default_params():
 
 def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                 max_inner_it=500, seed=210112164, sketch=None, precision="fp32",
-                outer_form="auto", keep_intermediates=False, stream=None, keep=None):
+                outer_form="auto", keep_intermediates=False, stream=None, keep=None,
+                variant="m2"):
     prm = nsp_default_params()
     prm.k, prm.p = int(k), int(p)
     prm.eps_inner, prm.eps_trunc_rel = float(eps_inner), float(eps_trunc_rel)
@@ -196,6 +199,7 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
     prm.outer_form = {"auto": NSP_OUTER_AUTO, "schur": NSP_OUTER_SCHUR,
                       "full": NSP_OUTER_FULL}[outer_form]
     prm.keep_intermediates = 1 if keep_intermediates else 0
+    prm.variant = {"m2": NSP_VARIANT_M2, "m2_adef": NSP_VARIANT_M2_ADEF}[variant]
     if sketch is not None:
         if hasattr(sketch, "data_ptr"):   # device tensor: passed through (float64, contiguous)
             if str(sketch.dtype) != "torch.float64" or not sketch.is_contiguous():

@@ -774,6 +774,9 @@ struct Engine : EngineBase {
     require(s <= 256, NSP_ERR_UNSUPPORTED, "k + p > 256");
     require(s <= an.nG, NSP_ERR_INVALID_ARG, "k + p exceeds the interface size");
     require(prm.inner_form == NSP_FORM_SGAMMA, NSP_ERR_UNSUPPORTED, "inner form");
+    require(prm.variant == NSP_VARIANT_M2 || prm.variant == NSP_VARIANT_M2_ADEF,
+            NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
+    variant = prm.variant;
     keep = prm.keep_intermediates != 0;
     ensure_ws(s);
     const size_t ns = (size_t)an.nG * s;
@@ -873,9 +876,36 @@ struct Engine : EngineBase {
       solve_G(U.p, Zt.p, k);
       launch_gather_rows<T, double>(nullptr, an.nG, Zt.p, Zs.p, k, st);
       launch_scale_cols(Zs.p, an.nG, k, Sigma.p, true, st);
+      if (variant == NSP_VARIANT_M2_ADEF) build_adef(prm.drop_tol);
       sync();
     }
     info.ms_core = ms_since(t1);
+  }
+
+  // ---- M_{2A-DEF} (§4.3): M = (I - Q S_G) A_G^{-1} + Q with Q = Zk E^{-1} Zk^T,
+  // Zk = A_G^{-1} U and E = Zk^T S_G Zk. With E = L L^T (columns whose pivot falls below
+  // drop_tol of their diagonal are dropped), Zd = Zk L^{-T} gives Q = Zd Zd^T, and
+  // Wd = S_G Zd turns the S_G A_G^{-1} r of every application into Wd^T (A_G^{-1} r):
+  // one S_G apply on k columns here, none per application.
+  int variant = NSP_VARIANT_M2;
+  DBuf<T> adefS;
+  DBuf<double> Zd, Wd, adefT, Ead, Rad;
+  DBuf<int32_t> adef_mask, adef_nk;
+  void build_adef(double drop_tol) {
+    const size_t nk = (size_t)an.nG * k;
+    adefS.ensure(nk);
+    for (DBuf<double> *b : {&Zd, &Wd, &adefT}) b->ensure(nk);
+    Ead.ensure((size_t)k * k);
+    Rad.ensure((size_t)k * k);
+    adef_mask.ensure(k);
+    adef_nk.ensure(1);
+    schur_apply(Zt.p, adefS.p, k, true);                     // S_G Zk (handle precision)
+    gram_acc64(Zt.p, adefS.p, k, k, Ead.p);                  // E = Zk^T S_G Zk
+    launch_chol_drop(Ead.p, k, drop_tol, Rad.p, adef_mask.p, adef_nk.p, Lwork.p, st);
+    launch_gather_rows<T, double>(nullptr, an.nG, Zt.p, adefT.p, k, st);
+    launch_block_update<double>(adefT.p, Rad.p, an.nG, k, k, 1.0, nullptr, 0.0, Zd.p, st);
+    launch_gather_rows<T, double>(nullptr, an.nG, adefS.p, adefT.p, k, st);
+    launch_block_update<double>(adefT.p, Rad.p, an.nG, k, k, 1.0, nullptr, 0.0, Wd.p, st);
   }
 
   // ---- M2 r = A_G^{-1} r + Z Sigma Z^T r (internal order, FP64 in/out)
@@ -894,7 +924,14 @@ struct Engine : EngineBase {
       solve_G(sT.p, sT2.p, 1);
       launch_gather_rows<T, double>(nullptr, an.nG, sT2.p, z, 1, st);
     }
-    if (rank > 0) {
+    if (rank > 0 && variant == NSP_VARIANT_M2_ADEF) {
+      // z = y + Zd (Zd^T r - Wd^T y) with y = A_G^{-1} r already in z
+      zt_vec.ensure(2 * (size_t)k);
+      launch_gemv_t(Zd.p, an.nG, k, r, zt_vec.p, dwork.p, st);
+      launch_gemv_t(Wd.p, an.nG, k, z, zt_vec.p + k, dwork.p, st);
+      launch_axpby(k, nullptr, -1.0, zt_vec.p + k, 1.0, zt_vec.p, st);
+      launch_gemv_n(Zd.p, an.nG, k, zt_vec.p, 1.0, z, st);
+    } else if (rank > 0) {
       zt_vec.ensure(k);
       launch_gemv_t(Zs.p, an.nG, k, r, zt_vec.p, dwork.p, st);
       launch_gemv_n(Zs.p, an.nG, k, zt_vec.p, 1.0, z, st);
@@ -1114,6 +1151,8 @@ struct Engine : EngineBase {
   }
 
   void construct_batched(const nsp_params &prm) override {
+    require(prm.variant == NSP_VARIANT_M2, NSP_ERR_UNSUPPORTED,
+            "batched handles build M2 only");
     auto t0 = Clock::now();
     require(prm.k > 0 && prm.p >= 0, NSP_ERR_INVALID_ARG, "k > 0 and p >= 0 required");
     s = prm.k + prm.p;
