@@ -14,7 +14,8 @@ Everything here is plain, slow and follows the paper step by step in float64:
                              the docstring).
 * ``nystrom_core``         : Algorithm 2 steps 5-10 (= Algorithm 1 steps 3-8).
 * ``build_m2``             : Algorithm 2, in the paper's S_I form (step 3) or the
-                             equivalent S_Gamma correction form (SMW identity, §4.1 eq. (S-1)).
+                             equivalent S_Gamma correction form (SMW identity, §4.1 eq. (S-1)),
+                             optionally with q power iterations (§2.1 eq. (power)).
 * ``M2ADEF``               : the adapted-deflation variant M_{2A-DEF} of §4.3 (defined
                              like eq. (deflation_comp_from_low_rank) and eq.
                              (our_two_level_preconditioner), moved through Z = A_G^{-1} U).
@@ -259,23 +260,9 @@ class M2ADEF:
         return self.apply(np.eye(n))
 
 
-def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500,
-             drop_tol=1e-12, variant="M2"):
-    """Algorithm 2. Returns (M2, info); variant="M2_ADEF" returns M_{2A-DEF} (class
-    M2ADEF) built from the same Z = A_G^{-1} U.
-
-    form="S_I":     F = A_IG G (step 2); solve S_I X = F by block PCG preconditioned by
-                    A_I (step 3, §5 setup); Y = A_GI X (step 4).
-    form="S_gamma": the same Y through the interface Schur complement. With
-                    T = A_GI A_I^{-1} A_IG (so S_Gamma = A_G - T) and the SMW
-                    identity (§4.1 eq. (S-1)), A_G S_Gamma^{-1} T = A_G S_Gamma^{-1} A_G - A_G
-                    = A_GI S_I^{-1} A_IG. So: Fh = T G; solve S_Gamma E = Fh by block PCG
-                    preconditioned by A_G (the first level S1, §2.3 eq. (S1)); Y = A_G E.
-    form="S_gamma_naive": solve S_Gamma Xh = A_G G, Y = A_G Xh - A_G G (same Y for exact
-                    solves, but the relative tolerance is measured against the trivial part
-                    A_G G of the right-hand side, so a loose tolerance stops too early).
-    """
-    G = np.asarray(G, dtype=np.float64)
+def sketch_product(dbbd, G, eps_inner=0.1, form="S_gamma", maxit=500, drop_tol=1e-12):
+    """Algorithm 2 steps 2-4: Y = A_GI S_I^{-1} A_IG G through the inner block PCG.
+    Returns (X, Y, iterations, residual history); the forms are those of build_m2."""
     if form == "S_I":
         F = dbbd.A_IG @ G
         X, it, hist = block_pcg(dbbd.apply_S_I, dbbd.solve_I, F, eps_inner, maxit, drop_tol)
@@ -292,9 +279,41 @@ def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500
         Y = dbbd.A_G @ X - AG
     else:
         raise ValueError(form)
+    return X, Y, it, hist
+
+
+def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500,
+             drop_tol=1e-12, variant="M2", q=0):
+    """Algorithm 2. Returns (M2, info); variant="M2_ADEF" returns M_{2A-DEF} (class
+    M2ADEF) built from the same Z = A_G^{-1} U.
+
+    q > 0: the q-power iteration Nyström method of §2.1 eq. (power), G = B^q Omega with
+    B = A_GI S_I^{-1} A_IG and Omega the given sketch, the columns orthonormalized after
+    every application of B (thresholded Cholesky-QR ``orth``; a column that falls in the
+    span of the others is dropped). Each application of B is one inner block PCG (steps 2-4)
+    and the last one gives the Y of step 4 for the final G.
+
+    form="S_I":     F = A_IG G (step 2); solve S_I X = F by block PCG preconditioned by
+                    A_I (step 3, §5 setup); Y = A_GI X (step 4).
+    form="S_gamma": the same Y through the interface Schur complement. With
+                    T = A_GI A_I^{-1} A_IG (so S_Gamma = A_G - T) and the SMW
+                    identity (§4.1 eq. (S-1)), A_G S_Gamma^{-1} T = A_G S_Gamma^{-1} A_G - A_G
+                    = A_GI S_I^{-1} A_IG. So: Fh = T G; solve S_Gamma E = Fh by block PCG
+                    preconditioned by A_G (the first level S1, §2.3 eq. (S1)); Y = A_G E.
+    form="S_gamma_naive": solve S_Gamma Xh = A_G G, Y = A_G Xh - A_G G (same Y for exact
+                    solves, but the relative tolerance is measured against the trivial part
+                    A_G G of the right-hand side, so a loose tolerance stops too early).
+    """
+    G = np.asarray(G, dtype=np.float64)
+    it_power = []
+    for _ in range(q):                                    # eq. (power)
+        _, Yq, itq, _ = sketch_product(dbbd, G, eps_inner, form, maxit, drop_tol)
+        it_power.append(itq)
+        G = orth(Yq, drop_tol)
+    X, Y, it, hist = sketch_product(dbbd, G, eps_inner, form, maxit, drop_tol)
     U, Sigma, info = nystrom_core(G, Y, k, eps_rel)       # steps 5-10
     Z = dbbd.solve_G(U)                                   # step 11
-    info.update(it_inner=it, inner_hist=hist, X=X, Y=Y, U=U)
+    info.update(it_inner=it, inner_hist=hist, X=X, Y=Y, U=U, G=G, it_power=it_power)
     if variant == "M2_ADEF":
         return M2ADEF(dbbd, Z, Sigma), info
     if variant != "M2":

@@ -355,3 +355,44 @@ def test_m2adef_iterations_close_to_m2_on_config0():
     xa, ita, _ = O.solve(D, Ma.apply, b, rtol=1e-8)
     assert O.relative_residual(P.A, xa, b) < 1e-7
     assert abs(ita - it2) <= 2
+
+
+# ---------------------------------------------------------------- power iteration (§2.1)
+def _dense_B(A, D):
+    # the matrix Algorithm 2 approximates, B = A_GI S_I^{-1} A_IG (§4.3 eq.
+    # (internal_term_lr_approximation_1)), with S_I^{-1} the interior block of A^{-1}
+    Ainv = np.linalg.inv(A.toarray())
+    SIinv = Ainv[np.ix_(D.interior, D.interior)]
+    return D.A_GI.toarray() @ SIinv @ D.A_IG.toarray()
+
+
+@pytest.mark.parametrize("q", [1, 2])
+def test_power_nystrom_matches_definition(q):
+    # eq. (NystromApprox) with eq. (power), G = B^q Omega formed without orthonormalization
+    A, part = tiny((12, 12), 2, lognormal=(4.0, 1.0), seed=8)
+    D = O.DBBD(A, part)
+    B = _dense_B(A, D)
+    s = 5
+    Om = np.random.default_rng(31).standard_normal((D.n_G, s))
+    G = np.linalg.matrix_power(B, q) @ Om
+    BG = B @ G
+    ref = BG @ np.linalg.solve(G.T @ BG, BG.T)
+    M, info = O.build_m2(D, Om, k=s, eps_inner=1e-14, eps_rel=1e-13, q=q)
+    got = (info["U"] * M.Sigma) @ info["U"].T
+    assert len(info["it_power"]) == q
+    assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_power_iteration_sharpens_the_approximation():
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=9)
+    D = O.DBBD(A, part)
+    B = _dense_B(A, D)
+    Om = np.random.default_rng(32).standard_normal((D.n_G, 8))
+    err = []
+    for q in (0, 1, 2):
+        M, info = O.build_m2(D, Om, k=6, eps_inner=1e-14, eps_rel=1e-13, q=q)
+        err.append(np.linalg.norm(B - (info["U"] * M.Sigma) @ info["U"].T, 2))
+    assert err[2] < err[0] and err[1] < err[0]
+    # the rank-6 truncation can do no better than the best rank-6 approximation
+    lam = np.sort(np.linalg.eigvalsh(B))[::-1]
+    assert min(err) >= lam[6] * (1 - 1e-8)
