@@ -395,35 +395,37 @@ def main():
     full_ms = (time.perf_counter() - t0) * 1e3
     h2.destroy()
 
-    # ---- the other preconditioner of §4.3 on the same workload (device-timed like the step)
-    other = "m2_adef" if args.variant == "m2" else "m2"
-    h3 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
-                     precision=args.precision, seed=seed, variant=other)
+    # ---- the other preconditioner of §4.3, and one power iteration (§2.1 eq. (power)), on
+    # the same workload, device-timed like the step
+    def time_variant(**kw):
+        h3 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                         precision=args.precision, seed=seed, **kw)
 
-    def step3():
-        h3.rebuild(val_d, on_device=True)
-        return h3.solve(b_d, x_d, rtol=P.rtol, maxit=500)
+        def step3():
+            h3.rebuild(val_d, on_device=True)
+            return h3.solve(b_d, x_d, rtol=P.rtol, maxit=500)
 
-    for _ in range(2):
-        step3()
-    torch.cuda.synchronize()
-    v_ms, v_infos = [], []
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        a0.record(stream)
-        v_infos.append(step3())
-        a1.record(stream)
+        for _ in range(2):
+            step3()
         torch.cuda.synchronize()
-        v_ms.append(a0.elapsed_time(a1))
-    v_res = float(np.linalg.norm(b - P.A @ x_d.cpu().numpy()) / np.linalg.norm(b))
-    variant_line = {"variant": other, "ms_per_step": float(np.mean(v_ms)),
-                    "it_inner": v_infos[-1]["it_inner"], "it_pcg": v_infos[-1]["it_pcg"],
-                    "final_residual": v_res,
-                    "phase_ms": {"factor": v_infos[-1]["ms_factor"],
-                                 "inner": v_infos[-1]["ms_inner"],
-                                 "core": v_infos[-1]["ms_core"],
-                                 "solve": v_infos[-1]["ms_solve"]}}
-    h3.destroy()
+        v_ms, v_infos = [], []
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            a0.record(stream)
+            v_infos.append(step3())
+            a1.record(stream)
+            torch.cuda.synchronize()
+            v_ms.append(a0.elapsed_time(a1))
+        v_res = float(np.linalg.norm(b - P.A @ x_d.cpu().numpy()) / np.linalg.norm(b))
+        last = v_infos[-1]
+        h3.destroy()
+        return dict(kw, ms_per_step=float(np.mean(v_ms)), it_inner=last["it_inner"],
+                    it_power=last["it_power"], it_pcg=last["it_pcg"], final_residual=v_res,
+                    phase_ms={"factor": last["ms_factor"], "inner": last["ms_inner"],
+                              "core": last["ms_core"], "solve": last["ms_solve"]})
+
+    variant_line = time_variant(variant="m2_adef" if args.variant == "m2" else "m2")
+    power_line = time_variant(variant=args.variant, q=1)
 
     out = None
     if rank == 0:
@@ -467,6 +469,7 @@ def main():
                             "what": "S_Gamma X: A_IG SpMM + interior sweep + A_G/A_GI SpMM "
                                     "(s=%d, %s)" % (s, args.precision)},
             "other_variant": variant_line,
+            "power_q1": power_line,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),

@@ -120,6 +120,12 @@ typedef struct {
   void *stream;              /* cudaStream_t for all device work (NULL = default stream)  */
   int32_t variant;           /* nsp_variant (default NSP_VARIANT_M2); other values:
                                 NSP_ERR_INVALID_ARG                                        */
+  int32_t q;                 /* power iterations (§2.1 eq. (power)), 0 <= q <= 16, default 0:
+                                G = B^q Omega with B = A_GI S_I^{-1} A_IG and Omega the drawn
+                                or given sketch; each application of B is one inner block PCG
+                                (steps 2-4) and the columns are orthonormalized after it by
+                                Cholesky-QR (a column whose pivot falls below drop_tol of its
+                                squared norm becomes zero). Batched handles: q = 0 only      */
 } nsp_params;
 
 typedef struct {
@@ -137,6 +143,8 @@ typedef struct {
   double pcg_residual;       /* updated-residual ratio ||r|| / ||f|| at exit              */
   int32_t failed_block;      /* block id for NSP_ERR_NOT_SPD (nblocks = the A_G factor)   */
   double ms_analyze, ms_factor, ms_inner, ms_core, ms_solve;   /* host wall times (ms)     */
+  int32_t it_power;          /* block-PCG iterations of the q power passes (it_inner is the
+                                final pass's)                                              */
 } nsp_info;
 
 typedef struct nsp_handle nsp_handle;

@@ -52,7 +52,7 @@ class nsp_params(C.Structure):
                 ("max_inner_it", C.c_int32), ("seed", C.c_uint64), ("sketch", C.c_void_p),
                 ("precision", C.c_int32), ("outer_form", C.c_int32), ("inner_form", C.c_int32),
                 ("keep_intermediates", C.c_int32), ("stream", C.c_void_p),
-                ("variant", C.c_int32)]
+                ("variant", C.c_int32), ("q", C.c_int32)]
 
 
 class nsp_net_shape(C.Structure):
@@ -70,7 +70,7 @@ class nsp_info(C.Structure):
                 ("final_residual", C.c_double), ("pcg_residual", C.c_double),
                 ("failed_block", C.c_int32), ("ms_analyze", C.c_double),
                 ("ms_factor", C.c_double), ("ms_inner", C.c_double), ("ms_core", C.c_double),
-                ("ms_solve", C.c_double)]
+                ("ms_solve", C.c_double), ("it_power", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -187,7 +187,7 @@ def nsp_default_params():
 def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                 max_inner_it=500, seed=210112164, sketch=None, precision="fp32",
                 outer_form="auto", keep_intermediates=False, stream=None, keep=None,
-                variant="m2"):
+                variant="m2", q=0):
     prm = nsp_default_params()
     prm.k, prm.p = int(k), int(p)
     prm.eps_inner, prm.eps_trunc_rel = float(eps_inner), float(eps_trunc_rel)
@@ -200,6 +200,7 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                       "full": NSP_OUTER_FULL}[outer_form]
     prm.keep_intermediates = 1 if keep_intermediates else 0
     prm.variant = {"m2": NSP_VARIANT_M2, "m2_adef": NSP_VARIANT_M2_ADEF}[variant]
+    prm.q = int(q)
     if sketch is not None:
         if hasattr(sketch, "data_ptr"):   # device tensor: passed through (float64, contiguous)
             if str(sketch.dtype) != "torch.float64" or not sketch.is_contiguous():

@@ -777,6 +777,7 @@ struct Engine : EngineBase {
     require(prm.variant == NSP_VARIANT_M2 || prm.variant == NSP_VARIANT_M2_ADEF,
             NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
     variant = prm.variant;
+    require(prm.q >= 0 && prm.q <= 16, NSP_ERR_INVALID_ARG, "power iterations q in [0, 16]");
     keep = prm.keep_intermediates != 0;
     ensure_ws(s);
     const size_t ns = (size_t)an.nG * s;
@@ -808,55 +809,69 @@ struct Engine : EngineBase {
       launch_gather_rows<double, T>(i2u_G.p, an.nG, g64.p, G.p, s, st);
       sync();
     }
-    // steps 2-3: block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G, preconditioner A_G^{-1}
-    schur_apply(G.p, Fh.p, s, false);
-    launch_col_sumsq<T>(Fh.p, an.nG, s, colsq.p, gram_work.p, st);
-    launch_sqrt_vec(colsq.p, s, bnorm.p, st);
-    // Breakdown-free block PCG (the paper's inner solver, §5.1) with search directions kept
-    // S_Gamma-orthonormal: W spans the new directions, Qw = S W, C = W^T Qw = L L^T (columns
-    // whose pivot falls below drop_tol are dropped), P = W L^{-T}, Q = Qw L^{-T}, so that
-    // P^T Q = I and alpha = P^T R, beta = -Q^T Z need no s x s solve. The block Krylov
-    // space, hence every iterate E, is the one of the 2-norm-orthonormal form.
-    NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
-    NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
-    solve_G(R.p, W.p, s);                 // W = Z0 = A_G^{-1} R0
-    int it = 0;
+    // q-power iteration (§2.1 eq. (power)): passes 0..q-1 apply B = A_GI S_I^{-1} A_IG to G
+    // by steps 2-4 and replace G by an orthonormal basis of B G (thresholded Cholesky-QR,
+    // dropped columns become zero columns); pass q gives the Y of step 4 for the final G.
+    int it_power = 0, it = 0, active = s;
     double rat = 1.0;
-    int active = s;
-    while (it < prm.max_inner_it) {
-      schur_apply(W.p, Z.p, s, true);     // Z holds Qw = S W
-      gram(W.p, Z.p, s, s, Cg.p);
-      launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
-      launch_block_update<T>(W.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
-      launch_block_update<T>(Z.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), Q.p, st);
-      gram(P.p, R.p, s, s, alpha.p);      // alpha = P^T R
-      launch_block_update<T>(P.p, alpha.p, an.nG, s, s, T(1), E.p, T(1), E.p, st);
-      launch_block_update<T>(Q.p, alpha.p, an.nG, s, s, T(-1), R.p, T(1), R.p, st);
-      ++it;
-      launch_col_sumsq<T>(R.p, an.nG, s, colsq.p, gram_work.p, st);
-      launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st);
-      NSP_CUDA(cudaMemcpyAsync(hscal, ratio.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-      NSP_CUDA(cudaMemcpyAsync(hint, nkept.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      sync();
-      rat = hscal[0];
-      active = hint[0];
-      if (active == 0) {  // no search direction left: the last pass changed nothing
-        --it;
-        break;
+    for (int pass = 0; pass <= prm.q; ++pass) {
+      if (pass > 0) {
+        it_power += it;
+        gram_acc64(Y.p, Y.p, s, s, K.p);
+        launch_chol_drop(K.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
+        launch_block_update<T>(Y.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), G.p, st);
       }
-      if (!(rat > prm.eps_inner)) break;
-      solve_G(R.p, Z.p, s);               // Z = A_G^{-1} R
-      gram(Q.p, Z.p, s, s, beta.p);       // Q^T Z
-      launch_block_update<T>(P.p, beta.p, an.nG, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
+      // steps 2-3: block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G, preconditioner A_G^{-1}
+      schur_apply(G.p, Fh.p, s, false);
+      launch_col_sumsq<T>(Fh.p, an.nG, s, colsq.p, gram_work.p, st);
+      launch_sqrt_vec(colsq.p, s, bnorm.p, st);
+      // Breakdown-free block PCG (the paper's inner solver, §5.1) with search directions kept
+      // S_Gamma-orthonormal: W spans the new directions, Qw = S W, C = W^T Qw = L L^T (columns
+      // whose pivot falls below drop_tol are dropped), P = W L^{-T}, Q = Qw L^{-T}, so that
+      // P^T Q = I and alpha = P^T R, beta = -Q^T Z need no s x s solve. The block Krylov
+      // space, hence every iterate E, is the one of the 2-norm-orthonormal form.
+      NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
+      NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      solve_G(R.p, W.p, s);                 // W = Z0 = A_G^{-1} R0
+      it = 0;
+      rat = 1.0;
+      active = s;
+      while (it < prm.max_inner_it) {
+        schur_apply(W.p, Z.p, s, true);     // Z holds Qw = S W
+        gram(W.p, Z.p, s, s, Cg.p);
+        launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
+        launch_block_update<T>(W.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
+        launch_block_update<T>(Z.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), Q.p, st);
+        gram(P.p, R.p, s, s, alpha.p);      // alpha = P^T R
+        launch_block_update<T>(P.p, alpha.p, an.nG, s, s, T(1), E.p, T(1), E.p, st);
+        launch_block_update<T>(Q.p, alpha.p, an.nG, s, s, T(-1), R.p, T(1), R.p, st);
+        ++it;
+        launch_col_sumsq<T>(R.p, an.nG, s, colsq.p, gram_work.p, st);
+        launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st);
+        NSP_CUDA(cudaMemcpyAsync(hscal, ratio.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        NSP_CUDA(cudaMemcpyAsync(hint, nkept.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        sync();
+        rat = hscal[0];
+        active = hint[0];
+        if (active == 0) {  // no search direction left: the last pass changed nothing
+          --it;
+          break;
+        }
+        if (!(rat > prm.eps_inner)) break;
+        solve_G(R.p, Z.p, s);               // Z = A_G^{-1} R
+        gram(Q.p, Z.p, s, s, beta.p);       // Q^T Z
+        launch_block_update<T>(P.p, beta.p, an.nG, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
+      }
+      check_status();
+      // step 4: Y = A_G E (= A_GI S_I^{-1} A_IG G)
+      launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
     }
-    check_status();
     info.it_inner = it;
+    info.it_power = it_power;
     info.inner_residual = rat;
     info.inner_active_cols = active;
     info.ms_inner = ms_since(t0);
     auto t1 = Clock::now();
-    // step 4: Y = A_G E (= A_GI S_I^{-1} A_IG G)
-    launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
     // steps 5-10
     gram_acc64(Y.p, Y.p, s, s, K.p);
     gram_acc64(G.p, Y.p, s, s, Cn.p);
@@ -1153,6 +1168,7 @@ struct Engine : EngineBase {
   void construct_batched(const nsp_params &prm) override {
     require(prm.variant == NSP_VARIANT_M2, NSP_ERR_UNSUPPORTED,
             "batched handles build M2 only");
+    require(prm.q == 0, NSP_ERR_UNSUPPORTED, "batched handles take no power iterations");
     auto t0 = Clock::now();
     require(prm.k > 0 && prm.p >= 0, NSP_ERR_INVALID_ARG, "k > 0 and p >= 0 required");
     s = prm.k + prm.p;
