@@ -16,6 +16,7 @@ Everything here is plain, slow and follows the paper step by step in float64:
 * ``build_m2``             : Algorithm 2, in the paper's S_I form (step 3) or the
                              equivalent S_Gamma correction form (SMW identity, §4.1 eq. (S-1)),
                              optionally with q power iterations (§2.1 eq. (power)).
+* ``build_m3``             : the variant M3 of §4.3 (Nyström on S_I^{-1}), and M_{3A-DEF}.
 * ``M2ADEF``               : the adapted-deflation variant M_{2A-DEF} of §4.3 (defined
                              like eq. (deflation_comp_from_low_rank) and eq.
                              (our_two_level_preconditioner), moved through Z = A_G^{-1} U).
@@ -129,9 +130,9 @@ def block_cholesky(A_block, order):
 # <= drop_tol * (its squared norm) lies (numerically) in the span of the kept columns and
 # is dropped, so P loses columns instead of breaking down.
 # ----------------------------------------------------------------------------------------
-def orth(W, drop_tol=1e-12):
-    """Orthonormal basis of the columns of W kept by a thresholded Cholesky-QR."""
-    C = W.T @ W
+def kept_columns(C, drop_tol=1e-12):
+    """Columns j of the Gram matrix C whose pivot, after eliminating the columns kept before
+    j, exceeds drop_tol * C[j, j] (the rule of the thresholded Cholesky-QR below)."""
     s = C.shape[0]
     keep = []
     for j in range(s):
@@ -148,6 +149,13 @@ def orth(W, drop_tol=1e-12):
             piv = C[j, j]
         if piv > drop_tol * C[j, j]:
             keep.append(j)
+    return keep
+
+
+def orth(W, drop_tol=1e-12):
+    """Orthonormal basis of the columns of W kept by a thresholded Cholesky-QR."""
+    C = W.T @ W
+    keep = kept_columns(C, drop_tol)
     if not keep:
         return W[:, :0]
     R = np.linalg.cholesky(C[np.ix_(keep, keep)]).T       # upper: C_kk = R^T R
@@ -239,13 +247,18 @@ class M2ADEF:
     approximation A_GI S_I^{-1} A_IG ~ U Sigma U^T, whose transformed basis is R_G^{-T} U.
     With Zk = R_G^{-1} R_G^{-T} U = A_G^{-1} U (Algorithm 2 step 11) every R_G cancels:
         E = Zk^T S_G Zk,   M = A_G^{-1} - Zk E^{-1} Zk^T S_G A_G^{-1} + Zk E^{-1} Zk^T.
-    Sigma does not enter (Q is invariant under a change of basis of span(Zk)).
+    Sigma does not enter (Q is invariant under a change of basis of span(Zk)). A column of
+    Zk that is (numerically) in the span of the others is left out by the thresholded
+    Cholesky rule of ``kept_columns`` applied to E, which leaves span(Zk), hence Q, unchanged.
     """
 
-    def __init__(self, dbbd, Zk, Sigma=None):
-        self.dbbd, self.Z, self.Sigma = dbbd, np.asarray(Zk, dtype=np.float64), Sigma
-        self.E = self.Z.T @ dbbd.apply_S_gamma(self.Z)
-        self.E = 0.5 * (self.E + self.E.T)
+    def __init__(self, dbbd, Zk, Sigma=None, drop_tol=1e-12):
+        self.dbbd, self.Sigma = dbbd, Sigma
+        Z = np.asarray(Zk, dtype=np.float64)
+        E = Z.T @ dbbd.apply_S_gamma(Z)
+        E = 0.5 * (E + E.T)
+        keep = kept_columns(E, drop_tol)
+        self.Z, self.E = Z[:, keep], E[np.ix_(keep, keep)]
         self._Ec = sla.cho_factor(self.E, lower=True)
 
     def apply(self, r):
@@ -315,10 +328,32 @@ def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500
     Z = dbbd.solve_G(U)                                   # step 11
     info.update(it_inner=it, inner_hist=hist, X=X, Y=Y, U=U, G=G, it_power=it_power)
     if variant == "M2_ADEF":
-        return M2ADEF(dbbd, Z, Sigma), info
+        return M2ADEF(dbbd, Z, Sigma, drop_tol), info
     if variant != "M2":
         raise ValueError(variant)
     return M2(dbbd, Z, Sigma), info
+
+
+def build_m3(dbbd, G_I, k, eps_inner=0.1, eps_rel=1e-10, maxit=500, drop_tol=1e-12,
+             variant="M3"):
+    """The variant M3 of §4.3 (eq. (internal_term_lr_approximation_2), eq. (left_prec_mat2)).
+
+    Nyström (Algorithm 1) applied to B = S_I^{-1} with the sketch G_I (n_I x (k+p)):
+    F = S_I^{-1} G_I by block PCG on S_I X = G_I preconditioned by A_I (the inner solver of
+    §5), then steps 3-8 of Algorithm 1 give S_I^{-1} ~ V Sigma V^T; Zh = A_G^{-1} A_GI V and
+    M3 = A_G^{-1} + Zh Sigma Zh^T. variant="M3_ADEF" deflates span(Zh) instead, like
+    M_{2A-DEF} (class M2ADEF). Returns (preconditioner, info).
+    """
+    G_I = np.asarray(G_I, dtype=np.float64)
+    X, it, hist = block_pcg(dbbd.apply_S_I, dbbd.solve_I, G_I, eps_inner, maxit, drop_tol)
+    V, Sigma, info = nystrom_core(G_I, X, k, eps_rel)
+    Zh = dbbd.solve_G(dbbd.A_GI @ V)
+    info.update(it_inner=it, inner_hist=hist, X=X, V=V)
+    if variant == "M3_ADEF":
+        return M2ADEF(dbbd, Zh, Sigma, drop_tol), info
+    if variant != "M3":
+        raise ValueError(variant)
+    return M2(dbbd, Zh, Sigma), info
 
 
 # ----------------------------------------------------------------------------------------

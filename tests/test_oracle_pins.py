@@ -396,3 +396,53 @@ def test_power_iteration_sharpens_the_approximation():
     # the rank-6 truncation can do no better than the best rank-6 approximation
     lam = np.sort(np.linalg.eigvalsh(B))[::-1]
     assert min(err) >= lam[6] * (1 - 1e-8)
+
+
+# ---------------------------------------------------------------- M3 (§4.3)
+def _dense_SIinv(A, D):
+    Ainv = np.linalg.inv(A.toarray())
+    return Ainv[np.ix_(D.interior, D.interior)]
+
+
+def test_m3_nystrom_of_SIinv_matches_definition():
+    # k = s, exact solves: V Sigma V^T = F (G^T F)^{-1} F^T with F = S_I^{-1} G (eq. (NystromApprox))
+    A, part = tiny((12, 12), 2, lognormal=(4.0, 1.0), seed=10)
+    D = O.DBBD(A, part)
+    B = _dense_SIinv(A, D)
+    G = np.random.default_rng(41).standard_normal((D.n_I, 7))
+    F = B @ G
+    ref = F @ np.linalg.solve(G.T @ F, F.T)
+    M, info = O.build_m3(D, G, k=7, eps_inner=1e-14, eps_rel=1e-13)
+    got = (info["V"] * M.Sigma) @ info["V"].T
+    assert np.linalg.norm(got - ref) <= 1e-7 * np.linalg.norm(ref)
+    # Zh = A_G^{-1} A_GI V, independent dense products
+    Zh = np.linalg.solve(D.A_G.toarray(), D.A_GI.toarray() @ info["V"])
+    assert np.allclose(M.Z, Zh, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("variant", ["M3", "M3_ADEF"])
+def test_m3_exact_when_sketch_spans_interior(variant):
+    # s = n_I: V Sigma V^T = S_I^{-1}, so by SMW (§4.1 eq. (S-1)) M3 = S_Gamma^{-1}
+    A, part = tiny((6, 6), 2, lognormal=(3.0, 1.0), seed=11)
+    D = O.DBBD(A, part)
+    G = np.random.default_rng(42).standard_normal((D.n_I, D.n_I))
+    M, _ = O.build_m3(D, G, k=D.n_I, eps_inner=1e-14, eps_rel=1e-14, variant=variant)
+    Sinv = np.linalg.inv(D.dense_S_gamma())
+    assert np.allclose(M.dense(), Sinv, rtol=1e-6, atol=1e-8 * np.abs(Sinv).max())
+    b = np.random.default_rng(43).standard_normal(D.n)
+    x, it, _ = O.solve(D, M.apply, b, rtol=1e-10)
+    assert it <= 2
+    assert O.relative_residual(A, x, b) < 1e-9
+
+
+def test_m3_spectral_inclusion():
+    # 0 <= V Sigma V^T <= S_I^{-1} for exact solves => A_G^{-1} <= M3 <= S_G^{-1}
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=12)
+    D = O.DBBD(A, part)
+    S = D.dense_S_gamma()
+    lam1 = sla.eigh(S, D.A_G.toarray(), eigvals_only=True).min()
+    G = np.random.default_rng(44).standard_normal((D.n_I, 20))
+    M, _ = O.build_m3(D, G, k=12, eps_inner=1e-14)
+    mu = np.linalg.eigvals(M.dense() @ S).real
+    assert mu.min() >= lam1 * (1 - 1e-7) and mu.max() <= 1 + 1e-7
+    assert mu.min() > lam1 * (1 + 1e-6)          # and it does improve on S1
