@@ -395,8 +395,9 @@ def main():
     full_ms = (time.perf_counter() - t0) * 1e3
     h2.destroy()
 
-    # ---- the other preconditioner of §4.3, and one power iteration (§2.1 eq. (power)), on
-    # the same workload, device-timed like the step
+    # ---- the other preconditioner of §4.3, one power iteration (§2.1 eq. (power)) and the
+    # S_I inner form (Algorithm 2 step 3 as printed) on the same workload, device-timed like
+    # the step
     def time_variant(**kw):
         h3 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
                          precision=args.precision, seed=seed, **kw)
@@ -426,6 +427,7 @@ def main():
 
     variant_line = time_variant(variant="m2_adef" if args.variant == "m2" else "m2")
     power_line = time_variant(variant=args.variant, q=1)
+    si_line = time_variant(variant=args.variant, inner_form="s_i")
 
     out = None
     if rank == 0:
@@ -470,6 +472,7 @@ def main():
                                     "(s=%d, %s)" % (s, args.precision)},
             "other_variant": variant_line,
             "power_q1": power_line,
+            "inner_s_i": si_line,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),

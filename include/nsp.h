@@ -63,8 +63,16 @@ typedef enum { NSP_OUTER_AUTO = 0, NSP_OUTER_SCHUR = 1, NSP_OUTER_FULL = 2 } nsp
 /* Inner system of Algorithm 2 step 3:
  *  NSP_FORM_SGAMMA : block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G preconditioned by A_G
  *                    (first level S1, §2.3 eq. (S1)), then Y = A_G E. By the SMW identity
- *                    (§4.1 eq. (S-1)) Y = A_GI S_I^{-1} A_IG G, the Y of Algorithm 2. */
-typedef enum { NSP_FORM_SGAMMA = 0 } nsp_inner_form;
+ *                    (§4.1 eq. (S-1)) Y = A_GI S_I^{-1} A_IG G, the Y of Algorithm 2.
+ *                    Block vectors of n_Gamma rows.
+ *  NSP_FORM_SI     : the system as Algorithm 2 writes it: F = A_IG G (step 2), block PCG on
+ *                    S_I X = F with S_I = A_I - A_IG A_G^{-1} A_GI (§4.1 eq. (SI))
+ *                    preconditioned by A_I (§5 setup), Y = A_GI X (step 4). Block vectors
+ *                    of n_interior rows; each iteration applies A_I^{-1} (preconditioner)
+ *                    and A_G^{-1} (inside S_I). Same Y for exact solves; at a loose
+ *                    tolerance the two forms stop at different iterates. Single handles
+ *                    only (nsp_build_batched: NSP_ERR_UNSUPPORTED). */
+typedef enum { NSP_FORM_SGAMMA = 0, NSP_FORM_SI = 1 } nsp_inner_form;
 
 /* Preconditioner built from the Nyström factor (§4.3):
  *  NSP_VARIANT_M2      : M2 = A_G^{-1} + Z Sigma Z^T, Z = A_G^{-1} U (eq. (left_prec_mat),
@@ -249,8 +257,10 @@ nsp_status nsp_factor_solve(const nsp_handle *h, int32_t which, const void *B, v
 nsp_status nsp_get_basis(const nsp_handle *h, double *Z, double *Sigma, int32_t *rank);
 
 /* Copy an intermediate of the last build to host (needs keep_intermediates=1), all
- * n_Gamma x s row-major in Gamma order as doubles: which = 0: G (the sketch, step 1),
- * 1: E (block-PCG solution), 2: Y (= A_G E, step 4), 3: U (step 10, n_Gamma x rank). */
+ * n_Gamma x s row-major in Gamma order as doubles: which = 0: G (the sketch, step 1; after
+ * q > 0 power iterations the final orthonormalized G), 1: E (block-PCG solution, S_Gamma
+ * form only: NSP_ERR_INVALID_ARG for the S_I form), 2: Y (step 4), 3: U (step 10,
+ * n_Gamma x rank). */
 nsp_status nsp_get_intermediate(const nsp_handle *h, int32_t which, double *out);
 
 /* ---- Learned sketch proposal --------------------------------------------------------

@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libnsp.so")
 NSP_FP64, NSP_FP32 = 0, 1
 NSP_OUTER_AUTO, NSP_OUTER_SCHUR, NSP_OUTER_FULL = 0, 1, 2
 NSP_VARIANT_M2, NSP_VARIANT_M2_ADEF = 0, 1
+NSP_FORM_SGAMMA, NSP_FORM_SI = 0, 1
 STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_ERR_NOT_SPD",
           4: "NSP_ERR_BREAKDOWN", 5: "NSP_ERR_NOT_CONVERGED", 6: "NSP_ERR_TIMEOUT",
           7: "NSP_ERR_CUDA", 8: "NSP_ERR_OOM", 9: "NSP_ERR_UNSUPPORTED"}
@@ -187,7 +188,7 @@ def nsp_default_params():
 def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                 max_inner_it=500, seed=210112164, sketch=None, precision="fp32",
                 outer_form="auto", keep_intermediates=False, stream=None, keep=None,
-                variant="m2", q=0):
+                variant="m2", q=0, inner_form="s_gamma"):
     prm = nsp_default_params()
     prm.k, prm.p = int(k), int(p)
     prm.eps_inner, prm.eps_trunc_rel = float(eps_inner), float(eps_trunc_rel)
@@ -201,6 +202,7 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
     prm.keep_intermediates = 1 if keep_intermediates else 0
     prm.variant = {"m2": NSP_VARIANT_M2, "m2_adef": NSP_VARIANT_M2_ADEF}[variant]
     prm.q = int(q)
+    prm.inner_form = {"s_gamma": NSP_FORM_SGAMMA, "s_i": NSP_FORM_SI}[inner_form]
     if sketch is not None:
         if hasattr(sketch, "data_ptr"):   # device tensor: passed through (float64, contiguous)
             if str(sketch.dtype) != "torch.float64" or not sketch.is_contiguous():

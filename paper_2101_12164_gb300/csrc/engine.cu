@@ -733,6 +733,16 @@ struct Engine : EngineBase {
     }
   }
 
+  // ---- S_I V = A_I V - A_IG A_G^{-1} A_GI V (§4.1 eq. (SI)), interior order, sc columns
+  int inner_form = NSP_FORM_SGAMMA;
+  DBuf<T> siA, siB;
+  void apply_SI(const T *V, T *O, int sc) {
+    launch_spmm<T>(A_GI.dT(), V, siA.p, sc, T(1), nullptr, T(0), st);
+    solve_G(siA.p, siB.p, sc);
+    launch_spmm<T>(A_I.dT(), V, O, sc, T(1), nullptr, T(0), st);
+    launch_spmm<T>(A_IG.dT(), siB.p, O, sc, T(-1), O, T(1), st);
+  }
+
   // ---- S_Gamma X with caller-order X, Y and every temporary carved from `scratch`
   // (no allocation). The sweep plan of the needed kind must already exist.
   static size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
@@ -773,7 +783,8 @@ struct Engine : EngineBase {
     k = prm.k;
     require(s <= 256, NSP_ERR_UNSUPPORTED, "k + p > 256");
     require(s <= an.nG, NSP_ERR_INVALID_ARG, "k + p exceeds the interface size");
-    require(prm.inner_form == NSP_FORM_SGAMMA, NSP_ERR_UNSUPPORTED, "inner form");
+    require(prm.inner_form == NSP_FORM_SGAMMA || prm.inner_form == NSP_FORM_SI,
+            NSP_ERR_INVALID_ARG, "unknown inner form");
     require(prm.variant == NSP_VARIANT_M2 || prm.variant == NSP_VARIANT_M2_ADEF,
             NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
     variant = prm.variant;
@@ -781,8 +792,19 @@ struct Engine : EngineBase {
     keep = prm.keep_intermediates != 0;
     ensure_ws(s);
     const size_t ns = (size_t)an.nG * s;
-    for (DBuf<T> *b : {&G, &Fh, &E, &R, &P, &Q, &Z, &W, &Y}) b->ensure(ns);
-    gram_work.ensure(std::max(gram_work_size(an.nG, s, s), gram_work_size(an.nG, s, 1)));
+    // block-PCG vector length: n_Gamma (S_Gamma form) or n_interior (S_I form)
+    const bool si = prm.inner_form == NSP_FORM_SI;
+    inner_form = prm.inner_form;
+    const int64_t nv = si ? an.nI : an.nG;
+    const size_t nvs = (size_t)std::max<int64_t>(nv, 1) * s;
+    for (DBuf<T> *b : {&G, &Y}) b->ensure(ns);
+    for (DBuf<T> *b : {&Fh, &E, &R, &P, &Q, &Z, &W}) b->ensure(std::max(ns, nvs));
+    if (si) {
+      siA.ensure(ns);
+      siB.ensure(ns);
+    }
+    const int64_t nmax = std::max(an.nG, nv);
+    gram_work.ensure(std::max(gram_work_size(nmax, s, s), gram_work_size(nmax, s, 1)));
     for (DBuf<double> *b : {&PtQ, &PtR, &QtZ, &Cg, &alpha, &beta, &K, &Cn})
       b->ensure((size_t)s * s);
     Rinv.ensure((size_t)s * s);
@@ -822,31 +844,38 @@ struct Engine : EngineBase {
         launch_block_update<T>(Y.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), G.p, st);
       }
       // steps 2-3: block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G, preconditioner A_G^{-1}
-      schur_apply(G.p, Fh.p, s, false);
-      launch_col_sumsq<T>(Fh.p, an.nG, s, colsq.p, gram_work.p, st);
+      // (S_Gamma form), or on S_I X = F = A_IG G, preconditioner A_I^{-1} (S_I form, the
+      // system of Algorithm 2 step 3 as the paper writes it, §5 setup)
+      if (si)
+        launch_spmm<T>(A_IG.dT(), G.p, Fh.p, s, T(1), nullptr, T(0), st);   // step 2
+      else
+        schur_apply(G.p, Fh.p, s, false);
+      launch_col_sumsq<T>(Fh.p, nv, s, colsq.p, gram_work.p, st);
       launch_sqrt_vec(colsq.p, s, bnorm.p, st);
       // Breakdown-free block PCG (the paper's inner solver, §5.1) with search directions kept
-      // S_Gamma-orthonormal: W spans the new directions, Qw = S W, C = W^T Qw = L L^T (columns
-      // whose pivot falls below drop_tol are dropped), P = W L^{-T}, Q = Qw L^{-T}, so that
-      // P^T Q = I and alpha = P^T R, beta = -Q^T Z need no s x s solve. The block Krylov
+      // operator-orthonormal: W spans the new directions, Qw = S W, C = W^T Qw = L L^T
+      // (columns whose pivot falls below drop_tol are dropped), P = W L^{-T}, Q = Qw L^{-T}, so
+      // that P^T Q = I and alpha = P^T R, beta = -Q^T Z need no s x s solve. The block Krylov
       // space, hence every iterate E, is the one of the 2-norm-orthonormal form.
-      NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
-      NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
-      solve_G(R.p, W.p, s);                 // W = Z0 = A_G^{-1} R0
+      NSP_CUDA(cudaMemsetAsync(E.p, 0, nvs * sizeof(T), st));
+      NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, nvs * sizeof(T), cudaMemcpyDeviceToDevice, st));
+      if (si) solve_I(R.p, W.p, s);         // W = Z0 = A_I^{-1} R0
+      else solve_G(R.p, W.p, s);            // W = Z0 = A_G^{-1} R0
       it = 0;
       rat = 1.0;
       active = s;
       while (it < prm.max_inner_it) {
-        schur_apply(W.p, Z.p, s, true);     // Z holds Qw = S W
-        gram(W.p, Z.p, s, s, Cg.p);
+        if (si) apply_SI(W.p, Z.p, s);      // Z holds Qw = S_I W
+        else schur_apply(W.p, Z.p, s, true);  // Z holds Qw = S_Gamma W
+        launch_gram<T, T>(W.p, Z.p, nv, s, s, Cg.p, gram_work.p, st);
         launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
-        launch_block_update<T>(W.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), P.p, st);
-        launch_block_update<T>(Z.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), Q.p, st);
-        gram(P.p, R.p, s, s, alpha.p);      // alpha = P^T R
-        launch_block_update<T>(P.p, alpha.p, an.nG, s, s, T(1), E.p, T(1), E.p, st);
-        launch_block_update<T>(Q.p, alpha.p, an.nG, s, s, T(-1), R.p, T(1), R.p, st);
+        launch_block_update<T>(W.p, Rinv.p, nv, s, s, T(1), nullptr, T(0), P.p, st);
+        launch_block_update<T>(Z.p, Rinv.p, nv, s, s, T(1), nullptr, T(0), Q.p, st);
+        launch_gram<T, T>(P.p, R.p, nv, s, s, alpha.p, gram_work.p, st);   // alpha = P^T R
+        launch_block_update<T>(P.p, alpha.p, nv, s, s, T(1), E.p, T(1), E.p, st);
+        launch_block_update<T>(Q.p, alpha.p, nv, s, s, T(-1), R.p, T(1), R.p, st);
         ++it;
-        launch_col_sumsq<T>(R.p, an.nG, s, colsq.p, gram_work.p, st);
+        launch_col_sumsq<T>(R.p, nv, s, colsq.p, gram_work.p, st);
         launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st);
         NSP_CUDA(cudaMemcpyAsync(hscal, ratio.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         NSP_CUDA(cudaMemcpyAsync(hint, nkept.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -858,13 +887,17 @@ struct Engine : EngineBase {
           break;
         }
         if (!(rat > prm.eps_inner)) break;
-        solve_G(R.p, Z.p, s);               // Z = A_G^{-1} R
-        gram(Q.p, Z.p, s, s, beta.p);       // Q^T Z
-        launch_block_update<T>(P.p, beta.p, an.nG, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
+        if (si) solve_I(R.p, Z.p, s);       // Z = A_I^{-1} R
+        else solve_G(R.p, Z.p, s);          // Z = A_G^{-1} R
+        launch_gram<T, T>(Q.p, Z.p, nv, s, s, beta.p, gram_work.p, st);    // Q^T Z
+        launch_block_update<T>(P.p, beta.p, nv, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
       }
       check_status();
-      // step 4: Y = A_G E (= A_GI S_I^{-1} A_IG G)
-      launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
+      // step 4: Y = A_GI X (S_I form) or Y = A_G E (S_Gamma form; = A_GI S_I^{-1} A_IG G)
+      if (si)
+        launch_spmm<T>(A_GI.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
+      else
+        launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
     }
     info.it_inner = it;
     info.it_power = it_power;
@@ -1545,6 +1578,8 @@ struct Engine : EngineBase {
   void get_intermediate(int which, double *out) override {
     require(keep, NSP_ERR_INVALID_ARG, "build without keep_intermediates");
     require(which >= 0 && which <= 3, NSP_ERR_INVALID_ARG, "intermediate id");
+    require(which != 1 || inner_form == NSP_FORM_SGAMMA, NSP_ERR_INVALID_ARG,
+            "the S_I form keeps no n_Gamma x s block E");
     const T *src = which == 0 ? G.p : which == 1 ? E.p : which == 2 ? Y.p : U.p;
     const int cols = which == 3 ? k : s;
     DBuf<double> o((size_t)an.nG * std::max(cols, 1));
