@@ -395,12 +395,13 @@ def main():
     full_ms = (time.perf_counter() - t0) * 1e3
     h2.destroy()
 
-    # ---- the other preconditioner of §4.3, one power iteration (§2.1 eq. (power)) and the
-    # S_I inner form (Algorithm 2 step 3 as printed) on the same workload, device-timed like
-    # the step
+    # ---- the other preconditioners of §4.3 (M2 / M_2A-DEF, M3, M_3A-DEF), one power
+    # iteration (§2.1 eq. (power)) and the S_I inner form (Algorithm 2 step 3 as printed) on
+    # the same workload, device-timed like the step
     def time_variant(**kw):
+        kw.setdefault("precision", args.precision)
         h3 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
-                         precision=args.precision, seed=seed, **kw)
+                         seed=seed, **kw)
 
         def step3():
             h3.rebuild(val_d, on_device=True)
@@ -428,6 +429,9 @@ def main():
     variant_line = time_variant(variant="m2_adef" if args.variant == "m2" else "m2")
     power_line = time_variant(variant=args.variant, q=1)
     si_line = time_variant(variant=args.variant, inner_form="s_i")
+    m3_lines = [time_variant(variant=v) for v in ("m3", "m3_adef")]
+    # the plain FP64 GPU form (FP64 factors, inner block PCG and sweeps) of the timed step
+    fp64_line = time_variant(variant=args.variant, precision="fp64")
 
     out = None
     if rank == 0:
@@ -473,6 +477,8 @@ def main():
             "other_variant": variant_line,
             "power_q1": power_line,
             "inner_s_i": si_line,
+            "variants_m3": m3_lines,
+            "plain_fp64": fp64_line,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),

@@ -85,9 +85,19 @@ typedef enum { NSP_FORM_SGAMMA = 0, NSP_FORM_SI = 1 } nsp_inner_form;
  *                        (columns of E whose pivot falls below drop_tol of their diagonal are
  *                        left out of the deflation space); each application costs the A_G
  *                        solve of M2 plus three length-n_G products with k columns. M is not
- *                        symmetric; the outer PCG uses it as is, as §5 does. Single handles
- *                        only: nsp_build_batched returns NSP_ERR_UNSUPPORTED for it. */
-typedef enum { NSP_VARIANT_M2 = 0, NSP_VARIANT_M2_ADEF = 1 } nsp_variant;
+ *                        symmetric; the outer PCG uses it as is, as §5 does.
+ *  NSP_VARIANT_M3      : M3 = A_G^{-1} + Zh Sigma Zh^T (§4.3 eq. (left_prec_mat2)): Nyström
+ *                        (Algorithm 1) of S_I^{-1} ~ V Sigma V^T (eq.
+ *                        (internal_term_lr_approximation_2)) from a sketch G_I of n_interior
+ *                        x (k+p), X = S_I^{-1} G_I by the S_I block PCG (preconditioner A_I,
+ *                        tolerance eps_inner, whatever inner_form says), Zh = A_G^{-1} A_GI V.
+ *                        params.sketch, when given, is then n_interior x s row-major in
+ *                        interior order (see nsp_factor_solve). q must be 0
+ *                        (NSP_ERR_UNSUPPORTED otherwise); nsp_get_intermediate is refused.
+ *  NSP_VARIANT_M3_ADEF : M_{3A-DEF}: the deflation of NSP_VARIANT_M2_ADEF on span(Zh).
+ * Single handles only: nsp_build_batched returns NSP_ERR_UNSUPPORTED for any but M2. */
+typedef enum { NSP_VARIANT_M2 = 0, NSP_VARIANT_M2_ADEF = 1, NSP_VARIANT_M3 = 2,
+               NSP_VARIANT_M3_ADEF = 3 } nsp_variant;
 
 /* Sparse matrix in CSR. Full symmetric pattern (both triangles) with sorted column
  * indices and no duplicates. rowptr has n+1 entries. Host pointers unless on_device. */
@@ -120,7 +130,8 @@ typedef struct {
   int32_t max_inner_it;      /* inner block-PCG iteration cap (e.g. 500)                  */
   uint64_t seed;             /* Gaussian sketch seed (Philox4x32-10 + Box-Muller)          */
   const double *sketch;      /* optional caller sketch G: n_Gamma x s row-major, Gamma
-                                order, host or device memory; NULL = draw from seed       */
+                                order (n_interior x s, interior order, for the M3
+                                variants), host or device memory; NULL = draw from seed   */
   int32_t precision;         /* nsp_precision of the factors and the inner block PCG      */
   int32_t outer_form;        /* nsp_outer_form                                            */
   int32_t inner_form;        /* nsp_inner_form                                            */

@@ -785,16 +785,20 @@ struct Engine : EngineBase {
     require(s <= an.nG, NSP_ERR_INVALID_ARG, "k + p exceeds the interface size");
     require(prm.inner_form == NSP_FORM_SGAMMA || prm.inner_form == NSP_FORM_SI,
             NSP_ERR_INVALID_ARG, "unknown inner form");
-    require(prm.variant == NSP_VARIANT_M2 || prm.variant == NSP_VARIANT_M2_ADEF,
+    require(prm.variant >= NSP_VARIANT_M2 && prm.variant <= NSP_VARIANT_M3_ADEF,
             NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
     variant = prm.variant;
     require(prm.q >= 0 && prm.q <= 16, NSP_ERR_INVALID_ARG, "power iterations q in [0, 16]");
+    // M3 (§4.3): Nyström of S_I^{-1} from an n_interior x s sketch, always by the S_I
+    // block PCG (S_I X = G_I, preconditioner A_I), without power iterations
+    m3 = variant == NSP_VARIANT_M3 || variant == NSP_VARIANT_M3_ADEF;
+    require(!m3 || prm.q == 0, NSP_ERR_UNSUPPORTED, "M3 takes no power iterations");
     keep = prm.keep_intermediates != 0;
     ensure_ws(s);
     const size_t ns = (size_t)an.nG * s;
     // block-PCG vector length: n_Gamma (S_Gamma form) or n_interior (S_I form)
-    const bool si = prm.inner_form == NSP_FORM_SI;
-    inner_form = prm.inner_form;
+    const bool si = m3 || prm.inner_form == NSP_FORM_SI;
+    inner_form = si ? NSP_FORM_SI : NSP_FORM_SGAMMA;
     const int64_t nv = si ? an.nI : an.nG;
     const size_t nvs = (size_t)std::max<int64_t>(nv, 1) * s;
     for (DBuf<T> *b : {&G, &Y}) b->ensure(ns);
@@ -820,8 +824,19 @@ struct Engine : EngineBase {
     drank.ensure(1);
     NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
 
-    // step 1: sketch G (caller order), moved to the internal order
-    {
+    // step 1: sketch G (caller order), moved to the internal order; for M3 the sketch G_I
+    // (n_interior x s, interior order) goes straight into the block-PCG right-hand side Fh
+    if (m3) {
+      const size_t nis = (size_t)an.nI * s;
+      g64.ensure(nis);
+      if (prm.sketch) {
+        NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, nis * sizeof(double), cudaMemcpyDefault, st));
+      } else {
+        launch_gaussian<double>(prm.seed, (int64_t)nis, g64.p, st);
+      }
+      launch_gather_rows<double, T>(i2u_I.p, an.nI, g64.p, Fh.p, s, st);
+      sync();
+    } else {
       g64.ensure(ns);
       if (prm.sketch) {
         NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyDefault, st));
@@ -846,9 +861,10 @@ struct Engine : EngineBase {
       // steps 2-3: block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G, preconditioner A_G^{-1}
       // (S_Gamma form), or on S_I X = F = A_IG G, preconditioner A_I^{-1} (S_I form, the
       // system of Algorithm 2 step 3 as the paper writes it, §5 setup)
-      if (si)
+      // (M3: Fh already holds G_I; X = S_I^{-1} G_I is Algorithm 1 step 2 for B = S_I^{-1})
+      if (!m3 && si)
         launch_spmm<T>(A_IG.dT(), G.p, Fh.p, s, T(1), nullptr, T(0), st);   // step 2
-      else
+      else if (!m3)
         schur_apply(G.p, Fh.p, s, false);
       launch_col_sumsq<T>(Fh.p, nv, s, colsq.p, gram_work.p, st);
       launch_sqrt_vec(colsq.p, s, bnorm.p, st);
@@ -893,8 +909,9 @@ struct Engine : EngineBase {
         launch_block_update<T>(P.p, beta.p, nv, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
       }
       check_status();
-      // step 4: Y = A_GI X (S_I form) or Y = A_G E (S_Gamma form; = A_GI S_I^{-1} A_IG G)
-      if (si)
+      // step 4: Y = A_GI X (S_I form) or Y = A_G E (S_Gamma form; = A_GI S_I^{-1} A_IG G);
+      // M3 uses X itself (E, n_interior x s) as the Y of its Nyström step
+      if (m3 || si)
         launch_spmm<T>(A_GI.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
       else
         launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
@@ -905,9 +922,13 @@ struct Engine : EngineBase {
     info.inner_active_cols = active;
     info.ms_inner = ms_since(t0);
     auto t1 = Clock::now();
-    // steps 5-10
-    gram_acc64(Y.p, Y.p, s, s, K.p);
-    gram_acc64(G.p, Y.p, s, s, Cn.p);
+    // steps 5-10 (M3: on G_I and X = S_I^{-1} G_I, n_interior rows)
+    {
+      const T *Ys = m3 ? E.p : Y.p, *Gs = m3 ? Fh.p : G.p;
+      const int64_t ny = m3 ? an.nI : an.nG;
+      launch_gram<T, double>(Ys, Ys, ny, s, s, K.p, gram_work.p, st);
+      launch_gram<T, double>(Gs, Ys, ny, s, s, Cn.p, gram_work.p, st);
+    }
     launch_nystrom_core(K.p, Cn.p, s, k, prm.eps_trunc_rel, 1e-14, Mix.p, Sigma.p, drank.p,
                         nys_work.p, st, 1, std::is_same<T, double>::value ? 1 : 0);
     NSP_CUDA(cudaMemcpyAsync(hint, drank.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -918,13 +939,20 @@ struct Engine : EngineBase {
     Zt.ensure((size_t)an.nG * k);
     Zs.ensure((size_t)an.nG * k);
     if (rank > 0) {
-      // U = Y Mix (columns beyond the rank are zero, Sigma there is zero)
-      launch_block_update<T>(Y.p, Mix.p, an.nG, s, k, T(1), nullptr, T(0), U.p, st);
+      if (m3) {
+        // V = X Mix (n_interior x k), then U = A_GI V so that Zt = A_G^{-1} A_GI V = Zh
+        launch_block_update<T>(E.p, Mix.p, an.nI, s, k, T(1), nullptr, T(0), W.p, st);
+        launch_spmm<T>(A_GI.dT(), W.p, U.p, k, T(1), nullptr, T(0), st);
+      } else {
+        // U = Y Mix (columns beyond the rank are zero, Sigma there is zero)
+        launch_block_update<T>(Y.p, Mix.p, an.nG, s, k, T(1), nullptr, T(0), U.p, st);
+      }
       // step 11: Z = A_G^{-1} U; M2's low-rank term kept as Zs = Z Sigma^{1/2} in FP64
       solve_G(U.p, Zt.p, k);
       launch_gather_rows<T, double>(nullptr, an.nG, Zt.p, Zs.p, k, st);
       launch_scale_cols(Zs.p, an.nG, k, Sigma.p, true, st);
-      if (variant == NSP_VARIANT_M2_ADEF) build_adef(prm.drop_tol);
+      if (variant == NSP_VARIANT_M2_ADEF || variant == NSP_VARIANT_M3_ADEF)
+        build_adef(prm.drop_tol);
       sync();
     }
     info.ms_core = ms_since(t1);
@@ -936,6 +964,7 @@ struct Engine : EngineBase {
   // Wd = S_G Zd turns the S_G A_G^{-1} r of every application into Wd^T (A_G^{-1} r):
   // one S_G apply on k columns here, none per application.
   int variant = NSP_VARIANT_M2;
+  bool m3 = false;
   DBuf<T> adefS;
   DBuf<double> Zd, Wd, adefT, Ead, Rad;
   DBuf<int32_t> adef_mask, adef_nk;
@@ -972,7 +1001,7 @@ struct Engine : EngineBase {
       solve_G(sT.p, sT2.p, 1);
       launch_gather_rows<T, double>(nullptr, an.nG, sT2.p, z, 1, st);
     }
-    if (rank > 0 && variant == NSP_VARIANT_M2_ADEF) {
+    if (rank > 0 && (variant == NSP_VARIANT_M2_ADEF || variant == NSP_VARIANT_M3_ADEF)) {
       // z = y + Zd (Zd^T r - Wd^T y) with y = A_G^{-1} r already in z
       zt_vec.ensure(2 * (size_t)k);
       launch_gemv_t(Zd.p, an.nG, k, r, zt_vec.p, dwork.p, st);
@@ -1580,6 +1609,7 @@ struct Engine : EngineBase {
     require(which >= 0 && which <= 3, NSP_ERR_INVALID_ARG, "intermediate id");
     require(which != 1 || inner_form == NSP_FORM_SGAMMA, NSP_ERR_INVALID_ARG,
             "the S_I form keeps no n_Gamma x s block E");
+    require(!m3, NSP_ERR_INVALID_ARG, "M3 keeps no n_Gamma x s intermediates");
     const T *src = which == 0 ? G.p : which == 1 ? E.p : which == 2 ? Y.p : U.p;
     const int cols = which == 3 ? k : s;
     DBuf<double> o((size_t)an.nG * std::max(cols, 1));
