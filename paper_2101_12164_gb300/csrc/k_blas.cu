@@ -123,22 +123,41 @@ __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
     }
 }
 
-__global__ void k_gram_reduce(const double *work, int nchunks, int64_t entries, double *C) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= entries) return;
-  // sixteen partials in flight per round, summed in chunk order (same result as one by one)
+// C[e] = sum over chunks of work[chunk * entries + e]. A CTA of BT threads serves RE = 32
+// consecutive entries with RL = BT / 32 lanes each: lane l sums the chunks l, l + RL, ... in
+// increasing order (eight loads in flight), then lane 0 adds the RL lane sums in lane order,
+// so the result is deterministic. Splitting the chunks over lanes puts RL times more CTAs
+// and RL times fewer dependent load rounds per thread on the reduction than one thread per
+// entry (the s x s Gram reduction sums 304 partials per entry over 6,400 entries).
+constexpr int RE = 32, RL = BT / RE;
+__global__ void __launch_bounds__(BT) k_gram_reduce(const double *work, int nchunks,
+                                                    int64_t entries, double *C) {
+  __shared__ double red[RL][RE + 1];
+  const int tx = threadIdx.x % RE, ty = threadIdx.x / RE;
+  const int64_t e = (int64_t)blockIdx.x * RE + tx;
   double acc = 0.0;
-  int c = 0;
-  for (; c + 16 <= nchunks; c += 16) {
-    double v[16];
+  if (e < entries) {
+    int c = ty;
+    for (; c + 7 * RL < nchunks; c += 8 * RL) {
+      double v[8];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = work[(size_t)(c + u) * entries + e];
+      for (int u = 0; u < 8; ++u) v[u] = work[(size_t)(c + u * RL) * entries + e];
 #pragma unroll
-    for (int u = 0; u < 16; ++u) acc += v[u];
+      for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; c < nchunks; c += RL) acc += work[(size_t)c * entries + e];
   }
-  for (; c < nchunks; ++c) acc += work[(size_t)c * entries + e];
-  C[e] = acc;
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && e < entries) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < RL; ++q) t += red[q][tx];
+    C[e] = t;
+  }
 }
+
+inline int reduce_grid(int64_t entries) { return (int)((entries + RE - 1) / RE); }
 
 int gram_rt(int s1, int s2) {
   const int smax = std::max(s1, s2);
@@ -444,7 +463,7 @@ void gram_rt_launch(const T *X, const T *Y, int64_t n, int s1, int s2, double *C
   k_gram_partial<T, AccT, RT><<<grid, BT, 0, stream>>>(X, Y, n, s1, s2, rpc, work);
   NSP_LAUNCH_CHECK();
   const int64_t ent = (int64_t)s1 * s2;
-  k_gram_reduce<<<ceil_div(ent, BT), BT, 0, stream>>>(work, ch, ent, C);
+  k_gram_reduce<<<reduce_grid(ent), BT, 0, stream>>>(work, ch, ent, C);
   NSP_LAUNCH_CHECK();
 }
 
@@ -467,7 +486,7 @@ void launch_gemv_t(const double *Z, int64_t n, int k, const double *r, double *t
   const int64_t rpc = (n + cs - 1) / cs;
   k_gemv_t_partial<<<(int)cs, BT, 0, stream>>>(Z, n, k, r, std::max<int64_t>(rpc, 1), work);
   NSP_LAUNCH_CHECK();
-  k_gram_reduce<<<ceil_div(k, BT), BT, 0, stream>>>(work, (int)cs, k, t);
+  k_gram_reduce<<<reduce_grid(k), BT, 0, stream>>>(work, (int)cs, k, t);
   NSP_LAUNCH_CHECK();
 }
 
@@ -501,7 +520,7 @@ void launch_col_sumsq(const T *X, int64_t n, int s, double *colsq, double *work,
   const int64_t rpc = (n + cs - 1) / cs;
   k_colsq_partial<T><<<(int)cs, BT, 0, stream>>>(X, n, s, std::max<int64_t>(rpc, 1), work);
   NSP_LAUNCH_CHECK();
-  k_gram_reduce<<<ceil_div(s, BT), BT, 0, stream>>>(work, (int)cs, s, colsq);
+  k_gram_reduce<<<reduce_grid(s), BT, 0, stream>>>(work, (int)cs, s, colsq);
   NSP_LAUNCH_CHECK();
 }
 
