@@ -174,6 +174,9 @@ int gram_chunks(int64_t n, int s1, int s2) {
 
 // ---------------------------------------------------------------- FP64 GEMV with a tall Z
 // t = Z^T r (Z n x k row-major): partials per row chunk, then an ordered sum.
+// A CTA owns a chunk of rows; per 32-column group, lane ty of 8 takes rows i0+ty, i0+ty+8, ...
+// with four rows (four loads of Z and r) in flight per round into four running sums, added
+// in a fixed order, so every partial is deterministic for a given n and chunk count.
 __global__ void __launch_bounds__(BT) k_gemv_t_partial(const double *Z, int64_t n, int k,
                                                        const double *r, int64_t rpc,
                                                        double *work) {
@@ -182,10 +185,21 @@ __global__ void __launch_bounds__(BT) k_gemv_t_partial(const double *Z, int64_t 
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
   for (int c0 = 0; c0 < k; c0 += 32) {
     const int c = c0 + tx;
-    double acc = 0.0;
-    if (c < k)
-      for (int64_t i = i0 + ty; i < i1; i += 8) acc += Z[(size_t)i * k + c] * r[i];
-    red[ty][tx] = acc;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    if (c < k) {
+      int64_t i = i0 + ty;
+      for (; i + 24 < i1; i += 32) {
+        const double z0 = Z[(size_t)i * k + c], z1 = Z[(size_t)(i + 8) * k + c];
+        const double z2 = Z[(size_t)(i + 16) * k + c], z3 = Z[(size_t)(i + 24) * k + c];
+        const double r0 = r[i], r1 = r[i + 8], r2 = r[i + 16], r3 = r[i + 24];
+        a0 += z0 * r0;
+        a1 += z1 * r1;
+        a2 += z2 * r2;
+        a3 += z3 * r3;
+      }
+      for (; i < i1; i += 8) a0 += Z[(size_t)i * k + c] * r[i];
+    }
+    red[ty][tx] = (a0 + a1) + (a2 + a3);
     __syncthreads();
     if (ty == 0 && c < k) {
       double t = 0.0;
@@ -194,6 +208,11 @@ __global__ void __launch_bounds__(BT) k_gemv_t_partial(const double *Z, int64_t 
     }
     __syncthreads();
   }
+}
+
+// row chunks of the FP64 GEMV: about 64 rows each, at most four CTAs per SM of a 152-SM part
+int64_t gemv_chunks(int64_t n) {
+  return std::max<int64_t>(1, std::min<int64_t>(4 * 152, (n + 63) / 64));
 }
 
 // z[i] = beta z[i] + sum_j Z[i, j] t[j]: one warp per row.
@@ -449,7 +468,8 @@ void launch_gather_values(const int64_t *src, int64_t count, const double *Aval,
 size_t gram_work_size(int64_t n, int s1, int s2) {
   const int ch = gram_chunks(n, s1, s2);
   const size_t g = (size_t)ch * s1 * s2;
-  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256));
+  const int64_t cs = std::max(gemv_chunks(n),
+                              std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256)));
   const size_t c = (size_t)cs * std::max(s1, s2);
   return std::max<size_t>(std::max(g, c), 4 * 152 + 8);
 }
@@ -482,7 +502,7 @@ void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C, d
 void launch_gemv_t(const double *Z, int64_t n, int k, const double *r, double *t, double *work,
                    cudaStream_t stream) {
   if (k <= 0) return;
-  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256));
+  const int64_t cs = gemv_chunks(n);
   const int64_t rpc = (n + cs - 1) / cs;
   k_gemv_t_partial<<<(int)cs, BT, 0, stream>>>(Z, n, k, r, std::max<int64_t>(rpc, 1), work);
   NSP_LAUNCH_CHECK();
