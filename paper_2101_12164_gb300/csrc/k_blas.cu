@@ -215,17 +215,21 @@ int64_t gemv_chunks(int64_t n) {
   return std::max<int64_t>(1, std::min<int64_t>(4 * 152, (n + 63) / 64));
 }
 
-// z[i] = beta z[i] + sum_j Z[i, j] t[j]: one warp per row.
+// z[i] = beta z[i] + sum_j Z[i, j] t[j]: eight lanes per row (four rows per warp), each lane
+// taking columns l, l + 8, ... so that the eight lanes of a row read it contiguously.
+constexpr int GN = 8;
 __global__ void __launch_bounds__(BT) k_gemv_n(const double *Z, int64_t n, int k,
                                                const double *t, double beta, double *z) {
-  const int64_t i = (int64_t)blockIdx.x * (BT / 32) + threadIdx.x / 32;
-  const int lane = threadIdx.x % 32;
-  if (i >= n) return;
+  const int64_t i = ((int64_t)blockIdx.x * BT + threadIdx.x) / GN;
+  const int l = threadIdx.x % GN;
   double acc = 0.0;
-  for (int j = lane; j < k; j += 32) acc += Z[(size_t)i * k + j] * t[j];
+  if (i < n) {
+#pragma unroll 4
+    for (int j = l; j < k; j += GN) acc += Z[(size_t)i * k + j] * t[j];
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-  if (lane == 0) z[i] = beta * z[i] + acc;
+  for (int o = GN / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (l == 0 && i < n) z[i] = beta * z[i] + acc;
 }
 
 // ---------------------------------------------------------------- block update
@@ -513,7 +517,7 @@ void launch_gemv_t(const double *Z, int64_t n, int k, const double *r, double *t
 void launch_gemv_n(const double *Z, int64_t n, int k, const double *t, double beta, double *z,
                    cudaStream_t stream) {
   if (n <= 0 || k <= 0) return;
-  k_gemv_n<<<ceil_div(n, BT / 32), BT, 0, stream>>>(Z, n, k, t, beta, z);
+  k_gemv_n<<<ceil_div(n, BT / GN), BT, 0, stream>>>(Z, n, k, t, beta, z);
   NSP_LAUNCH_CHECK();
 }
 

@@ -7,7 +7,8 @@ one, and properties that hold at any size:
 * S_Gamma applied to two sampled columns, and A_I^{-1} applied to one, against the oracle's
   sparse-direct results (FP32 tolerance);
 * the outer solve reaches ||b - A x|| / ||b|| <= 1e-8 and the oracle's outer iteration count
-  within +-2 (the oracle runs the same Algorithm 2 with the same sketch in FP64).
+  within +-2 (the oracle runs the same Algorithm 2 with the same sketch in FP64), also for
+  M_{2A-DEF}, M3 and the S_I inner form.
 """
 
 import numpy as np
@@ -80,6 +81,31 @@ def test_fullsize_solve_matches_oracle_iterations(N, torch, cfg1):
     assert O.relative_residual(P.A, x, b) < 1e-8
     M, info = O.build_m2(D, G, P.k, P.eps_inner)
     _, it_ref, _ = O.solve(D, M.apply, b, rtol=P.rtol)
+    assert abs(inf["it_inner"] - info["it_inner"]) <= 1, (inf["it_inner"], info["it_inner"])
+    assert abs(inf["it_pcg"] - it_ref) <= 2, (inf["it_pcg"], it_ref)
+    h.destroy()
+
+
+@pytest.mark.parametrize("variant,form", [("m2_adef", "s_gamma"), ("m2", "s_i"), ("m3", "s_gamma")])
+def test_fullsize_variants_match_oracle_iterations(N, torch, cfg1, variant, form):
+    # the §4.3 variants and the S_I inner form at the benchmark size, same sketch both sides
+    # (M3: an interior sketch of n_interior x s)
+    P, D = cfg1
+    _, b = F.make_rhs(P, 1, 0)
+    if variant == "m3":
+        G = np.random.default_rng(77).standard_normal((D.n_I, P.s))
+        M, info = O.build_m3(D, G, P.k, P.eps_inner)
+    else:
+        G = F.make_sketch(P.n_gamma, P.s, 1, 0)
+        M, info = O.build_m2(D, G, P.k, P.eps_inner, form="S_I" if form == "s_i" else "S_gamma",
+                             variant="M2_ADEF" if variant == "m2_adef" else "M2")
+    _, it_ref, _ = O.solve(D, M.apply, b, rtol=P.rtol)
+    h = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                    precision="fp32", sketch=G, variant=variant, inner_form=form)
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    xd = torch.zeros_like(bd)
+    inf = h.solve(bd, xd, rtol=P.rtol, maxit=500)
+    assert O.relative_residual(P.A, xd.cpu().numpy(), b) < 1e-8
     assert abs(inf["it_inner"] - info["it_inner"]) <= 1, (inf["it_inner"], info["it_inner"])
     assert abs(inf["it_pcg"] - it_ref) <= 2, (inf["it_pcg"], it_ref)
     h.destroy()
