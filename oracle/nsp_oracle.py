@@ -138,8 +138,6 @@ def kept_columns(C, drop_tol=1e-12):
     for j in range(s):
         if C[j, j] <= 0.0:
             continue
-        trial = keep + [j]
-        Ct = C[np.ix_(trial, trial)]
         # pivot of column j after eliminating the kept ones (Schur complement)
         if keep:
             Ck = C[np.ix_(keep, keep)]

@@ -446,3 +446,18 @@ def test_m3_spectral_inclusion():
     mu = np.linalg.eigvals(M.dense() @ S).real
     assert mu.min() >= lam1 * (1 - 1e-7) and mu.max() <= 1 + 1e-7
     assert mu.min() > lam1 * (1 + 1e-6)          # and it does improve on S1
+
+
+def test_kept_columns_drops_exactly_the_dependent_columns():
+    # the drop rule shared by the block-PCG orthonormalization and the A-DEF basis: a column
+    # is dropped iff it lies in the span of the columns kept before it (brute-force ranks)
+    rng = np.random.default_rng(51)
+    a, b, c = rng.standard_normal((3, 40))
+    W = np.stack([a, b, a + 2 * b, np.zeros(40), c, 3 * c - b], axis=1)
+    keep = O.kept_columns(W.T @ W, 1e-12)
+    assert keep == [0, 1, 4]
+    for j in range(W.shape[1]):
+        prev = [i for i in keep if i < j]
+        grows = np.linalg.matrix_rank(W[:, prev + [j]]) > np.linalg.matrix_rank(W[:, prev]) \
+            if prev else np.linalg.norm(W[:, j]) > 0
+        assert (j in keep) == bool(grows), j
