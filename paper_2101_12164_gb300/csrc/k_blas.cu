@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
 // consecutive entries with RL = BT / 32 lanes each: lane l sums the chunks l, l + RL, ... in
 // increasing order (eight loads in flight), then lane 0 adds the RL lane sums in lane order,
 // so the result is deterministic. Splitting the chunks over lanes puts RL times more CTAs
-// and RL times fewer dependent load rounds per thread on the reduction than one thread per
+// and RL times fewer dependent load passes per thread on the reduction than one thread per
 // entry (the s x s Gram reduction sums 304 partials per entry over 6,400 entries).
 constexpr int RE = 32, RL = BT / RE;
 __global__ void __launch_bounds__(BT) k_gram_reduce(const double *work, int nchunks,
@@ -175,7 +175,7 @@ int gram_chunks(int64_t n, int s1, int s2) {
 // ---------------------------------------------------------------- FP64 GEMV with a tall Z
 // t = Z^T r (Z n x k row-major): partials per row chunk, then an ordered sum.
 // A CTA owns a chunk of rows; per 32-column group, lane ty of 8 takes rows i0+ty, i0+ty+8, ...
-// with four rows (four loads of Z and r) in flight per round into four running sums, added
+// with four rows (four loads of Z and r) in flight per loop pass into four running sums, added
 // in a fixed order, so every partial is deterministic for a given n and chunk count.
 __global__ void __launch_bounds__(BT) k_gemv_t_partial(const double *Z, int64_t n, int k,
                                                        const double *r, int64_t rpc,
