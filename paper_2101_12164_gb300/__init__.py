@@ -218,8 +218,24 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
     return prm
 
 
+def _check_sketch(kw, n_gamma, n_interior):
+    """The library copies rows x (k + p) doubles from a caller sketch (rows = n_Gamma, or
+    n_interior for the M3 variants); refuse a smaller buffer before the copy could read past
+    its end."""
+    sk = kw.get("sketch")
+    if sk is None:
+        return
+    s = int(kw.get("k", 16)) + int(kw.get("p", 10))
+    rows = n_interior if kw.get("variant", "m2") in ("m3", "m3_adef") else n_gamma
+    size = int(sk.numel()) if hasattr(sk, "numel") else int(np.size(sk))
+    if size < rows * s:
+        raise ValueError("sketch holds %d values; the build reads %d x %d" % (size, rows, s))
+
+
 def nsp_build(A, part, nblocks, perm=None, **kw):
     """Build M2 (Algorithm 2) for A; returns a Handle. See make_params for keywords."""
+    pa = np.asarray(part)
+    _check_sketch(kw, int((pa < 0).sum()), int((pa >= 0).sum()))
     keep = []
     csr = _csr_struct(A, keep)
     ps = _part_struct(part, nblocks, perm, keep)
@@ -231,6 +247,8 @@ def nsp_build(A, part, nblocks, perm=None, **kw):
 
 def nsp_build_batched(mats, **kw):
     """Build one handle for a batch of matrices: mats = [(A, part, nblocks), ...]."""
+    _check_sketch(kw, sum(int((np.asarray(pt) < 0).sum()) for _, pt, _ in mats),
+                  sum(int((np.asarray(pt) >= 0).sum()) for _, pt, _ in mats))
     keep = []
     csrs = (nsp_csr * len(mats))()
     parts = (nsp_partition * len(mats))()

@@ -104,3 +104,18 @@ def test_rejects_malformed_inputs():
     _expect(N, 1, A, part, 2, perm[:-1].tolist() + [perm[0]])
     # empty interface
     _expect(N, 1, A, np.zeros_like(part), 1)
+
+
+def test_short_sketch_refused_before_the_library_reads_it():
+    import paper_2101_12164_gb300 as N
+    A, part, _ = tiny_problem((9, 8), 2, None)
+    n_g, n_i = int((part < 0).sum()), int((part >= 0).sum())
+    with pytest.raises(ValueError):
+        N.nsp_build(A, part, 2, k=4, p=2, sketch=np.zeros((n_g, 5)))
+    with pytest.raises(ValueError):      # M3 reads an interior sketch
+        N.nsp_build(A, part, 2, k=4, p=2, sketch=np.zeros((n_g, 6)), variant="m3")
+    with pytest.raises(ValueError):
+        N.nsp_build_batched([(A, part, 2), (A, part, 2)], k=4, p=2,
+                            sketch=np.zeros((n_g, 6)))
+    N._check_sketch(dict(k=4, p=2, sketch=np.zeros((n_i, 6)), variant="m3"), n_g, n_i)
+    N._check_sketch(dict(k=4, p=2, sketch=np.zeros((n_g, 6))), n_g, n_i)
