@@ -461,3 +461,42 @@ def test_kept_columns_drops_exactly_the_dependent_columns():
         grows = np.linalg.matrix_rank(W[:, prev + [j]]) > np.linalg.matrix_rank(W[:, prev]) \
             if prev else np.linalg.norm(W[:, j]) > 0
         assert (j in keep) == bool(grows), j
+
+
+# ---------------------------------------------------------------- Proposition 4.1 (§4.2)
+def test_expected_effective_condition_within_proposition_4_1():
+    # I - H = R^{-T} S_G R^{-1} (A_G = R^T R); the oracle's Nyström (Algorithm 1, q = 0, no
+    # truncation) of B = R^{-T} A_GI S_I^{-1} A_IG R^{-1} = (I - H)^{-1} - I (eq. (Rt_S-1_R))
+    # gives U (n_G x (k+p)); P = I - (I-H) U E^{-1} U^T. Over 60 seeds the mean sqrt of the
+    # effective condition number of P (I-H) stays below eq. (tight_bound), with lambda_1..k the
+    # k smallest eigenvalues of I - H (so that gamma_{t,k} <= 1) and E(c) of eq. (constant).
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=13)
+    D = O.DBBD(A, part)
+    n = D.n_G
+    R = np.linalg.cholesky(D.A_G.toarray()).T
+    Ri = np.linalg.inv(R)
+    IH = Ri.T @ D.dense_S_gamma() @ Ri
+    IH = 0.5 * (IH + IH.T)
+    lam = np.sort(np.linalg.eigvalsh(IH))            # lam[i-1] = lambda_i, increasing
+    k, p = min(4, int(np.sum(lam <= 0.5))), 4          # the proposition assumes lambda_k <= 1/2
+    assert k >= 2 and lam[k - 1] <= 0.5
+    B = np.linalg.inv(IH) - np.eye(n)
+    B = 0.5 * (B + B.T)
+    Ec = np.sqrt(k / (p - 1)) + np.e * np.sqrt((k + p) * (n - k)) / p
+    gam = lambda t: (1 / lam[k] - 1) / (1 / lam[t - 1] - 1)
+    bound = np.sqrt(2) * min(max(Ec * np.sqrt(2 * t) * np.sqrt(gam(t)), 1.0)
+                             * np.sqrt(lam[-1] / lam[t]) for t in range(1, k + 1))
+    vals = []
+    for seed in range(60):
+        G = np.random.default_rng(1000 + seed).standard_normal((n, k + p))
+        U, _, _ = O.nystrom_core(G, B @ G, k + p, eps_rel=1e-13)
+        E = U.T @ IH @ U
+        P = np.eye(n) - IH @ U @ np.linalg.solve(E, U.T)
+        mu = np.sort(np.abs(np.linalg.eigvals(P @ IH)))[U.shape[1]:]   # drop the deflated zeros
+        vals.append(np.sqrt(mu[-1] / mu[0]))
+    assert np.mean(vals) <= bound
+    # the bound is loose here (about 16); what the Nyström basis must also do is align with the
+    # smallest eigenvectors of I - H: deflating it cuts sqrt(kappa) well below the first
+    # level's (a basis of the largest ones, from Nyström of I - H itself, would not)
+    assert np.max(vals) <= np.sqrt(lam[-1] / lam[0]) * (1 + 1e-8)
+    assert np.mean(vals) < 0.8 * np.sqrt(lam[-1] / lam[0])
