@@ -500,3 +500,23 @@ def test_expected_effective_condition_within_proposition_4_1():
     # level's (a basis of the largest ones, from Nyström of I - H itself, would not)
     assert np.max(vals) <= np.sqrt(lam[-1] / lam[0]) * (1 + 1e-8)
     assert np.mean(vals) < 0.8 * np.sqrt(lam[-1] / lam[0])
+
+
+# ---------------------------------------------------------------- paper trends (§5), config 0
+def test_block_cg_beats_per_column_cg_and_loose_inner_tolerance_is_harmless():
+    # §5.1: block CG on the k + p right-hand sides needs fewer iterations than CG on each
+    # column; §5.2: it_PCG is flat for eps_{S_I} in [0.01, 0.3]
+    P = F.make_problem(0)
+    D = O.DBBD(P.A, P.part, P.nsub)
+    G = F.make_sketch(D.n_G, P.s, 0)
+    _, b = F.make_rhs(P, 0)
+    Fh = D.A_GI @ D.solve_I(D.A_IG @ G)
+    _, it_block, _ = O.block_pcg(D.apply_S_gamma, D.solve_G, Fh, 0.1)
+    it_cols = [O.pcg(D.apply_S_gamma, D.solve_G, Fh[:, j], rtol=0.1)[1]
+               for j in range(Fh.shape[1])]
+    assert it_block < max(it_cols)
+    its = []
+    for eps in (0.01, 0.1, 0.3):
+        M, _ = O.build_m2(D, G, P.k, eps)
+        its.append(O.solve(D, M.apply, b, rtol=1e-8)[1])
+    assert max(its) - min(its) <= 2, its
