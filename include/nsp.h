@@ -211,7 +211,8 @@ nsp_status nsp_solve_batched(const nsp_handle *h, const double *b, double *x, do
 
 /* Repeat the numeric part of nsp_build (factorization + Algorithm 2) for new values of A
  * with the same pattern (val has nnz entries in the CSR order given to nsp_build; device
- * memory if on_device). prm may change k, p, tolerances, seed, sketch, variant (not precision). */
+ * memory if on_device). prm may change k, p, tolerances, seed, sketch, variant, inner_form, q (not
+ * precision). */
 nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device,
                        const nsp_params *prm);
 
