@@ -177,7 +177,9 @@ void nsp_default_params(nsp_params *prm);
  * block PCG (steps 2-4), Nyström core (steps 5-10), Z = A_G^{-1} U (step 11).
  * A is copied; the caller keeps ownership of all inputs. On success *out owns all device
  * memory of the preconditioner. Errors: INVALID_ARG, NOT_DBBD, NOT_SPD, BREAKDOWN, CUDA,
- * OOM; *out is NULL on error. */
+ * OOM, UNSUPPORTED; *out is NULL on error. The parameter checks that need no analysis of A
+ * (k, p, k + p, precision, inner_form, variant, q; for batched handles also their
+ * restrictions) run on the host before any device work. */
 nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params *prm,
                      nsp_handle **out);
 

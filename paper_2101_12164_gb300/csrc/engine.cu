@@ -1751,6 +1751,31 @@ static nsp::EngineBase *make_engine(const nsp_csr *A, const int64_t *rp, const i
   throw nsp::Error(NSP_ERR_INVALID_ARG, "precision");
 }
 
+// The parameter checks of Engine::construct / construct_batched that need no analysis, in the
+// same order and with the same status codes, run on the host before any device work so that
+// a malformed request fails fast (the engine repeats them).
+static void validate_params(const nsp_params *prm, bool batched) {
+  nsp::require(prm != nullptr, NSP_ERR_INVALID_ARG, "params");
+  nsp::require(prm->precision == NSP_FP64 || prm->precision == NSP_FP32, NSP_ERR_INVALID_ARG,
+               "precision");
+  if (batched) {
+    nsp::require(prm->variant == NSP_VARIANT_M2, NSP_ERR_UNSUPPORTED,
+                 "batched handles build M2 only");
+    nsp::require(prm->q == 0, NSP_ERR_UNSUPPORTED, "batched handles take no power iterations");
+    nsp::require(prm->k > 0 && prm->p >= 0, NSP_ERR_INVALID_ARG, "k > 0 and p >= 0 required");
+    nsp::require(prm->k + prm->p <= 96, NSP_ERR_UNSUPPORTED, "batched handles support k + p <= 96");
+    return;
+  }
+  nsp::require(prm->k > 0 && prm->p >= 0, NSP_ERR_INVALID_ARG, "k > 0 and p >= 0 required");
+  nsp::require(prm->k + prm->p <= 256, NSP_ERR_UNSUPPORTED, "k + p > 256");
+  // the engine's next checks (k + p <= n_Gamma, then these) all answer NSP_ERR_INVALID_ARG
+  nsp::require(prm->inner_form == NSP_FORM_SGAMMA || prm->inner_form == NSP_FORM_SI,
+               NSP_ERR_INVALID_ARG, "unknown inner form");
+  nsp::require(prm->variant >= NSP_VARIANT_M2 && prm->variant <= NSP_VARIANT_M3_ADEF,
+               NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
+  nsp::require(prm->q >= 0 && prm->q <= 16, NSP_ERR_INVALID_ARG, "power iterations q in [0, 16]");
+}
+
 nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params *prm,
                      nsp_handle **out) {
   if (!out) return NSP_ERR_INVALID_ARG;
@@ -1758,7 +1783,7 @@ nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params 
   auto h = std::make_unique<nsp_handle>();
   nsp_status s = guard([&] {
     nsp::validate_csr(A);
-    nsp::require(prm != nullptr, NSP_ERR_INVALID_ARG, "params");
+    validate_params(prm, false);
     h->prm = *prm;
     std::vector<int64_t> rp;
     std::vector<int32_t> ci;
@@ -1786,6 +1811,7 @@ nsp_status nsp_build_batched(int32_t count, const nsp_csr *A, const nsp_partitio
   *out = nullptr;
   auto h = std::make_unique<nsp_handle>();
   nsp_status s = guard([&] {
+    validate_params(prm, true);
     h->prm = *prm;
     h->batch = count;
     // block-diagonal concatenation: unknowns and interior blocks renumbered matrix by matrix
@@ -1881,6 +1907,7 @@ nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device, cons
   return guard([&] {
     if (prm) {
       nsp::require(prm->precision == h->prm.precision, NSP_ERR_INVALID_ARG, "precision change");
+      validate_params(prm, h->batch > 0);
       void *stream = h->prm.stream;
       h->prm = *prm;
       h->prm.stream = stream;

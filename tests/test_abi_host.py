@@ -119,3 +119,38 @@ def test_short_sketch_refused_before_the_library_reads_it():
                             sketch=np.zeros((n_g, 6)))
     N._check_sketch(dict(k=4, p=2, sketch=np.zeros((n_i, 6)), variant="m3"), n_g, n_i)
     N._check_sketch(dict(k=4, p=2, sketch=np.zeros((n_g, 6))), n_g, n_i)
+
+
+def _build_status(N, A, part, nsub, batched=False, **fields):
+    keep = []
+    csr = N._csr_struct(A, keep)
+    ps = N._part_struct(part, nsub, None, keep)
+    prm = N.make_params(k=4, p=2, stream=0)
+    for f, v in fields.items():
+        setattr(prm, f, v)
+    h = ctypes.c_void_p()
+    if batched:
+        csrs, parts = (N.nsp_csr * 1)(csr), (N.nsp_partition * 1)(ps)
+        st = N.lib().nsp_build_batched(1, csrs, parts, ctypes.byref(prm), ctypes.byref(h))
+    else:
+        st = N.lib().nsp_build(ctypes.byref(csr), ctypes.byref(ps), ctypes.byref(prm),
+                               ctypes.byref(h))
+    if st == 0:
+        N.lib().nsp_destroy(h)
+    return st
+
+
+def test_parameters_checked_on_the_host_before_device_work():
+    # these statuses come back without a GPU: the checks run before any allocation
+    N = lib_or_build()
+    A, part, _ = tiny_problem((9, 8), 2, None)
+    bad = [dict(k=0), dict(p=-1), dict(variant=7), dict(q=-1), dict(q=17),
+           dict(inner_form=3), dict(precision=5)]
+    for f in bad:
+        assert _build_status(N, A, part, 2, **f) == 1, f          # NSP_ERR_INVALID_ARG
+    assert _build_status(N, A, part, 2, k=200, p=100) == 9         # NSP_ERR_UNSUPPORTED
+    for f in (dict(variant=1), dict(variant=2), dict(q=1), dict(k=60, p=40)):
+        assert _build_status(N, A, part, 2, batched=True, **f) == 9, f
+    # valid requests pass the checks (then build, or fail later at the device on a CPU machine)
+    for f in (dict(), dict(variant=3), dict(q=2), dict(inner_form=1)):
+        assert _build_status(N, A, part, 2, **f) not in (1, 9), f
