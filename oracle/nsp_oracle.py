@@ -16,6 +16,7 @@ Everything here is plain, slow and follows the paper step by step in float64:
 * ``build_m2``             : Algorithm 2, in the paper's S_I form (step 3) or the
                              equivalent S_Gamma correction form (SMW identity, §4.1 eq. (S-1)),
                              optionally with q power iterations (§2.1 eq. (power)).
+* ``build_m1``             : the variant M1 of §4.1 with a dense R_Gamma (small interfaces).
 * ``build_m3``             : the variant M3 of §4.3 (Nyström on S_I^{-1}), and M_{3A-DEF}.
 * ``M2ADEF``               : the adapted-deflation variant M_{2A-DEF} of §4.3 (defined
                              like eq. (deflation_comp_from_low_rank) and eq.
@@ -330,6 +331,28 @@ def build_m2(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500
     if variant != "M2":
         raise ValueError(variant)
     return M2(dbbd, Z, Sigma), info
+
+
+def build_m1(dbbd, G, k, eps_inner=0.1, form="S_gamma", eps_rel=1e-10, maxit=500,
+             drop_tol=1e-12):
+    """The variant M1 of §4.1 (eq. (proposed_deflation_prec), eq. (prec1S)).
+
+    R_G is the dense upper Cholesky factor of A_G (A_G = R^T R), so this is for interfaces of
+    up to a few thousand unknowns. Nyström (Algorithm 1) of
+    B = R^{-T} A_GI S_I^{-1} A_IG R^{-1} (eq. (lr_approximation_S-1_A-I)) with the sketch G:
+    F = B G = R^{-T} Y, where Y = A_GI S_I^{-1} A_IG (R^{-1} G) comes from the inner block PCG
+    (steps 2-4 of Algorithm 2 on the sketch R^{-1} G); steps 3-8 of Algorithm 1 on (G, F) give
+    Ub, Sigma; Zb = R^{-1} Ub and M1 = A_G^{-1} + Zb Sigma Zb^T. Returns (M1, info).
+    """
+    G = np.asarray(G, dtype=np.float64)
+    R = np.linalg.cholesky(dbbd.A_G.toarray()).T
+    Gp = sla.solve_triangular(R, G, lower=False)                  # R^{-1} G
+    X, Y, it, hist = sketch_product(dbbd, Gp, eps_inner, form, maxit, drop_tol)
+    F = sla.solve_triangular(R, Y, trans="T", lower=False)        # R^{-T} Y
+    Ub, Sigma, info = nystrom_core(G, F, k, eps_rel)
+    Zb = sla.solve_triangular(R, Ub, lower=False)                 # R^{-1} Ub
+    info.update(it_inner=it, inner_hist=hist, X=X, Y=Y, U=Ub, R=R)
+    return M2(dbbd, Zb, Sigma), info
 
 
 def build_m3(dbbd, G_I, k, eps_inner=0.1, eps_rel=1e-10, maxit=500, drop_tol=1e-12,

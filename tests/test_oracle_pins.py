@@ -520,3 +520,40 @@ def test_block_cg_beats_per_column_cg_and_loose_inner_tolerance_is_harmless():
         M, _ = O.build_m2(D, G, P.k, eps)
         its.append(O.solve(D, M.apply, b, rtol=1e-8)[1])
     assert max(its) - min(its) <= 2, its
+
+
+# ---------------------------------------------------------------- M1 (§4.1)
+def test_m1_without_truncation_is_m2_on_the_transformed_sketch():
+    # k = s, exact solves: F (G^T F)^+ F^T with F = R^{-T} Y and G^T F = (R^{-1} G)^T Y, so
+    # R^{-1} Ub Sigma Ub^T R^{-T} = A_G^{-1} Y C^+ Y^T A_G^{-1}: M1(G) = M2(R^{-1} G)
+    A, part = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=14)
+    D = O.DBBD(A, part)
+    G = np.random.default_rng(61).standard_normal((D.n_G, 7))
+    M1, info = O.build_m1(D, G, k=7, eps_inner=1e-14, eps_rel=1e-13)
+    Gp = np.linalg.solve(np.linalg.cholesky(D.A_G.toarray()).T, G)
+    M2, _ = O.build_m2(D, Gp, k=7, eps_inner=1e-14, eps_rel=1e-13)
+    ref = M2.dense()
+    assert np.allclose(M1.dense(), ref, rtol=1e-7, atol=1e-9 * np.abs(ref).max())
+    # eq. (Rt_S-1_R): R S_G^{-1} R^T = I + R^{-T} A_GI S_I^{-1} A_IG R^{-1}; Ub Sigma Ub^T is its
+    # Nyström approximation, so it never exceeds R S_G^{-1} R^T - I
+    R = info["R"]
+    B = R @ np.linalg.inv(D.dense_S_gamma()) @ R.T - np.eye(D.n_G)
+    Bk = (info["U"] * M1.Sigma) @ info["U"].T
+    assert np.linalg.eigvalsh(0.5 * (B - Bk + (B - Bk).T)).min() > -1e-8 * np.abs(B).max()
+
+
+def test_m1_exact_when_rank_captured_and_spectral_inclusion():
+    A, part, D = _small_problem()
+    s = D.n_G + 2
+    G = np.random.default_rng(62).standard_normal((D.n_G, s))
+    M, _ = O.build_m1(D, G, k=s, eps_inner=1e-14, eps_rel=1e-13)
+    Sinv = np.linalg.inv(D.dense_S_gamma())
+    assert np.allclose(M.dense(), Sinv, rtol=1e-7, atol=1e-9 * np.abs(Sinv).max())
+    A2, part2 = tiny((14, 14), 4, lognormal=(3.0, 1.5), seed=4)
+    D2 = O.DBBD(A2, part2)
+    S = D2.dense_S_gamma()
+    lam1 = sla.eigh(S, D2.A_G.toarray(), eigvals_only=True).min()
+    G2 = np.random.default_rng(63).standard_normal((D2.n_G, 9))
+    M2, _ = O.build_m1(D2, G2, k=5, eps_inner=1e-14)
+    mu = np.linalg.eigvals(M2.dense() @ S).real
+    assert mu.min() >= lam1 * (1 - 1e-7) and mu.max() <= 1 + 1e-7
