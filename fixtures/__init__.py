@@ -12,14 +12,17 @@ Nothing in this package computes any step of the preconditioner itself.
 
 from .seeds import substream_seed, rng_for, MASTER_SEED
 from .grids import grid_coords, diffusion_matrix
-from .fields import gaussian_field, lognormal_field
+from .fields import gaussian_field, gaussian_grid_field, lognormal_field, lognormal_grid_field
 from .partition import nd_partition, interior_nd_order
-from .configs import (CONFIGS, Problem, make_problem, make_rhs, make_sketch,
+from .configs import (CONFIGS, Problem, make_problem, make_rhs, make_sketch, make_probe,
+                      sample_rows,
                       batched_problem_specs, problem_from_spec)
 
 __all__ = [
     "substream_seed", "rng_for", "MASTER_SEED", "grid_coords", "diffusion_matrix",
-    "gaussian_field", "lognormal_field", "nd_partition", "interior_nd_order",
-    "CONFIGS", "Problem", "make_problem", "make_rhs", "make_sketch",
+    "gaussian_field", "gaussian_grid_field", "lognormal_field", "lognormal_grid_field",
+    "nd_partition", "interior_nd_order",
+    "CONFIGS", "Problem", "make_problem", "make_rhs", "make_sketch", "make_probe",
+    "sample_rows",
     "batched_problem_specs", "problem_from_spec",
 ]

@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .fields import lognormal_field
+from .fields import lognormal_grid_field
 from .grids import diffusion_matrix, grid_coords
 from .partition import interior_nd_order, nd_partition
 from .seeds import rng_for
@@ -50,7 +50,7 @@ class Problem:
     shape: tuple
     A: object                 # scipy.sparse.csr_matrix, float64, sorted indices
     part: np.ndarray          # int32, subdomain id or -1 for Gamma
-    perm: np.ndarray          # int64 elimination order of the interior nodes, block by block
+    boxes: list               # (lo, hi) inclusive grid bounds of each subdomain
     nsub: int
     k: int
     p: int
@@ -59,6 +59,16 @@ class Problem:
     coef: np.ndarray = None
     coords: np.ndarray = None
     meta: dict = field(default_factory=dict)
+    leaf: int = 16
+    _perm: np.ndarray = None
+
+    @property
+    def perm(self):
+        """int64 elimination order of the interior nodes, block by block (geometric nested
+        dissection inside each subdomain box), computed on first use."""
+        if self._perm is None:
+            self._perm = interior_nd_order(self.shape, self.boxes, self.leaf)
+        return self._perm
 
     @property
     def n(self):
@@ -81,9 +91,8 @@ class Problem:
 def _build(name, shape, nsub, k, p, coef=None, axis_scale=None, leaf=16, meta=None):
     A = diffusion_matrix(shape, coef, axis_scale)
     part, boxes = nd_partition(shape, nsub)
-    perm = interior_nd_order(shape, boxes, leaf)
-    return Problem(name=name, shape=tuple(shape), A=A, part=part, perm=perm, nsub=nsub,
-                   k=k, p=p, coef=coef, coords=grid_coords(shape), meta=meta or {})
+    return Problem(name=name, shape=tuple(shape), A=A, part=part, boxes=boxes, nsub=nsub,
+                   k=k, p=p, coef=coef, coords=grid_coords(shape), meta=meta or {}, leaf=leaf)
 
 
 def make_problem(config: int, index: int = 0):
@@ -100,7 +109,7 @@ def make_problem(config: int, index: int = 0):
         if isinstance(ell, tuple):
             ell = float(rng.uniform(*ell))
             sigma = float(rng.uniform(*sigma))
-        coef = lognormal_field(grid_coords(shape), ell, sigma, rng)
+        coef = lognormal_grid_field(shape, ell, sigma, rng)
         meta = dict(ell=ell, sigma=sigma)
     return _build(c["name"], shape, c["nsub"], c["k"], c["p"], coef,
                   c.get("axis_scale"), meta=meta)
@@ -140,3 +149,14 @@ def make_rhs(problem: Problem, config: int, index: int = 0):
 def make_sketch(n_gamma: int, s: int, config: int, index: int = 0):
     """Gaussian sketch G (n_gamma x s, row-major float64) for parity runs."""
     return rng_for(config, index, "sketch").standard_normal((n_gamma, s))
+
+
+def make_probe(rows: int, cols: int, config: int, index: int = 0):
+    """Seeded N(0, 1) block (rows x cols) to probe an operator at full size."""
+    return rng_for(config, index, "probe").standard_normal((rows, cols))
+
+
+def sample_rows(n: int, count: int, config: int, index: int = 0):
+    """Sorted distinct seeded row indices in [0, n) at which full-size outputs are compared."""
+    rng = rng_for(config, index, "sample")
+    return np.sort(rng.choice(n, size=min(count, n), replace=False))

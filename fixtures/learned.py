@@ -15,7 +15,7 @@
 
 import numpy as np
 
-from .fields import lognormal_field
+from .fields import lognormal_grid_field
 from .grids import diffusion_matrix, grid_coords
 from .partition import nd_partition
 from .seeds import rng_for
@@ -76,7 +76,7 @@ def training_field(index, shape=(256, 256), ell_range=(4.0, 16.0), sigma_range=(
     rng = rng_for(config, index, "train")
     ell = float(rng.uniform(*ell_range)) * ell_scale
     sigma = float(rng.uniform(*sigma_range))
-    coef = lognormal_field(grid_coords(shape), ell, sigma, rng)
+    coef = lognormal_grid_field(shape, ell, sigma, rng)
     return coef, dict(ell=ell, sigma=sigma)
 
 

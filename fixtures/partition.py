@@ -14,19 +14,10 @@ which is the ordering a caller would normally hand to a sparse direct solver.
 
 import numpy as np
 
-from .grids import grid_coords
-
 
 def _split_axis(lo, hi):
     ext = [h - l + 1 for l, h in zip(lo, hi)]
     return int(np.argmax(ext))  # argmax returns the lowest axis on ties
-
-
-def _box_mask(coords, lo, hi):
-    m = np.ones(coords.shape[0], dtype=bool)
-    for t in range(coords.shape[1]):
-        m &= (coords[:, t] >= lo[t]) & (coords[:, t] <= hi[t])
-    return m
 
 
 def nd_partition(shape, nsub):
@@ -38,9 +29,9 @@ def nd_partition(shape, nsub):
     if 1 << levels != nsub:
         raise ValueError("nsub must be a power of two")
     shape = tuple(int(s) for s in shape)
-    coords = grid_coords(shape)
-    n = coords.shape[0]
+    n = int(np.prod(shape))
     part = np.full(n, -1, dtype=np.int32)
+    grid = part.reshape(shape, order="F")   # view: grid[x, y, ...] is node x + nx*(y + ...)
     boxes = []
 
     def rec(lo, hi, depth):
@@ -49,7 +40,7 @@ def nd_partition(shape, nsub):
         if depth == levels:
             b = len(boxes)
             boxes.append((tuple(lo), tuple(hi)))
-            part[_box_mask(coords, lo, hi)] = b
+            grid[tuple(slice(l, h + 1) for l, h in zip(lo, hi))] = b
             return
         ax = _split_axis(lo, hi)
         m = (lo[ax] + hi[ax]) // 2

@@ -12,7 +12,8 @@ MASTER_SEED = 210112164
 _MASK = (1 << 64) - 1
 
 # purposes of random draws
-PURPOSE = {"field": 1, "xstar": 2, "sketch": 3, "net_init": 4, "draw": 5, "train": 6}
+PURPOSE = {"field": 1, "xstar": 2, "sketch": 3, "net_init": 4, "draw": 5, "train": 6,
+           "probe": 7, "sample": 8}
 
 
 def _splitmix64(state):

@@ -164,6 +164,14 @@ typedef struct {
   double ms_analyze, ms_factor, ms_inner, ms_core, ms_solve;   /* host wall times (ms)     */
   int32_t it_power;          /* block-PCG iterations of the q power passes (it_inner is the
                                 final pass's)                                              */
+  /* Condition estimate of the preconditioned operator of the last nsp_solve (the kappa of
+   * the CG error bound, §1 eq. (k-th_error_cg), and kappa_eff of §4.2): extreme eigenvalues
+   * of the Lanczos tridiagonal formed from the outer PCG's coefficients (alpha_j step
+   * lengths, beta_j direction ratios; CG and Lanczos share one Krylov basis), computed by
+   * Sturm-sequence bisection. They are Ritz values of M2 S_Gamma (for NSP_OUTER_FULL the
+   * same numbers: its iterates equal the Schur form's). 0 when no iteration ran; batched
+   * handles leave them 0.                                                                  */
+  double lambda_min_est, lambda_max_est, kappa_est;
 } nsp_info;
 
 typedef struct nsp_handle nsp_handle;

@@ -26,6 +26,11 @@ Everything here is plain, slow and follows the paper step by step in float64:
 * ``solve_full_space``     : PCG on A with the block-factorization preconditioner of §2.3
                              whose Schur block is M2 (a reading used by the GPU's
                              mixed-precision outer solve; equal iterates in exact arithmetic).
+* ``lanczos_tridiagonal``,
+  ``kappa_estimate``       : the condition number of the preconditioned operator (the
+                             kappa of the CG error bound eq. (k-th_error_cg) of §1, and the
+                             kappa_eff of §4.2) estimated from the outer PCG's coefficients,
+                             whose Lanczos tridiagonal has the extreme Ritz values.
 
 Library primitives used as single steps: SuperLU sparse direct solves (for A_I^{-1},
 A_Gamma^{-1}), numpy QR, symmetric EVD, dense Cholesky, matrix products.
@@ -380,10 +385,13 @@ def build_m3(dbbd, G_I, k, eps_inner=0.1, eps_rel=1e-10, maxit=500, drop_tol=1e-
 # ----------------------------------------------------------------------------------------
 # Outer PCG on S_Gamma w = f (§2.3 eq. (Sx=b)), and the block elimination of §2.3 eq. (A_LDLT)
 # ----------------------------------------------------------------------------------------
-def pcg(apply_A, apply_M, f, rtol=1e-8, maxit=500, x0=None):
+def pcg(apply_A, apply_M, f, rtol=1e-8, maxit=500, x0=None, coeffs=None):
     """Textbook PCG. Stops when ||r_k|| / ||f|| <= rtol on the updated residual.
 
     Returns (x, iterations, residual history); iterations = number of operator applies.
+    ``coeffs`` (a dict, optional) receives the step lengths alpha_j = r_j^T z_j / p_j^T A p_j
+    ("alpha", one per iteration) and the ratios beta_j = r_{j+1}^T z_{j+1} / r_j^T z_j that
+    formed the next direction ("beta", one fewer).
     """
     f = np.asarray(f, dtype=np.float64)
     x = np.zeros_like(f) if x0 is None else np.array(x0, dtype=np.float64)
@@ -398,6 +406,8 @@ def pcg(apply_A, apply_M, f, rtol=1e-8, maxit=500, x0=None):
     p = z.copy()
     rz = r @ z
     it = 0
+    if coeffs is not None:
+        coeffs["alpha"], coeffs["beta"] = [], []
     while it < maxit:
         q = apply_A(p)
         alpha = rz / (p @ q)
@@ -405,16 +415,52 @@ def pcg(apply_A, apply_M, f, rtol=1e-8, maxit=500, x0=None):
         r -= alpha * q
         it += 1
         hist.append(np.linalg.norm(r) / fn)
+        if coeffs is not None:
+            coeffs["alpha"].append(float(alpha))
         if hist[-1] <= rtol:
             break
         z = apply_M(r)
         rz_new = r @ z
-        p = z + (rz_new / rz) * p
+        beta = rz_new / rz
+        p = z + beta * p
         rz = rz_new
+        if coeffs is not None:
+            coeffs["beta"].append(float(beta))
     return x, it, hist
 
 
-def solve(dbbd, prec_apply, b, rtol=1e-8, maxit=500):
+def lanczos_tridiagonal(alpha, beta):
+    """The m x m Lanczos tridiagonal T of PCG's first m iterations (Saad, Iterative Methods
+    for Sparse Linear Systems, 2nd ed., §6.7.3: CG and Lanczos generate the same Krylov
+    basis). With preconditioner M and operator A, T is the matrix of the symmetrized
+    operator M^{1/2} A M^{1/2} in the orthonormal basis of normalized preconditioned
+    residuals; written in the coefficients alone:
+        T[0, 0] = 1 / alpha_0,
+        T[j, j] = 1 / alpha_j + beta_{j-1} / alpha_{j-1}          (j >= 1),
+        T[j-1, j] = T[j, j-1] = sqrt(beta_{j-1}) / alpha_{j-1}.
+    Its eigenvalues are Ritz values of the preconditioned operator M A; after n steps on an
+    n x n system they are its eigenvalues."""
+    a = np.asarray(alpha, dtype=np.float64)
+    b = np.asarray(beta, dtype=np.float64)[:max(len(a) - 1, 0)]
+    m = len(a)
+    T = np.zeros((m, m))
+    for j in range(m):
+        T[j, j] = 1.0 / a[j] + (b[j - 1] / a[j - 1] if j > 0 else 0.0)
+        if j > 0:
+            T[j - 1, j] = T[j, j - 1] = np.sqrt(b[j - 1]) / a[j - 1]
+    return T
+
+
+def kappa_estimate(alpha, beta):
+    """(lambda_min, lambda_max, kappa) of the preconditioned operator estimated by the
+    extreme eigenvalues of ``lanczos_tridiagonal`` (numpy's symmetric EVD as one step)."""
+    if len(alpha) == 0:
+        return 0.0, 0.0, 0.0
+    e = np.linalg.eigvalsh(lanczos_tridiagonal(alpha, beta))
+    return float(e[0]), float(e[-1]), float(e[-1] / e[0])
+
+
+def solve(dbbd, prec_apply, b, rtol=1e-8, maxit=500, coeffs=None):
     """x = A^{-1} b by the block elimination of §2.3 eq. (A_LDLT) with PCG on S_Gamma (§2.3 eq. (Sx=b)).
 
     f = b_G - A_GI A_I^{-1} b_I; PCG on S_Gamma w = f preconditioned by ``prec_apply``;
@@ -423,7 +469,7 @@ def solve(dbbd, prec_apply, b, rtol=1e-8, maxit=500):
     b = np.asarray(b, dtype=np.float64)
     bI, bG = b[dbbd.interior], b[dbbd.gamma]
     f = bG - dbbd.A_GI @ dbbd.solve_I(bI)
-    w, it, hist = pcg(dbbd.apply_S_gamma, prec_apply, f, rtol, maxit)
+    w, it, hist = pcg(dbbd.apply_S_gamma, prec_apply, f, rtol, maxit, coeffs=coeffs)
     xI = dbbd.solve_I(bI - dbbd.A_IG @ w)
     x = np.empty(dbbd.n)
     x[dbbd.interior] = xI
@@ -431,7 +477,7 @@ def solve(dbbd, prec_apply, b, rtol=1e-8, maxit=500):
     return x, it, hist
 
 
-def solve_full_space(dbbd, prec_apply, b, rtol=1e-8, maxit=500):
+def solve_full_space(dbbd, prec_apply, b, rtol=1e-8, maxit=500, coeffs=None):
     """PCG on A x = b with the block-factorization preconditioner of §2.3 (Schur block M2).
 
     M^{-1} r: z_G = M2 (r_G - A_GI A_I^{-1} r_I), z_I = A_I^{-1}(r_I - A_IG z_G).
@@ -455,7 +501,7 @@ def solve_full_space(dbbd, prec_apply, b, rtol=1e-8, maxit=500):
     x0[I] = dbbd.solve_I(b[I])
     r0 = b - A @ x0
     fn = np.linalg.norm(r0)
-    x, it, hist = pcg(lambda v: A @ v, prec, r0, rtol, maxit)
+    x, it, hist = pcg(lambda v: A @ v, prec, r0, rtol, maxit, coeffs=coeffs)
     return x0 + x, it, hist
 
 

@@ -71,7 +71,9 @@ class nsp_info(C.Structure):
                 ("final_residual", C.c_double), ("pcg_residual", C.c_double),
                 ("failed_block", C.c_int32), ("ms_analyze", C.c_double),
                 ("ms_factor", C.c_double), ("ms_inner", C.c_double), ("ms_core", C.c_double),
-                ("ms_solve", C.c_double), ("it_power", C.c_int32)]
+                ("ms_solve", C.c_double), ("it_power", C.c_int32),
+                ("lambda_min_est", C.c_double), ("lambda_max_est", C.c_double),
+                ("kappa_est", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -265,6 +265,52 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
   an.ms = ms_since(t0);
 }
 
+// Extreme eigenvalues of the Lanczos tridiagonal of a PCG run (Saad, Iterative Methods for
+// Sparse Linear Systems, §6.7.3): diagonal 1/a_0, 1/a_j + b_{j-1}/a_{j-1}; off-diagonal
+// sqrt(b_{j-1})/a_{j-1}. Bisection on the Sturm count (number of eigenvalues below x, the
+// negative pivots of T - x I; Golub & Van Loan §8.4), inside the Gershgorin interval.
+static void lanczos_extremes(const std::vector<double> &a, const std::vector<double> &b,
+                             double *lmin, double *lmax) {
+  *lmin = *lmax = 0.0;
+  const int m = (int)a.size();
+  if (m == 0) return;
+  std::vector<double> d(m), e2(m, 0.0), e(m, 0.0);
+  for (int j = 0; j < m; ++j) {
+    d[j] = 1.0 / a[j] + (j > 0 ? b[j - 1] / a[j - 1] : 0.0);
+    if (j > 0) {
+      e[j] = std::sqrt(std::max(b[j - 1], 0.0)) / a[j - 1];
+      e2[j] = e[j] * e[j];
+    }
+  }
+  double lo = d[0], hi = d[0];
+  for (int j = 0; j < m; ++j) {
+    const double r = (j > 0 ? std::fabs(e[j]) : 0.0) + (j + 1 < m ? std::fabs(e[j + 1]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  auto below = [&](double x) {           // eigenvalues < x
+    int c = 0;
+    double q = 1.0;
+    for (int j = 0; j < m; ++j) {
+      q = d[j] - x - (j > 0 ? e2[j] / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0.0) ++c;
+    }
+    return c;
+  };
+  auto kth = [&](int k) {                // k-th smallest (0-based)
+    double l = lo, h = hi;
+    for (int it = 0; it < 200 && h - l > 1e-15 * std::max(std::fabs(l), std::fabs(h)); ++it) {
+      const double mid = 0.5 * (l + h);
+      if (below(mid) > k) h = mid;
+      else l = mid;
+    }
+    return 0.5 * (l + h);
+  };
+  *lmin = kth(0);
+  *lmax = kth(m - 1);
+}
+
 // ------------------------------------------------------------------ device containers
 template <typename T>
 struct DevCsr {
@@ -1051,6 +1097,8 @@ struct Engine : EngineBase {
   }
 
   // ---- PCG (textbook; FP64 recurrences, scalars kept on the device)
+  std::vector<double> lanczos_alpha, lanczos_beta;   // coefficients of the last outer PCG
+
   template <typename Aop, typename Mop>
   int pcg(int64_t n, Aop &&A, Mop &&M, const double *f, double *x, double rtol, int maxit,
           double *rel_out) {
@@ -1065,6 +1113,8 @@ struct Engine : EngineBase {
     sync();
     const double fn = std::sqrt(hscal[0]);
     *rel_out = 0.0;
+    lanczos_alpha.clear();
+    lanczos_beta.clear();
     if (fn == 0.0) return 0;
     M(vr.p, vz.p);
     NSP_CUDA(cudaMemcpyAsync(vp.p, vz.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1079,9 +1129,12 @@ struct Engine : EngineBase {
       launch_axpby(n, d_alpha, -1.0, vq.p, 1.0, vr.p, st);
       ++it;
       launch_dot(vr.p, vr.p, n, d_rr, dwork.p, st);
-      NSP_CUDA(cudaMemcpyAsync(hscal, d_rr, sizeof(double), cudaMemcpyDeviceToHost, st));
+      // alpha_j, beta_{j-1} (the ratio that formed this direction) and r^T r in one copy
+      NSP_CUDA(cudaMemcpyAsync(hscal + 2, d_alpha, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
       sync();
-      rel = std::sqrt(std::max(hscal[0], 0.0)) / fn;
+      lanczos_alpha.push_back(hscal[2]);
+      if (it >= 2) lanczos_beta.push_back(hscal[3]);
+      rel = std::sqrt(std::max(hscal[4], 0.0)) / fn;
       if (!(rel > rtol)) break;
       M(vr.p, vz.p);
       launch_dot(vr.p, vz.p, n, d_rznew, dwork.p, st);
@@ -1155,6 +1208,8 @@ struct Engine : EngineBase {
     check_status();
     info.it_pcg = it;
     info.pcg_residual = rel;
+    lanczos_extremes(lanczos_alpha, lanczos_beta, &info.lambda_min_est, &info.lambda_max_est);
+    info.kappa_est = info.lambda_min_est > 0 ? info.lambda_max_est / info.lambda_min_est : 0.0;
     info.final_residual = hscal[9] > 0 ? std::sqrt(hscal[8] / hscal[9]) : 0.0;
     info.ms_solve = ms_since(t0);
     if (rel > rtol) throw Error(NSP_ERR_NOT_CONVERGED, "outer PCG did not converge");

@@ -9,7 +9,7 @@ import pytest
 import fixtures as F
 import oracle as O
 
-from ._util import lib_or_build, tiny_problem
+from ._util import lib_or_build, operator_err, tiny_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +23,6 @@ def N():
 def torch():
     import torch as T
     return T
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 def _parity(N, torch, A, part, nsub, k, p, prec="fp64", its_tol=2):
@@ -56,7 +52,7 @@ def test_widest_sketch_block(N, torch):
     # agree to 1e-7; the tail of the 200 kept eigenvalues is clustered (relative gaps ~1e-2),
     # so the eigenvectors carry rounding of order eps * cond / gap: 1e-5 as an operator
     assert np.allclose(S, M.Sigma, rtol=1e-7)
-    assert _rel((Z * S) @ Z.T, (M.Z * M.Sigma) @ M.Z.T) < 1e-5
+    assert operator_err(Z, S, M.Z, M.Sigma) < 1e-5
     h.destroy()
 
 

@@ -1,9 +1,14 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step.
 
-Tolerances: FP64 handles are compared at rounding level (the two sides factorize with
+Every comparison is entry-wise, column by column (``colwise_err``: the largest
+|gpu - oracle| of a column over that column's largest |oracle| entry), except the Nyström
+factor, which is compared as an operator (eigenvector signs and rotations inside clusters are
+arbitrary). Tolerances: FP64 handles at rounding level (the two sides factorize with
 different orderings, so agreement is to a few hundred ulps times the condition number of
-the operation); FP32 handles at the FP32 level, relative error <= c * kappa * 2^-24 with
-the bounds written in each test.
+the operation); FP32 handles at the FP32 level, c * kappa * 2^-24 with the bounds written in
+each test. The case "cluster3d" (a 20^3 grid in two subdomains) has fronts of more than 192
+rows, so its factorization takes the clustered path (a cluster of CTAs per front); the
+factor test checks that such a front exists.
 """
 
 import numpy as np
@@ -13,7 +18,7 @@ import fixtures as F
 import oracle as O
 from oracle import philox
 
-from ._util import lib_or_build, tiny_problem
+from ._util import colwise_err, lib_or_build, operator_err, tiny_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -21,7 +26,9 @@ CASES = {
     "tiny2d": dict(shape=(13, 11), nsub=2, lognormal=(3.0, 1.5)),
     "tiny3d": dict(shape=(9, 8, 7), nsub=4, lognormal=(2.0, 1.5)),
     "ragged2d": dict(shape=(37, 29), nsub=4, lognormal=(5.0, 2.0)),
+    "cluster3d": dict(shape=(20, 20, 20), nsub=2, lognormal=(4.0, 1.5)),
 }
+BIG_FRONT = 192   # fronts with at least this many rows are factorized by a CTA cluster
 
 
 @pytest.fixture(scope="module")
@@ -41,21 +48,24 @@ def _case(name):
     return A, part, c["nsub"]
 
 
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
-
-
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_factor_entries_match_dense_cholesky(N, name, prec):
     A, part, nsub = _case(name)
     h = N.nsp_build(A, part, nsub, k=4, p=2, precision=prec)
-    tol = 1e-11 if prec == "fp64" else 2e-5
+    tol = 1e-10 if prec == "fp64" else 1e-4
     sizes = [int((part == b).sum()) for b in range(nsub)] + [int((part < 0).sum())]
+    biggest = 0
     for b, nb in enumerate(sizes):
         order, L = h.get_factor(b, nb)
         ref = np.linalg.cholesky(A[order][:, order].toarray())
-        assert _rel(L, ref) < tol, (b, _rel(L, ref))
+        err = colwise_err(L, ref)
+        assert err < tol, (b, err)
+        # rows of the largest front: the structural column count of L (first column of a
+        # supernode = its front's rows)
+        biggest = max(biggest, int((L != 0).sum(axis=0).max()))
+    if name == "cluster3d":
+        assert biggest >= BIG_FRONT, biggest
     h.destroy()
 
 
@@ -68,7 +78,7 @@ def test_factor_solves_match_oracle(N, torch, name, prec, s):
     h = N.nsp_build(A, part, nsub, k=4, p=2, precision=prec)
     dt = torch.float64 if prec == "fp64" else torch.float32
     rng = np.random.default_rng(s)
-    tol = 1e-11 if prec == "fp64" else 1e-4
+    tol = 1e-10 if prec == "fp64" else 5e-4
     for which, n, ref_solve in ((0, D.n_I, D.solve_I), (1, D.n_G, D.solve_G)):
         B = rng.standard_normal((n, s))
         Bd = torch.tensor(B, dtype=dt, device="cuda")
@@ -76,8 +86,9 @@ def test_factor_solves_match_oracle(N, torch, name, prec, s):
         h.factor_solve(which, Bd, Xd)
         torch.cuda.synchronize()
         X = Xd.double().cpu().numpy()
-        ref = ref_solve(B)
-        assert _rel(X, ref) < tol, (which, _rel(X, ref))
+        ref = ref_solve(B.astype(np.float32).astype(np.float64) if prec == "fp32" else B)
+        err = colwise_err(X.reshape(n, s), ref.reshape(n, s))
+        assert err < tol, (which, err)
     h.destroy()
 
 
@@ -94,9 +105,10 @@ def test_schur_apply_matches_oracle(N, torch, name, prec, s):
     Yd = torch.empty_like(Xd)
     h.schur_apply(Xd, Yd)
     torch.cuda.synchronize()
-    ref = D.apply_S_gamma(X)
-    tol = 1e-10 if prec == "fp64" else 2e-4
-    assert _rel(Yd.double().cpu().numpy(), ref) < tol
+    ref = D.apply_S_gamma(X.astype(np.float32).astype(np.float64) if prec == "fp32" else X)
+    tol = 1e-9 if prec == "fp64" else 1e-3
+    err = colwise_err(Yd.double().cpu().numpy(), ref)
+    assert err < tol, err
     h.destroy()
 
 
@@ -123,13 +135,12 @@ def test_build_parity_fp64(N, name):
     assert gi["it_inner"] == info["it_inner"]
     assert gi["rank"] == len(info["eig_T"][:k])
     assert np.allclose(h.get_intermediate(0), G)
-    assert _rel(h.get_intermediate(1), info["X"]) < 1e-8
-    assert _rel(h.get_intermediate(2), info["Y"]) < 1e-8
+    assert colwise_err(h.get_intermediate(1), info["X"]) < 1e-7
+    assert colwise_err(h.get_intermediate(2), info["Y"]) < 1e-7
     Z, S = h.get_basis()
     assert np.allclose(S, info["eig_T"][:k], rtol=1e-8)
     # M2 as an operator: Z Sigma Z^T (signs/rotations of eigenvectors are arbitrary)
-    ref = (M.Z * M.Sigma) @ M.Z.T
-    assert _rel((Z * S) @ Z.T, ref) < 1e-7
+    assert operator_err(Z, S, M.Z, M.Sigma) < 1e-7
     h.destroy()
 
 
@@ -147,8 +158,9 @@ def test_apply_m2_matches_oracle(N, torch, name, prec):
     rd = torch.tensor(r, dtype=torch.float64, device="cuda")
     zd = torch.empty_like(rd)
     h.apply(rd, zd)
-    tol = 1e-8 if prec == "fp64" else 2e-3
-    assert _rel(zd.cpu().numpy(), M.apply(r)) < tol
+    tol = 1e-7 if prec == "fp64" else 5e-3
+    err = colwise_err(zd.cpu().numpy(), M.apply(r))
+    assert err < tol, err
     h.destroy()
 
 
@@ -163,13 +175,23 @@ def test_solve_parity(N, torch, name, prec, form):
     b = A @ x_star
     h = N.nsp_build(A, part, nsub, k=k, p=p, precision=prec, sketch=G, outer_form=form)
     M, _ = O.build_m2(D, G, k, 0.1)
-    _, it_ref, _ = O.solve(D, M.apply, b, rtol=1e-8)
+    c = {}
+    x_ref, it_ref, _ = O.solve(D, M.apply, b, rtol=1e-8, coeffs=c)
     bd = torch.tensor(b, dtype=torch.float64, device="cuda")
     xd = torch.zeros_like(bd)
     inf = h.solve(bd, xd, rtol=1e-8, maxit=500)
     x = xd.cpu().numpy()
     assert O.relative_residual(A, x, b) < 1e-8 * 10
     assert abs(inf["it_pcg"] - it_ref) <= 2, (inf["it_pcg"], it_ref)
+    # condition estimate of M2 S_Gamma from the outer PCG's Lanczos coefficients (both sides
+    # stop at 1e-8, where the extreme Ritz values have converged)
+    lmin, lmax, kappa = O.kappa_estimate(c["alpha"], c["beta"])
+    ktol = 1e-6 if (prec == "fp64" and inf["it_pcg"] == it_ref) else 5e-2
+    assert abs(inf["kappa_est"] - kappa) <= ktol * kappa, (inf["kappa_est"], kappa)
+    assert abs(inf["lambda_max_est"] - lmax) <= ktol * lmax
+    # the residual tolerance leaves x free up to kappa(A) * 1e-8 relative, on both sides:
+    # the GPU solution is entry-wise as close to the exact x* as the oracle's (within 10x)
+    assert colwise_err(x, x_star) <= 10 * max(colwise_err(x_ref, x_star), 1e-10)
     # host buffers go through the same entry point
     xh = np.zeros_like(b)
     inf2 = h.solve(np.ascontiguousarray(b), xh, rtol=1e-8, maxit=500)
@@ -206,5 +228,5 @@ def test_singular_c_matches_oracle(N):
     assert gi["rank"] == len(info["eig_T"][:k])
     Z, S = h.get_basis()
     assert np.allclose(S, info["eig_T"][:gi["rank"]], rtol=1e-8)
-    assert _rel((Z * S) @ Z.T, (M.Z * M.Sigma) @ M.Z.T) < 1e-7
+    assert operator_err(Z, S, M.Z, M.Sigma) < 1e-7
     h.destroy()
