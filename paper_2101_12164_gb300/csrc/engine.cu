@@ -348,8 +348,11 @@ struct ForestData {
     SweepPlan d;
     DBuf<int32_t> item_a, item_b, group_sn, sn_parent, need_f, units_f, units_b;
     DBuf<uint32_t> counters;  // cnt_f, self_f, done_b (nsn each), claim, abort, epoch, base
+    DBuf<int32_t> res_blk_ptr, res_lvl_ptr, res_lvl_nwarp, res_job;   // block-resident schedule
     int32_t maxneed = 1;
-    std::map<int, int> tuned_grid;  // right-hand-side count -> persistent grid (autotuner)
+    // right-hand-side count -> persistent grid of the dependency-driven sweep, or
+    // kResidentGrid for the block-resident sweep (autotuner)
+    std::map<int, int> tuned_grid;
   };
   std::unique_ptr<Plan> plans[2];  // 0: block (s > 1), 1: vector (s = 1)
   int vec_rows = 128;
@@ -478,6 +481,49 @@ struct ForestData {
     P.d.abort_flag = P.counters.p + 3 * (size_t)nsn + 1;
     P.d.epoch = P.counters.p + 3 * (size_t)nsn + 2;
     P.d.claim_base = P.counters.p + 3 * (size_t)nsn + 3;
+    // block-resident schedule: per block, its supernodes by height; warp-sized ones first,
+    // largest first, so that the warps' shares of a height are balanced
+    {
+      const int nb = h.nblocks;
+      std::vector<std::vector<std::vector<int32_t>>> bl(nb);
+      for (int J = 0; J < nsn; ++J) {
+        auto &v = bl[h.sn_block[J]];
+        const int l = h.sn_level[J];
+        if ((int)v.size() <= l) v.resize(l + 1);
+        v[l].push_back(J);
+      }
+      auto warp_sized = [&](int J) {
+        return vector ? (h.sn_m[J] <= kSmallM && h.sn_w[J] <= kSmallW)
+                      : (h.sn_w[J] <= kResW && h.sn_m[J] <= kResM);
+      };
+      std::vector<int32_t> bptr(nb + 1, 0), lptr(1, 0), lnw, job;
+      for (int b = 0; b < nb; ++b) {
+        for (auto &lev : bl[b]) {
+          if (lev.empty()) continue;
+          std::vector<int32_t> wv, cv;
+          for (int J : lev) (warp_sized(J) ? wv : cv).push_back(J);
+          std::stable_sort(wv.begin(), wv.end(), [&](int a, int c) {
+            return (int64_t)h.sn_m[a] * h.sn_w[a] > (int64_t)h.sn_m[c] * h.sn_w[c];
+          });
+          job.insert(job.end(), wv.begin(), wv.end());
+          job.insert(job.end(), cv.begin(), cv.end());
+          lnw.push_back((int32_t)wv.size());
+          lptr.push_back((int32_t)job.size());
+        }
+        bptr[b + 1] = (int32_t)lnw.size();
+      }
+      if (job.empty()) job.push_back(0);
+      if (lnw.empty()) lnw.push_back(0);
+      P.res_blk_ptr.upload(bptr, st);
+      P.res_lvl_ptr.upload(lptr, st);
+      P.res_lvl_nwarp.upload(lnw, st);
+      P.res_job.upload(job, st);
+      P.d.res_nblocks = nb;
+      P.d.res_blk_ptr = P.res_blk_ptr.p;
+      P.d.res_lvl_ptr = P.res_lvl_ptr.p;
+      P.d.res_lvl_nwarp = P.res_lvl_nwarp.p;
+      P.d.res_job = P.res_job.p;
+    }
     return P;
   }
 
@@ -703,13 +749,28 @@ struct Engine : EngineBase {
     auto &P = F.plan(sc == 1, st);
     int grid = 0;
     auto it = P.tuned_grid.find(sc);
-    if (it != P.tuned_grid.end()) {
+    if (const int forced = forced_scheduler(); forced != 0) {
+      grid = forced > 0 ? 0 : kResidentGrid;
+      if (grid == kResidentGrid && F.h.nblocks < 2) grid = 0;
+    } else if (it != P.tuned_grid.end()) {
       grid = it->second;
     } else if (autotune_enabled() && !capturing()) {
       grid = tune_sweep(F, P, panel, B, Ywk, Uwk, X, sc);
       P.tuned_grid[sc] = grid;
     }
-    launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, grid);
+    if (grid == kResidentGrid)
+      launch_res_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st);
+    else
+      launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, grid);
+  }
+  static constexpr int kResidentGrid = -1;
+  // NSP_SWEEP=resident / global forces one scheduler (measurements); unset: the autotuner
+  static int forced_scheduler() {
+    const char *e = std::getenv("NSP_SWEEP");
+    if (!e) return 0;
+    if (e[0] == 'r') return -1;
+    if (e[0] == 'g') return 1;
+    return 0;
   }
 
   // Autotuner of the persistent sweep: the grid (CTAs resident per SM, 1 to the occupancy
@@ -736,6 +797,21 @@ struct Engine : EngineBase {
     NSP_CUDA(cudaEventCreate(&e1));
     int best = gmax;
     float best_ms = 1e30f;
+    if (F.h.nblocks >= 2) {   // the block-resident sweep is a candidate for forests of blocks
+      float tot = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        NSP_CUDA(cudaEventRecord(e0, st));
+        launch_res_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st);
+        NSP_CUDA(cudaEventRecord(e1, st));
+        NSP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+      }
+      tune_log.push_back({kResidentGrid, tot / 2});
+      best_ms = tot;
+      best = kResidentGrid;
+    }
     for (int g = sms; g <= gmax; g += sms) {
       float tot = 0.f;
       for (int rep = 0; rep < 2; ++rep) {

@@ -23,13 +23,11 @@
 //                   (backward); supernodes with m <= 96, w <= 32 are processed a warp
 //                   each, up to 8 per item;
 //   block (s > 1):  a register-blocked (TM x K) * (K x s) product per tile on CUDA cores.
-#include "kernels.cuh"
+#include "sweep_tiles.cuh"
 
 namespace nsp {
 namespace {
 
-constexpr int ST = 256;      // threads per CTA
-constexpr int TK = 64;       // K chunk of the block product
 constexpr int MAX_SPINS = 1 << 22;  // default bound of a dependency wait (seconds at most)
 
 // ---------------------------------------------------------------- synchronization
@@ -69,567 +67,6 @@ __global__ void k_sweep_begin(SweepPlan p) {
     *p.claim_base = *p.claim;
   }
 }
-
-template <typename T>
-struct Vec;
-template <>
-struct Vec<float> {
-  using V = float4;
-  static constexpr int N = 4;
-  __device__ static V load(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-  __device__ static float get(const V &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
-};
-template <>
-struct Vec<double> {
-  using V = double2;
-  static constexpr int N = 2;
-  __device__ static V load(const double *p) { return __ldg(reinterpret_cast<const double2 *>(p)); }
-  __device__ static double get(const V &v, int i) { return i == 0 ? v.x : v.y; }
-};
-
-struct SweepCtx {
-  ForestDev f;
-  SweepPlan p;
-  int s;
-  DevStatus *st;
-  int max_spins;
-};
-
-// f_top / f_bot entry k of supernode J (column b, s columns): B row + children's update rows
-template <typename T>
-__device__ __forceinline__ T front_rhs(const SweepCtx &c, const T *B, const T *U, int J, int k,
-                                       int col, bool with_b) {
-  const int64_t rp = c.f.sn_rowptr[J];
-  T v = (with_b && B) ? B[(size_t)(c.f.sn_first[J] + k) * c.s + col] : T(0);
-  for (int64_t e = c.f.gptr[rp + k]; e < c.f.gptr[rp + k + 1]; ++e)
-    v += __ldcg(&U[(size_t)c.f.gsrc[e] * c.s + col]);
-  return v;
-}
-
-// v[i] += the update rows landing on front position pos[i] of the supernode whose rows start
-// at rp (pos[i] < 0: none), column col: the NR positions advance together so that their
-// dependent index and value loads are in flight at the same time.
-template <typename T, int NR>
-__device__ __forceinline__ void gather_rows(const SweepCtx &c, const T *U, int64_t rp,
-                                            const int (&pos)[NR], T (&v)[NR], int col) {
-  int64_t e[NR], ee[NR];
-#pragma unroll
-  for (int i = 0; i < NR; ++i) {
-    e[i] = pos[i] >= 0 ? c.f.gptr[rp + pos[i]] : 0;
-    ee[i] = pos[i] >= 0 ? c.f.gptr[rp + pos[i] + 1] : 0;
-  }
-  bool more = true;
-  while (more) {
-    int64_t src[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) src[i] = e[i] < ee[i] ? c.f.gsrc[e[i]] : -1;
-    more = false;
-#pragma unroll
-    for (int i = 0; i < NR; ++i)
-      if (src[i] >= 0) {
-        v[i] += __ldcg(&U[(size_t)src[i] * c.s + col]);
-        more |= ++e[i] < ee[i];
-      }
-  }
-}
-
-// ---------------------------------------------------------------- vector items (s = 1)
-// Forward tile: kVecRG row groups of VN rows x ST / kVecRG K groups; each thread keeps 8
-// vector loads in flight. Rows of the tile: kVecRG VN.
-constexpr int kVecRG = 32;
-template <typename T>
-__device__ void vec_fwd_tile(const SweepCtx &c, const T *panel, const T *B, T *Y, T *U, int J,
-                             int r0, T *sm) {
-  using VT = Vec<T>;
-  constexpr int VN = VT::N, TMV = kVecRG * VN, KG = ST / kVecRG;
-  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
-  const int first = c.f.sn_first[J];
-  const T *P = panel + c.f.sn_panel[J];
-  const int r1 = min(r0 + TMV, m);
-  const int kmax = (r1 <= w) ? r1 : w;
-  T *fs = sm;                      // [kmax]
-  T *red = sm + ((ld + 3) & ~3);   // [KG][TMV]
-  T *gb = red + KG * TMV;          // [TMV] update-row gathers of the tile's rows
-  const int tid = threadIdx.x;
-  for (int kb = tid; kb < kmax; kb += 3 * ST) {  // three positions' gathers in flight
-    int pos[3];
-    T v[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int k = kb + q * ST;
-      pos[q] = k < kmax ? k : -1;
-      v[q] = (k < kmax && B) ? B[first + k] : T(0);
-    }
-    gather_rows<T, 3>(c, U, c.f.sn_rowptr[J], pos, v, 0);
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      if (kb + q * ST < kmax) fs[kb + q * ST] = v[q];
-  }
-  if (kmax <= ST - TMV && tid >= ST - TMV) {  // otherwise idle threads gather concurrently
-    const int i = tid - (ST - TMV), r = r0 + i;
-    int pos[1] = {(r >= w && r < r1) ? r : -1};
-    T v[1] = {T(0)};
-    gather_rows<T, 1>(c, U, c.f.sn_rowptr[J], pos, v, 0);
-    gb[i] = v[0];
-  }
-  __syncthreads();
-  const int rg = tid % kVecRG, kg = tid / kVecRG;
-  const int row = r0 + VN * rg;
-  T acc[VN];
-#pragma unroll
-  for (int i = 0; i < VN; ++i) acc[i] = T(0);
-  if (row < ld) {
-    int k = kg;
-    for (; k + 7 * KG < kmax; k += 8 * KG) {
-      typename VT::V v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = VT::load(P + row + (size_t)(k + KG * u) * ld);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const T f = fs[k + KG * u];
-#pragma unroll
-        for (int i = 0; i < VN; ++i) acc[i] += VT::get(v[u], i) * f;
-      }
-    }
-    for (; k < kmax; k += KG) {
-      typename VT::V v0 = VT::load(P + row + (size_t)k * ld);
-      const T f0 = fs[k];
-#pragma unroll
-      for (int i = 0; i < VN; ++i) acc[i] += VT::get(v0, i) * f0;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < VN; ++i) red[kg * TMV + VN * rg + i] = acc[i];
-  __syncthreads();
-  if (tid < TMV) {
-    const int r = r0 + tid;
-    if (r < r1) {
-      T v = T(0);
-#pragma unroll
-      for (int q = 0; q < KG; ++q) v += red[q * TMV + tid];
-      if (r < w) {
-        Y[first + r] = v;
-      } else {
-        const T g = kmax <= ST - TMV ? gb[tid] : front_rhs<T>(c, B, U, J, r, 0, false);
-        U[c.f.sn_upd[J] + r - w] = g - v;
-      }
-    }
-  }
-}
-
-// Backward tile: vec_cols consecutive panel columns, a warp per column in turn, over one
-// gathered front vector; a lane keeps up to 4 vector loads of its column in flight.
-template <typename T>
-__device__ void vec_bwd_tile(const SweepCtx &c, const T *panel, const T *Y, T *X, int J, int c0,
-                             T *sm) {
-  using VT = Vec<T>;
-  constexpr int VN = VT::N, STEP = 32 * VN;
-  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
-  const int first = c.f.sn_first[J];
-  const int64_t rp = c.f.sn_rowptr[J];
-  const T *P = panel + c.f.sn_panel[J];
-  const int kbeg = c0 & ~(VN - 1);
-  T *g = sm;  // [ld]
-  const int tid = threadIdx.x;
-  for (int kb = kbeg + tid; kb < ld; kb += 3 * ST) {  // indices, then values, in flight
-    int64_t row[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int k = kb + q * ST;
-      row[q] = k < w ? (int64_t)(first + k) : k < m ? (int64_t)c.f.rows[rp + k] : -1;
-    }
-    T v[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int k = kb + q * ST;
-      v[q] = row[q] < 0 ? T(0) : k < w ? __ldcg(&Y[row[q]]) : -__ldcg(&X[row[q]]);
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-      if (kb + q * ST < ld) g[kb + q * ST] = v[q];
-  }
-  __syncthreads();
-  const int lane = tid & 31, wid = tid >> 5;
-  const int c1 = min(c0 + c.p.vec_cols, w);
-  for (int col = c0 + wid; col < c1; col += ST / 32) {  // the gathered g serves every column
-    const T *Pc = P + (size_t)col * ld;
-    const int ks = col & ~(VN - 1);
-    T acc = T(0);
-    int k = ks + VN * lane;
-    for (; k + 3 * STEP < ld; k += 4 * STEP) {
-      typename VT::V v[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = VT::load(Pc + k + u * STEP);
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int i = 0; i < VN; ++i) acc += VT::get(v[u], i) * g[k + u * STEP + i];
-    }
-    for (; k < ld; k += STEP) {
-      typename VT::V v = VT::load(Pc + k);
-#pragma unroll
-      for (int i = 0; i < VN; ++i) acc += VT::get(v, i) * g[k + i];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) X[first + col] = acc;
-  }
-}
-
-// a warp processes one small supernode (m <= 96, w <= 32)
-template <typename T>
-__device__ void vec_fwd_small(const SweepCtx &c, const T *panel, const T *B, T *Y, T *U, int J) {
-  const int lane = threadIdx.x & 31;
-  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
-  const int first = c.f.sn_first[J];
-  const T *P = panel + c.f.sn_panel[J];
-  // f_top entry of row lane (< w) and the update-row gathers of rows lane + 32 q (>= w)
-  int pos[3];
-  T gv[3];
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int r = lane + 32 * q;
-    pos[q] = r < m ? r : -1;
-    gv[q] = (r < w && B) ? B[first + r] : T(0);
-  }
-  gather_rows<T, 3>(c, U, c.f.sn_rowptr[J], pos, gv, 0);
-  const T fk = lane < w ? gv[0] : T(0);
-  T acc[3] = {T(0), T(0), T(0)};
-  for (int k0 = 0; k0 < w; k0 += 8) {  // 8 x 3 independent loads in flight per lane
-    T v[3][8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const int r = lane + 32 * q;
-        v[q][u] = (k0 + u < w && r < m) ? __ldg(&P[r + (size_t)(k0 + u) * ld]) : T(0);
-      }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const T f = __shfl_sync(0xffffffffu, fk, (k0 + u) & 31);
-#pragma unroll
-      for (int q = 0; q < 3; ++q) acc[q] += v[q][u] * f;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const int r = lane + 32 * q;
-    if (r >= m) continue;
-    if (r < w) Y[first + r] = acc[q];
-    else U[c.f.sn_upd[J] + r - w] = gv[q] - acc[q];
-  }
-}
-
-template <typename T>
-__device__ void vec_bwd_small(const SweepCtx &c, const T *panel, const T *Y, T *X, int J,
-                              T *tile /* [32][33] of this warp */) {
-  const int lane = threadIdx.x & 31;
-  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
-  const int first = c.f.sn_first[J];
-  const int64_t rp = c.f.sn_rowptr[J];
-  const T *P = panel + c.f.sn_panel[J];
-  T acc = T(0);
-  for (int kb = 0; kb < m; kb += 32) {
-    const int k = kb + lane;
-    T gk = T(0);
-    if (k < w) gk = __ldcg(&Y[first + k]);
-    else if (k < m) gk = -__ldcg(&X[c.f.rows[rp + k]]);
-    for (int c0 = 0; c0 < w; c0 += 8) {  // 8 independent loads in flight per lane
-      T v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        v[u] = (k < m && c0 + u < w) ? __ldg(&P[k + (size_t)(c0 + u) * ld]) : T(0);
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (c0 + u < w) tile[lane * 33 + c0 + u] = v[u];
-    }
-    __syncwarp();
-    const int kn = min(32, m - kb);
-    for (int kk = 0; kk < kn; ++kk) {
-      const T gv = __shfl_sync(0xffffffffu, gk, kk);
-      if (lane < w) acc += tile[kk * 33 + lane] * gv;
-    }
-    __syncwarp();
-  }
-  if (lane < w) X[first + lane] = acc;
-}
-
-// ---------------------------------------------------------------- block items (s > 1)
-template <int TC, int CM, int RM>
-struct Cfg {
-  static constexpr int TR = ST / TC;
-  static constexpr int TM = TR * RM;
-  static constexpr int NCP = TC * CM;
-};
-
-// acc += As[0:kc, rows of this thread]^T Bs[0:kc, columns of this thread] (unrolled by 4:
-// full unrolling of every chunk made the kernel too large for the instruction cache).
-template <typename T, int TC, int CM, int RM>
-__device__ __forceinline__ void mac_chunk(const T *As, const T *Bs, int tc, int tr, int kc,
-                                          T (&acc)[RM][CM]) {
-  using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP;
-  auto step = [&](int k) {
-    T a[RM], b[CM];
-#pragma unroll
-    for (int i = 0; i < RM; ++i) a[i] = As[k * (TM + 1) + tr * RM + i];
-#pragma unroll
-    for (int j = 0; j < CM; ++j) b[j] = Bs[k * NCP + tc + TC * j];
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-      for (int j = 0; j < CM; ++j) acc[i][j] += a[i] * b[j];
-  };
-#pragma unroll 4
-  for (int k = 0; k < kc; ++k) step(k);
-}
-
-// Staging of one K chunk. In-order issue stalls a thread at the first use of a load, so
-// every staging step first issues all its independent loads into registers and only then
-// writes shared memory: the panel tile (NA values per thread), and the right-hand-side rows
-// of a warp (RB rows x CPW columns per lane; row indices, first gather sources, values in
-// three waves). Sums are formed in the same order as one row at a time would.
-template <typename T, int TM>
-__device__ __forceinline__ void stage_panel_fwd(const T *P, int ld, int m, int r0, int k0, int kc,
-                                                T *As) {
-  constexpr int NA = (TK * TM + ST - 1) / ST;
-  T av[NA];
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    const int i = threadIdx.x + q * ST, r = i % TM, k = i / TM;
-    av[q] = (k < kc && r0 + r < m) ? __ldg(&P[(size_t)(r0 + r) + (size_t)(k0 + k) * ld]) : T(0);
-  }
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    const int i = threadIdx.x + q * ST, r = i % TM, k = i / TM;
-    if (k < kc) As[k * (TM + 1) + r] = av[q];
-  }
-}
-
-template <typename T, int TM>
-__device__ __forceinline__ void stage_panel_bwd(const T *P, int ld, int r0, int r1, int k0, int kc,
-                                                T *As) {
-  constexpr int NA = (TK * TM + ST - 1) / ST;
-  T av[NA];
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    const int i = threadIdx.x + q * ST, k = i % TK, r = i / TK;
-    av[q] = (k < kc && r0 + r < r1) ? __ldg(&P[(size_t)(k0 + k) + (size_t)(r0 + r) * ld]) : T(0);
-  }
-#pragma unroll
-  for (int q = 0; q < NA; ++q) {
-    const int i = threadIdx.x + q * ST, k = i % TK, r = i / TK;
-    if (k < kc) As[k * (TM + 1) + r] = av[q];
-  }
-}
-
-// f rows k0 + [0, kc) of supernode J: b + the children's update rows landing there
-template <typename T, int NCP>
-__device__ __forceinline__ void stage_f(const SweepCtx &c, const T *B, const T *U, int64_t rp,
-                                        int first, int k0, int kc, T *Bs) {
-  constexpr int NW = ST / 32, CPW = (NCP + 31) / 32, RB = CPW >= 8 ? 2 : 24 / CPW;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int s = c.s;
-  for (int kb = wid; kb < kc; kb += NW * RB) {
-    int32_t e0[RB], e1[RB];
-    T v[RB][CPW];
-#pragma unroll
-    for (int q = 0; q < RB; ++q) {
-      const int k = kb + q * NW;
-      const bool on = k < kc;
-      e0[q] = on ? (int32_t)c.f.gptr[rp + k0 + k] : 0;
-      e1[q] = on ? (int32_t)c.f.gptr[rp + k0 + k + 1] : 0;
-#pragma unroll
-      for (int j = 0; j < CPW; ++j) {
-        const int col = lane + 32 * j;
-        v[q][j] = (on && B && col < s) ? B[(size_t)(first + k0 + k) * s + col] : T(0);
-      }
-    }
-    int64_t src[RB];
-#pragma unroll
-    for (int q = 0; q < RB; ++q) src[q] = e0[q] < e1[q] ? c.f.gsrc[e0[q]] : -1;
-#pragma unroll
-    for (int q = 0; q < RB; ++q)
-      if (src[q] >= 0) {
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-          const int col = lane + 32 * j;
-          if (col < s) v[q][j] += __ldcg(&U[(size_t)src[q] * s + col]);
-        }
-      }
-#pragma unroll
-    for (int q = 0; q < RB; ++q)
-      for (int e = e0[q] + 1; e < e1[q]; ++e) {
-        const int64_t sr = c.f.gsrc[e];
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-          const int col = lane + 32 * j;
-          if (col < s) v[q][j] += __ldcg(&U[(size_t)sr * s + col]);
-        }
-      }
-#pragma unroll
-    for (int q = 0; q < RB; ++q) {
-      const int k = kb + q * NW;
-      if (k < kc) {
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-          const int col = lane + 32 * j;
-          if (col < NCP) Bs[k * NCP + col] = v[q][j];
-        }
-      }
-    }
-  }
-}
-
-// g rows k0 + [0, kc) of supernode J for the backward sweep: y of its own rows, -x below
-template <typename T, int NCP>
-__device__ __forceinline__ void stage_g(const SweepCtx &c, const T *Y, const T *X, int64_t rp,
-                                        int first, int w, int k0, int kc, T *Bs) {
-  constexpr int NW = ST / 32, CPW = (NCP + 31) / 32, RB = CPW >= 8 ? 2 : 24 / CPW;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int s = c.s;
-  for (int kb = wid; kb < kc; kb += NW * RB) {
-    int64_t row[RB];
-#pragma unroll
-    for (int q = 0; q < RB; ++q) {
-      const int k = kb + q * NW, kk = k0 + k;
-      row[q] = k >= kc ? -1 : kk < w ? (int64_t)(first + kk) : (int64_t)c.f.rows[rp + kk];
-    }
-    T v[RB][CPW];
-#pragma unroll
-    for (int q = 0; q < RB; ++q) {
-      const int kk = k0 + kb + q * NW;
-      const T *src = kk < w ? Y : X;
-#pragma unroll
-      for (int j = 0; j < CPW; ++j) {
-        const int col = lane + 32 * j;
-        v[q][j] = (row[q] >= 0 && col < s) ? __ldcg(&src[(size_t)row[q] * s + col]) : T(0);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < RB; ++q) {
-      const int k = kb + q * NW;
-      if (k < kc) {
-        const T sg = k0 + k < w ? T(1) : T(-1);
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-          const int col = lane + 32 * j;
-          if (col < NCP) Bs[k * NCP + col] = sg * v[q][j];
-        }
-      }
-    }
-  }
-}
-
-// Forward tile: rows [r0, r0 + TM) of supernode J, all s columns, K = panel columns.
-template <typename T, int TC, int CM, int RM>
-__device__ void blk_fwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *B, T *Y,
-                             T *U, int J, int r0, T *sm) {
-  using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP;
-  static_assert((TM & (TM - 1)) == 0, "tile rows must be a power of two");
-  T *As = sm;                  // [TK][TM + 1]
-  T *Bs = As + TK * (TM + 1);  // [TK][NCP]
-  const int s = c.s;
-  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
-  const int first = c.f.sn_first[J];
-  const int64_t rp = c.f.sn_rowptr[J];
-  const T *P = panel + c.f.sn_panel[J];
-  const int r1 = min(r0 + TM, m);
-  const int kmax = (r1 <= w) ? r1 : w;
-  const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
-  T acc[RM][CM];
-#pragma unroll
-  for (int i = 0; i < RM; ++i)
-#pragma unroll
-    for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
-  for (int k0 = 0; k0 < kmax; k0 += TK) {
-    const int kc = min(TK, kmax - k0);
-    stage_panel_fwd<T, TM>(P, ld, m, r0, k0, kc, As);
-    stage_f<T, NCP>(c, B, U, rp, first, k0, kc, Bs);
-    __syncthreads();
-    if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
-    __syncthreads();
-  }
-  // epilogue: y rows, or update rows u = f_bot - P_bot f_top (gathers of the thread's rows
-  // issued together)
-  const int64_t upd = c.f.sn_upd[J];
-  int32_t e0[RM], e1[RM];
-  int64_t src[RM];
-#pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    const int r = r0 + tr * RM + i;
-    const bool bot = r < r1 && r >= w;
-    e0[i] = bot ? (int32_t)c.f.gptr[rp + r] : 0;
-    e1[i] = bot ? (int32_t)c.f.gptr[rp + r + 1] : 0;
-  }
-#pragma unroll
-  for (int i = 0; i < RM; ++i) src[i] = e0[i] < e1[i] ? c.f.gsrc[e0[i]] : -1;
-#pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    const int r = r0 + tr * RM + i;
-    if (r >= r1) continue;
-    if (r < w) {
-#pragma unroll
-      for (int j = 0; j < CM; ++j) {
-        const int col = tc + TC * j;
-        if (col < s) Y[(size_t)(first + r) * s + col] = acc[i][j];
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < CM; ++j) {
-        const int col = tc + TC * j;
-        if (col < s) {
-          T v = src[i] >= 0 ? __ldcg(&U[(size_t)src[i] * s + col]) : T(0);
-          for (int e = e0[i] + 1; e < e1[i]; ++e) v += __ldcg(&U[(size_t)c.f.gsrc[e] * s + col]);
-          U[(size_t)(upd + r - w) * s + col] = v - acc[i][j];
-        }
-      }
-    }
-  }
-}
-
-// Backward tile: x rows [r0, r0 + TM) of supernode J (rows of its own columns), all s
-// columns, K over the m front positions.
-template <typename T, int TC, int CM, int RM>
-__device__ void blk_bwd_tile(const SweepCtx &c, const T *__restrict__ panel, const T *Y, T *X,
-                             int J, int r0, T *sm) {
-  using C = Cfg<TC, CM, RM>;
-  constexpr int TM = C::TM, NCP = C::NCP;
-  T *As = sm;
-  T *Bs = As + TK * (TM + 1);
-  const int s = c.s;
-  const int w = c.f.sn_w[J], m = c.f.sn_m[J], ld = (m + 3) & ~3;
-  const int first = c.f.sn_first[J];
-  const int64_t rp = c.f.sn_rowptr[J];
-  const T *P = panel + c.f.sn_panel[J];
-  const int r1 = min(r0 + TM, w);
-  const int tid = threadIdx.x, tc = tid % TC, tr = tid / TC;
-  T acc[RM][CM];
-#pragma unroll
-  for (int i = 0; i < RM; ++i)
-#pragma unroll
-    for (int j = 0; j < CM; ++j) acc[i][j] = T(0);
-  for (int k0 = r0; k0 < m; k0 += TK) {
-    const int kc = min(TK, m - k0);
-    stage_panel_bwd<T, TM>(P, ld, r0, r1, k0, kc, As);
-    stage_g<T, NCP>(c, Y, X, rp, first, w, k0, kc, Bs);
-    __syncthreads();
-    if (r0 + tr * RM < r1) mac_chunk<T, TC, CM, RM>(As, Bs, tc, tr, kc, acc);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < RM; ++i) {
-    const int r = r0 + tr * RM + i;
-    if (r >= r1) continue;
-#pragma unroll
-    for (int j = 0; j < CM; ++j) {
-      const int col = tc + TC * j;
-      if (col < s) X[(size_t)(first + r) * s + col] = acc[i][j];
-    }
-  }
-}
-
 // ---------------------------------------------------------------- the persistent sweep
 // item_b >= 0: tile of supernode item_a starting at row/column item_b;
 // item_b < 0 : group of -item_b small supernodes group_sn[item_a ...] (vector mode only).

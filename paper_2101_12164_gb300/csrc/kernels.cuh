@@ -44,6 +44,12 @@ struct SweepPlan {
   const int32_t *sn_parent = nullptr, *need_f = nullptr, *units_f = nullptr, *units_b = nullptr;
   uint32_t *cnt_f = nullptr, *self_f = nullptr, *done_b = nullptr;
   uint32_t *claim = nullptr, *abort_flag = nullptr, *epoch = nullptr, *claim_base = nullptr;
+  // Block-resident schedule (k_rsweep.cu): block b owns heights [res_blk_ptr[b],
+  // res_blk_ptr[b+1]); height L owns supernodes res_job[res_lvl_ptr[L] .. res_lvl_ptr[L+1]),
+  // the first res_lvl_nwarp[L] of them warp-sized (largest first), the rest CTA-sized.
+  int32_t res_nblocks = 0;
+  const int32_t *res_blk_ptr = nullptr, *res_lvl_ptr = nullptr, *res_lvl_nwarp = nullptr,
+                *res_job = nullptr;
 };
 
 // ---- numeric factorization (k_factor.cu) -----------------------------------------
@@ -72,6 +78,12 @@ template <typename T>
 int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y, T *U,
                  T *X, int s, DevStatus *st, cudaStream_t stream, int grid_req = 0,
                  int max_spins = 0);
+// The same solve with one CTA per block of the forest and no cross-CTA dependency (the
+// plan's block-resident schedule), both sweeps of a block in its CTA. Grid = blocks.
+template <typename T>
+void launch_res_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y,
+                      T *U, T *X, int s, DevStatus *st, cudaStream_t stream);
+constexpr int kResW = 32, kResM = 128;   // block mode: supernodes a warp runs (w, m bounds)
 // rows of a forward tile in vector mode for elements of elem_bytes
 int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile

@@ -112,6 +112,37 @@ def test_schur_apply_matches_oracle(N, torch, name, prec, s):
     h.destroy()
 
 
+@pytest.mark.parametrize("sched", ["resident", "global"])
+@pytest.mark.parametrize("name", ["tiny3d", "ragged2d", "cluster3d"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("s", [1, 7, 80, 160])
+def test_both_sweep_schedulers_match_oracle(N, torch, monkeypatch, sched, name, prec, s):
+    # the block-resident sweep (one CTA per block) and the dependency-driven persistent sweep
+    # compute the same A_I^{-1} B and S_Gamma X; each is forced here (the autotuner would
+    # otherwise keep only the faster one)
+    monkeypatch.setenv("NSP_SWEEP", sched)
+    A, part, nsub = _case(name)
+    D = O.DBBD(A, part, nsub)
+    h = N.nsp_build(A, part, nsub, k=4, p=2, precision=prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    cast = (lambda M: M) if prec == "fp64" else (lambda M: M.astype(np.float32).astype(np.float64))
+    tol = 1e-10 if prec == "fp64" else 5e-4
+    B = cast(np.random.default_rng(40 + s).standard_normal((D.n_I, s)))
+    Bd = torch.tensor(B, dtype=dt, device="cuda")
+    Xd = torch.empty_like(Bd)
+    h.factor_solve(0, Bd, Xd)
+    X = cast(np.random.default_rng(50 + s).standard_normal((D.n_G, s)))
+    Xg = torch.tensor(X, dtype=dt, device="cuda")
+    Yg = torch.empty_like(Xg)
+    h.schur_apply(Xg, Yg)
+    torch.cuda.synchronize()
+    err = colwise_err(Xd.double().cpu().numpy().reshape(D.n_I, s), D.solve_I(B))
+    assert err < tol, err
+    err = colwise_err(Yg.double().cpu().numpy().reshape(D.n_G, s), D.apply_S_gamma(X))
+    assert err < (1e-9 if prec == "fp64" else 1e-3), err
+    h.destroy()
+
+
 def test_gaussian_sketch_matches_oracle_generator(N, torch):
     n = 100003
     out = torch.empty(n, dtype=torch.float64, device="cuda")
