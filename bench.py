@@ -1,19 +1,31 @@
 """Benchmark of the Nyström–Schur preconditioner hot path on one GB300 (per rank).
 
-Workload (default): 3D 7-point heterogeneous diffusion on a 64^3 grid (n = 262,144),
-lognormal coefficient (correlation length 8 cells, sigma = 2), 32 subdomains by recursive
-coordinate bisection, k = 64, p = 16, FP32 inner solves / FP64 Nyström core and outer PCG,
-outer PCG to a relative residual of 1e-8 with b = A x*, x* ~ N(0, 1).
+Workload (default, --config 4): 3D 7-point anisotropic diffusion on a 128^3 grid
+(n = 2,097,152), axis scales (1, 1, 1e-3), lognormal coefficient (sigma = 1.5, correlation
+length 8 cells), 256 subdomains by recursive coordinate bisection, k = 128, p = 32 (block CG
+with 160 right-hand sides), FP32 factors and inner solves / FP64 Nyström core and outer PCG,
+outer PCG to a relative residual of 1e-8 with b = A x*, x* ~ N(0, 1). --config 1 runs the
+64^3 lognormal workload (32 subdomains, k = 64, p = 16) the same way, --config 2 the
+64-matrix batch.
 
 One step = numeric rebuild of the preconditioner (device factorization of every interior
 block and of A_G, sketch, inner block PCG, Nyström core, Z) + the outer PCG solve, with A's
 values and b resident in device memory. The host symbolic analysis of A's pattern is done
-once per pattern and reported separately (analyze_ms). e2e repeats the step through the same
-public calls from pinned host buffers (values and b in, x out).
+once per pattern and reported separately (analyze_ms; with_analysis_ms in e2e includes it).
+e2e repeats the step through the same public calls from pinned host buffers (values and b
+in, x out).
 
---impl reference times the FP64 CPU oracle (the program that defines correctness), on a
-bounded sample per step, extrapolated to one full solve with the iteration counts the
-oracle itself measures once.
+Errors against the FP64 oracle are stated from tests/golden/<workload>.json (written by
+tests/golden/make_golden.py, which calls only the oracle) with the same sketch and
+right-hand side: the Nyström term Z Sigma Z^T and Sigma, the condition estimate of M2 S_Gamma
+from the outer PCG's Lanczos coefficients, and the solution.
+
+cpu_baseline / --impl reference time the FP64 CPU oracle (the program that defines
+correctness) on a bounded sample of the same workload on this host, single-threaded: the
+sparse factorization and the 160-column and single-column solves of a subset of the
+interior blocks, scaled to all blocks and to the oracle's own iteration counts. The
+interface (A_G) work of the oracle is not in the sample, so the value is a lower bound of
+the oracle's build + solve time.
 """
 
 import argparse
@@ -24,6 +36,10 @@ import subprocess
 import sys
 import threading
 import time
+
+# the oracle legs are reported single-threaded: keep BLAS to one thread (GPU work unaffected)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np
 
@@ -40,12 +56,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="nsp", choices=["nsp", "reference"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--config", type=int, default=4)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--variant", default="m2", choices=["m2", "m2_adef"],
                     help="preconditioner of the timed step (§4.3: M2 or M_2A-DEF)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--apply-reps", type=int, default=20)
+    ap.add_argument("--variants", action="store_true",
+                    help="also time q = 1, the S_I inner form, M3 and M_3A-DEF on the workload")
+    ap.add_argument("--sample-blocks", type=int, default=64,
+                    help="interior blocks in the oracle's timed CPU sample")
     ap.add_argument("--profile", action="store_true",
                     help="one warm-up step, then one step inside the NVTX range 'timed_step' "
                          "and one S_Gamma block apply inside 'schur_apply'; no timing output")
@@ -162,35 +182,73 @@ def sub_nnz(P):
 
 
 # --------------------------------------------------------------------------- oracle arm
-def oracle_sample(P, G, b, counts=None):
-    """Time the oracle on a bounded sample and extrapolate to one full solve.
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
-    Sample: DBBD split + sparse factorizations, one block S_Gamma apply (s columns), one
-    A_G solve with s columns, one single-vector S_Gamma apply and M2 apply. A full solve is
-    factor + (1 + it_inner) block applies + it_inner A_G solves + it_pcg (apply + M2).
-    """
+
+def golden_for(P):
+    path = os.path.join(GOLDEN, "%s.json" % P.name)
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        return json.load(f)
+
+
+def oracle_counts(P, G, b):
+    """The oracle's own (it_inner, it_pcg) with sketch G: stored for the 128^3 workload,
+    computed by one oracle run otherwise (returns the run's wall time too)."""
+    gold = golden_for(P)
+    if gold is not None:
+        return (gold["build"]["it_inner"], gold["solve"]["it_pcg"]), None
     import oracle as O
     t0 = time.perf_counter()
     D = O.DBBD(P.A, P.part, P.nsub)
-    t_fact = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    D.apply_S_gamma(G)
-    t_block = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    D.solve_G(G)
-    t_gsolve = time.perf_counter() - t0
-    v = G[:, 0].copy()
-    t0 = time.perf_counter()
-    D.apply_S_gamma(v)
-    D.solve_G(v)
-    t_single = time.perf_counter() - t0
-    if counts is None:
-        M, info = O.build_m2(D, G, P.k, P.eps_inner)
-        _, it_pcg, _ = O.solve(D, M.apply, b, rtol=P.rtol)
-        counts = (info["it_inner"], it_pcg)
+    M, info = O.build_m2(D, G, P.k, P.eps_inner)
+    _, it_pcg, _ = O.solve(D, M.apply, b, rtol=P.rtol)
+    return (info["it_inner"], it_pcg), time.perf_counter() - t0
+
+
+def oracle_sample(P, counts, nsample):
+    """Time the FP64 oracle (single thread) on a bounded sample of the workload: SuperLU
+    factorization, one s-column solve and one single-column solve of `nsample` interior
+    blocks spread over the subdomains. Scaled to all blocks and to the oracle's counts: the
+    interior work of one build + solve is factorizing every block, 1 + it_inner s-column
+    solves (the inner right-hand side and one S_Gamma apply per block-PCG iteration) and
+    it_pcg + 2 single-column solves (f, one S_Gamma apply per outer iteration, x_I). The
+    A_Gamma factorization and solves are left out: a lower bound of the oracle's time."""
+    from oracle import nsp_oracle as NO
+    A = P.A.tocsr()
+    part = P.part
+    blocks = np.unique(np.linspace(0, P.nsub - 1, min(nsample, P.nsub)).astype(int))
+    rng = np.random.default_rng(0)
+    t_fact = t_block = t_vec = 0.0
+    t_start = time.perf_counter()
+    for blk in blocks:
+        idx = np.nonzero(part == blk)[0]
+        Ab = A[idx][:, idx]
+        t0 = time.perf_counter()
+        lu = NO._lu(Ab)
+        t_fact += time.perf_counter() - t0
+        B = rng.standard_normal((len(idx), P.s))
+        t0 = time.perf_counter()
+        lu.solve(B)
+        t_block += time.perf_counter() - t0
+        v = np.ascontiguousarray(B[:, 0])
+        t0 = time.perf_counter()
+        lu.solve(v)
+        t_vec += time.perf_counter() - t0
+    sample_s = time.perf_counter() - t_start
+    scale = P.nsub / len(blocks)
     it_inner, it_pcg = counts
-    total = t_fact + (1 + it_inner) * t_block + it_inner * t_gsolve + it_pcg * t_single
-    return total * 1e3, counts
+    phases = {"factor_ms": 1e3 * scale * t_fact,
+              "inner_solves_ms": 1e3 * scale * (1 + it_inner) * t_block,
+              "outer_solves_ms": 1e3 * scale * (it_pcg + 2) * t_vec}
+    total = sum(phases.values())
+    desc = ("FP64 oracle (SciPy SuperLU, one thread) on %d of the %d interior blocks: "
+            "factorization, one %d-column and one single-column solve each (%.1f s on this "
+            "host), scaled to all blocks and to the oracle's counts it_inner=%d, it_pcg=%d; "
+            "the A_Gamma work is not in the sample, so this is a lower bound of the oracle's "
+            "build + solve" % (len(blocks), P.nsub, P.s, sample_s, it_inner, it_pcg))
+    return total, phases, sample_s, desc
 
 
 def cpu_cores():
@@ -204,34 +262,37 @@ def run_reference(args, P, G, b):
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    counts = None
+    counts, _ = oracle_counts(P, G, b)
     for _ in range(max(args.warmup, 0)):
-        _, counts = oracle_sample(P, G, b, counts)
-    if counts is None:
-        _, counts = oracle_sample(P, G, b, None)
-    times = []
+        oracle_sample(P, counts, max(4, args.sample_blocks // 4))
+    vals, samples = [], []
     for _ in range(args.steps):
-        ms, counts = oracle_sample(P, G, b, counts)
-        times.append(ms)
-    ms = float(np.mean(times))
-    sample = ("per step: oracle DBBD + SuperLU factorizations, one %d-column S_Gamma apply, "
-              "one A_G solve, one single-vector S_Gamma + M2 apply; extrapolated with the "
-              "oracle's own counts it_inner=%d, it_pcg=%d" % (P.s, counts[0], counts[1]))
+        ms, phases, sample_s, desc = oracle_sample(P, counts, args.sample_blocks)
+        vals.append(ms)
+        samples.append(sample_s)
+    ms = float(np.mean(vals))
     return {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(P, args),
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-                             "sample": sample},
+            "timed_sample_s_per_step": float(np.mean(samples)),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle",
+                             "sample": desc, "phases": phases, "lower_bound": True},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
 
+WORKLOADS = {
+    4: "aniso3d_128: 3D 7-point anisotropic diffusion 128^3 (n=2097152), axis scales "
+       "(1, 1, 1e-3), lognormal a (ell=8, sigma=1.5), 256 subdomains, k=128, p=32",
+    1: "lognormal3d_64: 3D 7-point diffusion 64^3 (n=262144), lognormal a (ell=8, sigma=2), "
+       "32 subdomains, k=64, p=16",
+}
+
+
 def workload_config(P, args):
-    return {"workload": "lognormal3d_64: 3D 7-point diffusion 64^3 (n=262144), lognormal a "
-                        "(ell=8, sigma=2), 32 subdomains, k=64, p=16" if args.config == 1
-                        else P.name,
+    return {"workload": WORKLOADS.get(args.config, P.name),
             "n": int(P.n), "n_gamma": int(P.n_gamma), "subdomains": int(P.nsub),
             "k": int(P.k), "p": int(P.p), "eps_inner": P.eps_inner, "rtol": P.rtol,
             "precision": args.precision, "parallelism": "replicas%d" % args.gpus,
@@ -239,6 +300,76 @@ def workload_config(P, args):
 
 
 # --------------------------------------------------------------------------- nsp arm
+def time_events(stream, fn, reps):
+    """Mean device time (ms) of fn() over reps calls, CUDA events on `stream`."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(reps):
+        fn()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    return a0.elapsed_time(a1) / reps
+
+
+def oracle_errors(N, torch, P, args, dev, b):
+    """Build + solve with the stored oracle run's sketch and right-hand side; errors against
+    the FP64 oracle (sampled rows of tests/golden/<workload>.json)."""
+    gold = golden_for(P)
+    if gold is None:
+        return None
+    G = F_make_sketch(P, args.config)
+    x_star, _ = F_make_rhs(P, args.config)
+    h = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                    precision=args.precision, sketch=G)
+    bd = torch.tensor(b, dtype=torch.float64, device=dev)
+    xd = torch.zeros_like(bd)
+    inf = h.solve(bd, xd, rtol=P.rtol, maxit=500)
+    x = xd.cpu().numpy()
+    Z, S = h.get_basis()
+    h.destroy()
+
+    def sampled(full, block, rows):
+        full = np.asarray(full, dtype=np.float64).reshape(full.shape[0], -1)
+        ref = np.asarray(block["values"], dtype=np.float64)
+        scale = np.asarray(block["colmax"], dtype=np.float64)
+        return float((np.abs(full[rows] - ref).max(axis=0) / scale).max())
+
+    import fixtures as F
+    V = F.make_probe(gold["n_gamma"], 4, args.config, 2)
+    g = gold["build"]
+    r = min(len(S), len(g["sigma"]))
+    xs = gold["solve"]
+    return {
+        "reference": "FP64 oracle, same sketch and right-hand side (tests/golden/%s.json, "
+                     "%d sampled rows per output)" % (P.name, gold["nsample"]),
+        "it_inner": [int(inf["it_inner"]), int(g["it_inner"])],
+        "it_pcg": [int(inf["it_pcg"]), int(xs["it_pcg"])],
+        "nystrom_term_err": sampled((Z * S) @ (Z.T @ V), g["nystrom_term"], gold["rows_gamma"]),
+        "sigma_rel_err": float(np.max(np.abs(S[:r] - np.asarray(g["sigma"][:r]))
+                                      / np.asarray(g["sigma"][:r]))),
+        "kappa": [float(inf["kappa_est"]), float(xs["kappa"])],
+        "kappa_rel_err": abs(inf["kappa_est"] - xs["kappa"]) / xs["kappa"],
+        "solution_err": sampled(x, xs["x"], gold["rows_full"]),
+        "x_err_vs_xstar": [float(np.linalg.norm(x - x_star) / np.linalg.norm(x_star)),
+                           float(xs["err_vs_xstar"])],
+        "final_residual": [float(np.linalg.norm(b - P.A @ x) / np.linalg.norm(b)),
+                           float(xs["residual"])],
+    }
+
+
+def F_make_sketch(P, config):
+    import fixtures as F
+    return F.make_sketch(P.n_gamma, P.s, config, 0)
+
+
+def F_make_rhs(P, config):
+    import fixtures as F
+    return F.make_rhs(P, config, 0)
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
@@ -246,8 +377,8 @@ def main():
     if args.config == 2 and args.impl != "reference":
         return main_batched(args, F, world, rank, local)
     P = F.make_problem(args.config, 0)
-    G = F.make_sketch(P.n_gamma, P.s, args.config, rank)
-    _, b = F.make_rhs(P, args.config, rank)
+    G = F.make_sketch(P.n_gamma, P.s, args.config, 0)
+    _, b = F.make_rhs(P, args.config, 0)
 
     if args.impl == "reference":
         if world > 1 and rank != 0:
@@ -293,23 +424,6 @@ def main():
         step()
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
-        X = torch.randn(P.n_gamma, P.s, device=dev,
-                        dtype=torch.float32 if args.precision == "fp32" else torch.float64)
-        Y = torch.empty_like(X)
-        h.schur_apply(X, Y)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("schur_apply")
-        h.schur_apply(X, Y)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-        Bi = torch.randn(info0["n_interior"], P.s, device=dev, dtype=X.dtype)
-        Xi = torch.empty_like(Bi)
-        h.factor_solve(0, Bi, Xi)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_push("interior_sweep")
-        h.factor_solve(0, Bi, Xi)
-        torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
         h.destroy()
         return
 
@@ -345,32 +459,34 @@ def main():
     wbytes = 4 if args.precision == "fp32" else 8
     X = torch.randn(P.n_gamma, s, dtype=dt, device=dev)
     Y = torch.empty_like(X)
-    h.schur_apply(X, Y)
-    torch.cuda.synchronize()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(args.apply_reps):
-        h.schur_apply(X, Y)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    apply_ms = a0.elapsed_time(a1) / args.apply_reps
+    apply_ms = time_events(stream, lambda: h.schur_apply(X, Y), args.apply_reps)
     nbytes = schur_apply_bytes(info0, s, wbytes, sub_nnz(P))
     hbm, peak_kind = peaks()
     achieved = nbytes / (apply_ms * 1e-3) / 1e9
     flops = 4.0 * info0["nnz_L_interior"] * s
-    # dominant kernel of the apply: the persistent interior sweep A_I^{-1} (n_I x s), alone
+    # dominant kernel of the apply: the interior sweep A_I^{-1} (n_I x s), alone
     Bi = torch.randn(info0["n_interior"], s, dtype=dt, device=dev)
     Xi = torch.empty_like(Bi)
-    h.factor_solve(0, Bi, Xi)
-    torch.cuda.synchronize()
-    a0.record(stream)
-    for _ in range(args.apply_reps):
-        h.factor_solve(0, Bi, Xi)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    sweep_ms = a0.elapsed_time(a1) / args.apply_reps
+    sweep_ms = time_events(stream, lambda: h.factor_solve(0, Bi, Xi), args.apply_reps)
     sweep_bytes = sweep_algorithmic_bytes(info0, s, wbytes)
     sweep_gbs = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+    del Bi, Xi
+    # the block-CG Gram X^T Y (n_Gamma x s, FP32) on the tensor cores, alone
+    gram = None
+    if args.precision == "fp32":
+        Yg = torch.randn(P.n_gamma, s, dtype=torch.float32, device=dev)
+        Cg = torch.empty(s, s, dtype=torch.float64, device=dev)
+        nbw = N.lib().nsp_gram_work_bytes(P.n_gamma, s, s)
+        Wg = torch.empty(nbw, dtype=torch.uint8, device=dev)
+        g_ms = time_events(stream, lambda: N.lib().nsp_gram(
+            X.data_ptr(), Yg.data_ptr(), P.n_gamma, s, s, Cg.data_ptr(), Wg.data_ptr(),
+            stream.cuda_stream), args.apply_reps)
+        gbytes = 2 * P.n_gamma * s * 4
+        gram = {"ms": g_ms, "GBps": gbytes / (g_ms * 1e-3) / 1e9,
+                "frac_hbm": gbytes / (g_ms * 1e-3) / 1e9 / hbm,
+                "tflops": 2.0 * P.n_gamma * s * s / (g_ms * 1e-3) / 1e12,
+                "what": "X^T Y, n_Gamma x %d FP32, tcgen05 3xTF32 (three MMAs per product)" % s}
+        del Yg, Cg, Wg
 
     # ---- e2e: same step through the public calls from pinned host buffers
     val_h = torch.tensor(P.A.data, dtype=torch.float64).pin_memory()
@@ -394,11 +510,14 @@ def main():
     torch.cuda.synchronize()
     full_ms = (time.perf_counter() - t0) * 1e3
     h2.destroy()
+    h.destroy()
 
-    # ---- the other preconditioners of §4.3 (M2 / M_2A-DEF, M3, M_3A-DEF), one power
-    # iteration (§2.1 eq. (power)) and the S_I inner form (Algorithm 2 step 3 as printed) on
-    # the same workload, device-timed like the step
-    def time_variant(**kw):
+    errors = oracle_errors(N, torch, P, args, dev, b)
+
+    # ---- other forms of the step on the same workload, device-timed like the step
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def time_variant(steps=2, **kw):
         kw.setdefault("precision", args.precision)
         h3 = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
                          seed=seed, **kw)
@@ -407,11 +526,10 @@ def main():
             h3.rebuild(val_d, on_device=True)
             return h3.solve(b_d, x_d, rtol=P.rtol, maxit=500)
 
-        for _ in range(2):
-            step3()
+        step3()
         torch.cuda.synchronize()
         v_ms, v_infos = [], []
-        for i in range(args.steps):
+        for i in range(steps):
             flush.fill_(float(i))
             a0.record(stream)
             v_infos.append(step3())
@@ -427,25 +545,65 @@ def main():
                               "core": last["ms_core"], "solve": last["ms_solve"]})
 
     variant_line = time_variant(variant="m2_adef" if args.variant == "m2" else "m2")
-    power_line = time_variant(variant=args.variant, q=1)
-    si_line = time_variant(variant=args.variant, inner_form="s_i")
-    m3_lines = [time_variant(variant=v) for v in ("m3", "m3_adef")]
     # the plain FP64 GPU form (FP64 factors, inner block PCG and sweeps) of the timed step
     fp64_line = time_variant(variant=args.variant, precision="fp64")
+    extra = {}
+    if args.variants:
+        extra["power_q1"] = time_variant(variant=args.variant, q=1)
+        extra["inner_s_i"] = time_variant(variant=args.variant, inner_form="s_i")
+        extra["variants_m3"] = [time_variant(variant=v) for v in ("m3", "m3_adef")]
+
+    # ---- the 64^3 workload beside the 128^3 one (same step, fewer and smaller blocks)
+    second = None
+    if args.config == 4:
+        P1 = F.make_problem(1, 0)
+        _, b1 = F.make_rhs(P1, 1, 0)
+        v1 = torch.tensor(P1.A.data, dtype=torch.float64, device=dev)
+        b1d = torch.tensor(b1, dtype=torch.float64, device=dev)
+        x1d = torch.zeros_like(b1d)
+        h1 = N.nsp_build(P1.A, P1.part, P1.nsub, k=P1.k, p=P1.p, eps_inner=P1.eps_inner,
+                         precision=args.precision, seed=seed)
+        i1 = h1.info()
+
+        def step1():
+            h1.rebuild(v1, on_device=True)
+            return h1.solve(b1d, x1d, rtol=P1.rtol, maxit=500)
+
+        for _ in range(2):
+            step1()
+        torch.cuda.synchronize()
+        t1 = []
+        for i in range(3):
+            flush.fill_(float(i))
+            a0.record(stream)
+            l1 = step1()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t1.append(a0.elapsed_time(a1))
+        B1 = torch.randn(i1["n_interior"], P1.s, dtype=dt, device=dev)
+        X1 = torch.empty_like(B1)
+        sw1 = time_events(stream, lambda: h1.factor_solve(0, B1, X1), args.apply_reps)
+        sb1 = sweep_algorithmic_bytes(i1, P1.s, wbytes)
+        second = {"workload": WORKLOADS[1], "ms_per_step": float(np.mean(t1)),
+                  "it_inner": l1["it_inner"], "it_pcg": l1["it_pcg"],
+                  "final_residual": float(np.linalg.norm(b1 - P1.A @ x1d.cpu().numpy())
+                                          / np.linalg.norm(b1)),
+                  "phase_ms": {"factor": l1["ms_factor"], "inner": l1["ms_inner"],
+                               "core": l1["ms_core"], "solve": l1["ms_solve"]},
+                  "sweep_ms": sw1, "sweep_frac_hbm": sb1 / (sw1 * 1e-3) / 1e9 / hbm}
+        h1.destroy()
 
     out = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            t0 = time.perf_counter()
-            o_ms, counts = oracle_sample(P, G, b, None)
-            cpu = {"value": o_ms, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
-                   "sample": "one oracle DBBD + SuperLU factorization, one %d-column "
-                             "S_Gamma apply, one A_G solve, one single-vector S_Gamma + M2 "
-                             "apply, extrapolated with the oracle's own iteration counts "
-                             "(it_inner=%d, it_pcg=%d, from one full oracle run)"
-                             % (s, counts[0], counts[1]),
-                   "wall_s": time.perf_counter() - t0}
+            counts, full_s = oracle_counts(P, G, b)
+            o_ms, phases, sample_s, desc = oracle_sample(P, counts, args.sample_blocks)
+            cpu = {"value": o_ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc,
+                   "phases": phases, "lower_bound": True, "sample_s": sample_s}
+            gold = golden_for(P)
+            if gold is not None:
+                cpu["oracle_full_run_s_elsewhere"] = gold["oracle_seconds"]
         last = infos[-1]
         out = {
             "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": world,
@@ -457,6 +615,7 @@ def main():
                            analyze_ms=info0["ms_analyze"], first_build_ms=build_first_ms,
                            it_inner=last["it_inner"], it_pcg=last["it_pcg"],
                            rank=last["rank"], final_residual=res,
+                           kappa_est=last["kappa_est"],
                            nnz_L_interior=info0["nnz_L_interior"],
                            nnz_L_gamma=info0["nnz_L_gamma"],
                            step_ms_min=float(np.min(step_ms)),
@@ -464,7 +623,7 @@ def main():
                                      "core": last["ms_core"], "solve": last["ms_solve"]}),
             "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": sweep_gbs / hbm, "traffic": SWEEP_TRAFFIC.get((args.config, s)),
-                         "kernel": "k_sweep (s=%d, %s): persistent forward+backward supernodal "
+                         "kernel": "interior sweep (s=%d, %s): forward+backward supernodal "
                                    "sweep of every interior block, the dominant kernel of the "
                                    "S_Gamma block apply" % (s, args.precision),
                          "launch_ms": sweep_ms, "algorithmic_bytes": sweep_bytes,
@@ -474,11 +633,11 @@ def main():
                             "apply_ms": apply_ms, "algorithmic_bytes": nbytes,
                             "what": "S_Gamma X: A_IG SpMM + interior sweep + A_G/A_GI SpMM "
                                     "(s=%d, %s)" % (s, args.precision)},
+            "gram": gram,
+            "errors_vs_oracle": errors,
             "other_variant": variant_line,
-            "power_q1": power_line,
-            "inner_s_i": si_line,
-            "variants_m3": m3_lines,
             "plain_fp64": fp64_line,
+            "second_workload": second,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),
@@ -486,8 +645,8 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clocks.summary(),
         }
+        out.update(extra)
         print(json.dumps(out))
-    h.destroy()
     if pg:
         pg.barrier()
         pg.destroy_process_group()
@@ -580,20 +739,25 @@ def main_batched(args, F, world, rank, local):
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            # oracle on the first matrices for a bounded time, scaled by unknowns
+            # the oracle's full build + solve on the first matrices for a bounded time (a
+            # timed run, one thread), scaled by unknowns
+            import oracle as O
             t_start = time.perf_counter()
-            done_ms, done_n = 0.0, 0
+            done_s, done_n = 0.0, 0
             for m, Pm in enumerate(probs):
                 if time.perf_counter() - t_start > 20.0:
                     break
                 Gm = F.make_sketch(Pm.n_gamma, Pm.s, 2, m)
-                o_ms, _ = oracle_sample(Pm, Gm, bs[m], None)
-                done_ms += o_ms
+                t0 = time.perf_counter()
+                D = O.DBBD(Pm.A, Pm.part, Pm.nsub)
+                M, _ = O.build_m2(D, Gm, Pm.k, Pm.eps_inner)
+                O.solve(D, M.apply, bs[m], rtol=Pm.rtol)
+                done_s += time.perf_counter() - t0
                 done_n += Pm.n
-            cpu = {"value": done_ms * n_tot / done_n, "unit": "ms", "cores": cpu_cores(),
+            cpu = {"value": 1e3 * done_s * n_tot / done_n, "unit": "ms", "cores": 1,
                    "kind": "oracle",
-                   "sample": "oracle (sample-extrapolated per matrix) on the first matrices "
-                             "for ~20 s (%d unknowns), scaled to the batch's %d unknowns"
+                   "sample": "FP64 oracle build + solve of the first matrices for ~20 s "
+                             "(%d unknowns, one thread), scaled to the batch's %d unknowns"
                              % (done_n, n_tot)}
         last = infos[-1]
         its = [i["it_pcg"] for i in last]

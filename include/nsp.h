@@ -379,6 +379,27 @@ const char *nsp_status_string(nsp_status s);
  * Used to count the device launches of a timed region. */
 int64_t nsp_kernel_launches(void);
 
+/* ---- Dense products of the inner block PCG (standalone, for tests and measurements) -----
+ * The block-CG iteration (§5.1: breakdown-free block PCG) needs, besides the S_Gamma block
+ * apply, s x s inner products of n x s blocks and tall updates of such blocks. The handle
+ * runs them internally with the kernels these two calls expose: FP32 data on the tcgen05
+ * tensor cores, each operand split into two TF32 parts (three MMAs per product, FP32-level
+ * accuracy, FP32 accumulation in tensor memory; Gram partials of row chunks added in FP64
+ * in a fixed order). Row-major device arrays; s1, s2 in [1, 256]; work is a device buffer of
+ * at least the queried size that the call uses as scratch (its last 8 bytes receive a
+ * device status word: nonzero if a bounded wait of the kernel ran out, which never happens
+ * on a working GPU). Asynchronous on `stream` (cudaStream_t, NULL = default stream).
+ *   nsp_gram         : C (s1 x s2, doubles) = X^T Y, X n x s1, Y n x s2 (floats).
+ *   nsp_block_update : Out (n x s2) = scale * A M + beta * Cin, A n x s1 (floats), M s1 x s2
+ *                      (doubles), Cin n x s2 or NULL (may alias Out).                       */
+int64_t nsp_gram_work_bytes(int64_t n, int32_t s1, int32_t s2);
+nsp_status nsp_gram(const float *X, const float *Y, int64_t n, int32_t s1, int32_t s2,
+                    double *C, void *work, void *stream);
+int64_t nsp_block_update_work_bytes(int32_t s1, int32_t s2);
+nsp_status nsp_block_update(const float *A, const double *M, int64_t n, int32_t s1, int32_t s2,
+                            float scale, const float *Cin, float beta, float *Out, void *work,
+                            void *stream);
+
 /* Philox4x32-10 (Salmon et al., SC'11) + Box-Muller normals, as used for the sketch:
  * out[i] for i in [0, count), stream defined by seed; out is a device pointer. */
 nsp_status nsp_gaussian(uint64_t seed, int64_t count, double *out, void *stream);

@@ -29,7 +29,8 @@ EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_s
            "nsp_analyze", "nsp_kernel_launches", "nsp_schur_apply_noalloc", "nsp_build_batched",
            "nsp_solve_batched", "nsp_net_num_params", "nsp_net_create", "nsp_net_set_params",
            "nsp_net_get", "nsp_net_forward", "nsp_net_loss_grad", "nsp_net_zero_grad",
-           "nsp_net_adam_step", "nsp_net_sketch", "nsp_net_destroy", "nsp_check_timeout_path"]
+           "nsp_net_adam_step", "nsp_net_sketch", "nsp_net_destroy", "nsp_check_timeout_path",
+           "nsp_gram_work_bytes", "nsp_gram", "nsp_block_update_work_bytes", "nsp_block_update"]
 
 
 class NspError(RuntimeError):
@@ -126,6 +127,11 @@ def lib():
             "nsp_net_sketch": (C.c_int, [P, P, C.c_int64, P, C.POINTER(C.c_int32)]),
             "nsp_net_destroy": (C.c_int, [P]),
             "nsp_check_timeout_path": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32)]),
+            "nsp_gram_work_bytes": (C.c_int64, [C.c_int64, C.c_int32, C.c_int32]),
+            "nsp_gram": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
+            "nsp_block_update_work_bytes": (C.c_int64, [C.c_int32, C.c_int32]),
+            "nsp_block_update": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, C.c_float, P,
+                                           C.c_float, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -356,6 +362,51 @@ def nsp_analyze(A, part, nblocks, perm=None):
 
 def nsp_kernel_launches():
     return int(lib().nsp_kernel_launches())
+
+
+def _status_word(work, nbytes):
+    """The device status word the dense-product calls leave in the last 8 bytes of work."""
+    import torch
+    w = work.view(torch.uint8)[nbytes - 256:nbytes - 248].cpu()
+    return int(w.view(torch.int32)[0])
+
+
+def nsp_gram(X, Y, C, work=None):
+    """C = X^T Y on the tensor cores (X n x s1, Y n x s2 float32 CUDA tensors, C s1 x s2
+    float64). Synchronizes and checks the kernel's status word."""
+    import torch
+    n, s1 = X.shape
+    s2 = Y.shape[1]
+    nb = lib().nsp_gram_work_bytes(n, s1, s2)
+    if nb < 0:
+        raise NspError(1, "nsp_gram_work_bytes")
+    if work is None or work.numel() * work.element_size() < nb:
+        work = torch.empty(nb, dtype=torch.uint8, device=X.device)
+    _check(lib().nsp_gram(_ptr(X), _ptr(Y), n, s1, s2, _ptr(C), _ptr(work), _stream()), "nsp_gram")
+    torch.cuda.synchronize()
+    if _status_word(work, nb) != 0:
+        raise NspError(6, "nsp_gram: a bounded device wait ran out")
+    return C
+
+
+def nsp_block_update(A, M, Out, scale=1.0, Cin=None, beta=0.0, work=None):
+    """Out = scale * A M + beta * Cin on the tensor cores (A n x s1 float32, M s1 x s2
+    float64, Out / Cin n x s2 float32 CUDA tensors). Synchronizes and checks the status."""
+    import torch
+    n, s1 = A.shape
+    s2 = M.shape[1]
+    nb = lib().nsp_block_update_work_bytes(s1, s2)
+    if nb < 0:
+        raise NspError(1, "nsp_block_update_work_bytes")
+    if work is None or work.numel() * work.element_size() < nb:
+        work = torch.empty(nb, dtype=torch.uint8, device=A.device)
+    _check(lib().nsp_block_update(_ptr(A), _ptr(M), n, s1, s2, scale,
+                                  _ptr(Cin) if Cin is not None else None, beta, _ptr(Out),
+                                  _ptr(work), _stream()), "nsp_block_update")
+    torch.cuda.synchronize()
+    if _status_word(work, nb) != 0:
+        raise NspError(6, "nsp_block_update: a bounded device wait ran out")
+    return Out
 
 
 def nsp_gaussian(seed, count, out):

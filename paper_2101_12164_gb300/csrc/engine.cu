@@ -890,11 +890,44 @@ struct Engine : EngineBase {
     launch_scatter_rows<T, T>(i2u_G.p, an.nG, yi, (T *)Yv, sc, st);
   }
 
-  void gram(const T *X, const T *Yv, int s1, int s2, double *C) {
-    launch_gram<T, T>(X, Yv, an.nG, s1, s2, C, gram_work.p, st);
+  void gram(const T *X, const T *Yv, int s1, int s2, double *C) { gram_n(X, Yv, an.nG, s1, s2, C); }
+  // X^T Y (n rows): FP32 on the tensor cores (3xTF32), FP64 on the SIMT pipes
+  // every Gram sizes the chunk partials for its own (n, s1, s2): the SIMT kernel splits the
+  // rows into more chunks when the output is a single tile
+  void gram_n(const T *X, const T *Yv, int64_t n, int s1, int s2, double *C) {
+    gram_work.ensure(gram_work_size(n, s1, s2));
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc_enabled()) {
+        launch_tc_gram(X, Yv, n, s1, s2, C, gram_work.p, dstat.p, st);
+        return;
+      }
+    }
+    launch_gram<T, T>(X, Yv, n, s1, s2, C, gram_work.p, st);
+  }
+  // Out = scale A M + beta C (A n x s1, M s1 x s2 FP64)
+  DBuf<float> tc_mt;
+  void block_update(const T *A, const double *M, int64_t n, int s1, int s2, T scale, const T *C,
+                    T beta, T *Out) {
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc_enabled()) {
+        tc_mt.ensure(tc_update_work_floats(256, 256));
+        launch_tc_block_update(A, M, n, s1, s2, scale, C, beta, Out, tc_mt.p, dstat.p, st);
+        return;
+      }
+    }
+    launch_block_update<T>(A, M, n, s1, s2, scale, C, beta, Out, st);
+  }
+  // NSP_TC=0 keeps the FP32 Grams and block updates on the SIMT pipes (measurements)
+  static bool tc_enabled() {
+    const char *e = std::getenv("NSP_TC");
+    return !(e && e[0] == '0');
   }
   void gram_acc64(const T *X, const T *Yv, int s1, int s2, double *C) {
-    launch_gram<T, double>(X, Yv, an.nG, s1, s2, C, gram_work.p, st);
+    gram_acc64_n(X, Yv, an.nG, s1, s2, C);
+  }
+  void gram_acc64_n(const T *X, const T *Yv, int64_t n, int s1, int s2, double *C) {
+    gram_work.ensure(gram_work_size(n, s1, s2));
+    launch_gram<T, double>(X, Yv, n, s1, s2, C, gram_work.p, st);
   }
 
   // ---- Algorithm 2
@@ -978,7 +1011,7 @@ struct Engine : EngineBase {
         it_power += it;
         gram_acc64(Y.p, Y.p, s, s, K.p);
         launch_chol_drop(K.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
-        launch_block_update<T>(Y.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), G.p, st);
+        block_update(Y.p, Rinv.p, an.nG, s, s, T(1), nullptr, T(0), G.p);
       }
       // steps 2-3: block PCG on S_Gamma E = A_GI A_I^{-1} A_IG G, preconditioner A_G^{-1}
       // (S_Gamma form), or on S_I X = F = A_IG G, preconditioner A_I^{-1} (S_I form, the
@@ -1005,13 +1038,13 @@ struct Engine : EngineBase {
       while (it < prm.max_inner_it) {
         if (si) apply_SI(W.p, Z.p, s);      // Z holds Qw = S_I W
         else schur_apply(W.p, Z.p, s, true);  // Z holds Qw = S_Gamma W
-        launch_gram<T, T>(W.p, Z.p, nv, s, s, Cg.p, gram_work.p, st);
+        gram_n(W.p, Z.p, nv, s, s, Cg.p);
         launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st);
-        launch_block_update<T>(W.p, Rinv.p, nv, s, s, T(1), nullptr, T(0), P.p, st);
-        launch_block_update<T>(Z.p, Rinv.p, nv, s, s, T(1), nullptr, T(0), Q.p, st);
-        launch_gram<T, T>(P.p, R.p, nv, s, s, alpha.p, gram_work.p, st);   // alpha = P^T R
-        launch_block_update<T>(P.p, alpha.p, nv, s, s, T(1), E.p, T(1), E.p, st);
-        launch_block_update<T>(Q.p, alpha.p, nv, s, s, T(-1), R.p, T(1), R.p, st);
+        block_update(W.p, Rinv.p, nv, s, s, T(1), nullptr, T(0), P.p);
+        block_update(Z.p, Rinv.p, nv, s, s, T(1), nullptr, T(0), Q.p);
+        gram_n(P.p, R.p, nv, s, s, alpha.p);   // alpha = P^T R
+        block_update(P.p, alpha.p, nv, s, s, T(1), E.p, T(1), E.p);
+        block_update(Q.p, alpha.p, nv, s, s, T(-1), R.p, T(1), R.p);
         ++it;
         launch_col_sumsq<T>(R.p, nv, s, colsq.p, gram_work.p, st);
         launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st);
@@ -1027,8 +1060,8 @@ struct Engine : EngineBase {
         if (!(rat > prm.eps_inner)) break;
         if (si) solve_I(R.p, Z.p, s);       // Z = A_I^{-1} R
         else solve_G(R.p, Z.p, s);          // Z = A_G^{-1} R
-        launch_gram<T, T>(Q.p, Z.p, nv, s, s, beta.p, gram_work.p, st);    // Q^T Z
-        launch_block_update<T>(P.p, beta.p, nv, s, s, T(-1), Z.p, T(1), W.p, st);  // W = Z - P Q^T Z
+        gram_n(Q.p, Z.p, nv, s, s, beta.p);    // Q^T Z
+        block_update(P.p, beta.p, nv, s, s, T(-1), Z.p, T(1), W.p);  // W = Z - P Q^T Z
       }
       check_status();
       // step 4: Y = A_GI X (S_I form) or Y = A_G E (S_Gamma form; = A_GI S_I^{-1} A_IG G);
@@ -1048,8 +1081,8 @@ struct Engine : EngineBase {
     {
       const T *Ys = m3 ? E.p : Y.p, *Gs = m3 ? Fh.p : G.p;
       const int64_t ny = m3 ? an.nI : an.nG;
-      launch_gram<T, double>(Ys, Ys, ny, s, s, K.p, gram_work.p, st);
-      launch_gram<T, double>(Gs, Ys, ny, s, s, Cn.p, gram_work.p, st);
+      gram_acc64_n(Ys, Ys, ny, s, s, K.p);
+      gram_acc64_n(Gs, Ys, ny, s, s, Cn.p);
     }
     launch_nystrom_core(K.p, Cn.p, s, k, prm.eps_trunc_rel, 1e-14, Mix.p, Sigma.p, drank.p,
                         nys_work.p, st, 1, std::is_same<T, double>::value ? 1 : 0);
@@ -1063,11 +1096,11 @@ struct Engine : EngineBase {
     if (rank > 0) {
       if (m3) {
         // V = X Mix (n_interior x k), then U = A_GI V so that Zt = A_G^{-1} A_GI V = Zh
-        launch_block_update<T>(E.p, Mix.p, an.nI, s, k, T(1), nullptr, T(0), W.p, st);
+        block_update(E.p, Mix.p, an.nI, s, k, T(1), nullptr, T(0), W.p);
         launch_spmm<T>(A_GI.dT(), W.p, U.p, k, T(1), nullptr, T(0), st);
       } else {
         // U = Y Mix (columns beyond the rank are zero, Sigma there is zero)
-        launch_block_update<T>(Y.p, Mix.p, an.nG, s, k, T(1), nullptr, T(0), U.p, st);
+        block_update(Y.p, Mix.p, an.nG, s, k, T(1), nullptr, T(0), U.p);
       }
       // step 11: Z = A_G^{-1} U; M2's low-rank term kept as Zs = Z Sigma^{1/2} in FP64
       solve_G(U.p, Zt.p, k);
@@ -2173,6 +2206,41 @@ nsp_status nsp_schur_apply_noalloc(const nsp_handle *h, const void *X, void *Y, 
                  "problem too large for the fixed scratch of nsp_schur_apply_noalloc");
     unsigned char *scratch = scratch_for_current_device();
     h->eng->schur_apply_noalloc(X, Y, s, scratch);
+  });
+}
+
+int64_t nsp_gram_work_bytes(int64_t n, int32_t s1, int32_t s2) {
+  if (n < 0 || s1 < 1 || s2 < 1 || s1 > 256 || s2 > 256) return -1;
+  return (int64_t)(nsp::tc_gram_chunks(n) * (size_t)s1 * s2 * sizeof(double)) + 256;
+}
+nsp_status nsp_gram(const float *X, const float *Y, int64_t n, int32_t s1, int32_t s2,
+                    double *C, void *work, void *stream) {
+  if (!X || !Y || !C || !work || n < 0 || s1 < 1 || s2 < 1 || s1 > 256 || s2 > 256)
+    return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t off = nsp::tc_gram_chunks(n) * (size_t)s1 * s2 * sizeof(double);
+    auto *status = reinterpret_cast<nsp::DevStatus *>(static_cast<unsigned char *>(work) + off);
+    NSP_CUDA(cudaMemsetAsync(status, 0, sizeof(nsp::DevStatus), st));
+    nsp::launch_tc_gram(X, Y, n, s1, s2, C, static_cast<double *>(work), status, st);
+  });
+}
+int64_t nsp_block_update_work_bytes(int32_t s1, int32_t s2) {
+  if (s1 < 1 || s2 < 1 || s1 > 256 || s2 > 256) return -1;
+  return (int64_t)(nsp::tc_update_work_floats(s1, s2) * sizeof(float)) + 256;
+}
+nsp_status nsp_block_update(const float *A, const double *M, int64_t n, int32_t s1, int32_t s2,
+                            float scale, const float *Cin, float beta, float *Out, void *work,
+                            void *stream) {
+  if (!A || !M || !Out || !work || n < 0 || s1 < 1 || s2 < 1 || s1 > 256 || s2 > 256)
+    return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t off = nsp::tc_update_work_floats(s1, s2) * sizeof(float);
+    auto *status = reinterpret_cast<nsp::DevStatus *>(static_cast<unsigned char *>(work) + off);
+    NSP_CUDA(cudaMemsetAsync(status, 0, sizeof(nsp::DevStatus), st));
+    nsp::launch_tc_block_update(A, M, n, s1, s2, scale, Cin, beta, Out,
+                                static_cast<float *>(work), status, st);
   });
 }
 

@@ -470,7 +470,7 @@ void launch_gather_values(const int64_t *src, int64_t count, const double *Aval,
 }
 
 size_t gram_work_size(int64_t n, int s1, int s2) {
-  const int ch = gram_chunks(n, s1, s2);
+  const int ch = std::max<int>(gram_chunks(n, s1, s2), (int)tc_gram_chunks(n));
   const size_t g = (size_t)ch * s1 * s2;
   const int64_t cs = std::max(gemv_chunks(n),
                               std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 255) / 256)));
@@ -501,6 +501,13 @@ void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C, d
     case 6: gram_rt_launch<T, AccT, 6>(X, Y, n, s1, s2, C, work, stream); break;
     default: gram_rt_launch<T, AccT, 8>(X, Y, n, s1, s2, C, work, stream); break;
   }
+}
+
+void launch_gram_reduce(const double *work, int nchunks, int64_t entries, double *C,
+                        cudaStream_t stream) {
+  if (entries <= 0) return;
+  k_gram_reduce<<<reduce_grid(entries), BT, 0, stream>>>(work, nchunks, entries, C);
+  NSP_LAUNCH_CHECK();
 }
 
 void launch_gemv_t(const double *Z, int64_t n, int k, const double *r, double *t, double *work,

@@ -117,6 +117,20 @@ template <typename T, typename AccT>
 void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C,
                  double *work, cudaStream_t stream);
 size_t gram_work_size(int64_t n, int s1, int s2);
+// C[e] = sum over chunks c (in order) of work[c * entries + e]
+void launch_gram_reduce(const double *work, int nchunks, int64_t entries, double *C,
+                        cudaStream_t stream);
+// Tensor-core forms (k_tc.cu, FP32 data, 3xTF32 on tcgen05, FP32 accumulation in TMEM):
+// C = X^T Y with FP64 chunk partials (work >= tc_gram_chunks(n) * s1 * s2 doubles), and
+// Out = scale * A M + beta * C (mt_work >= tc_update_work_floats(s1, s2) floats). s1, s2 <=
+// 256. A bounded wait that runs out records DEV_TIMEOUT in st.
+size_t tc_gram_chunks(int64_t n);
+void launch_tc_gram(const float *X, const float *Y, int64_t n, int s1, int s2, double *C,
+                    double *work, DevStatus *st, cudaStream_t stream);
+size_t tc_update_work_floats(int s1, int s2);
+void launch_tc_block_update(const float *A, const double *M, int64_t n, int s1, int s2,
+                            float scale, const float *C, float beta, float *Out, float *mt_work,
+                            DevStatus *st, cudaStream_t stream);
 // Out (n x s2) = scale * A (n x s1) M (s1 x s2, FP64) + beta * C  (C may alias Out or be
 // nullptr)
 template <typename T>

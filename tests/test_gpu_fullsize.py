@@ -198,6 +198,23 @@ def test_fullsize128_build_and_solve_match_oracle(N, torch, cfg4):
     h.destroy()
 
 
+@pytest.mark.parametrize("variant", ["m2_adef", "m3"])
+def test_fullsize128_variants_solve(N, torch, cfg4, variant):
+    # the §4.3 variants at the 128^3 size (k = 128: the k x k Grams of M_2A-DEF and the
+    # interior sketch of M3 run at widths the M2 build does not use): the outer solve
+    # reaches 1e-8 (no stored oracle run for these)
+    P, gold = cfg4
+    _, b = F.make_rhs(P, 4, 0)
+    h = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                    precision="fp32", variant=variant)
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    xd = torch.zeros_like(bd)
+    inf = h.solve(bd, xd, rtol=P.rtol, maxit=500)
+    assert O.relative_residual(P.A, xd.cpu().numpy(), b) < 1e-8
+    assert inf["it_pcg"] > 0
+    h.destroy()
+
+
 def test_fullsize_batch_sampled_matrices(N, torch):
     specs = F.batched_problem_specs()
     probs = [F.problem_from_spec(sp) for sp in specs]
