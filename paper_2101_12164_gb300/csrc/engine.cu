@@ -107,22 +107,27 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
   require(an.nnz < (int64_t(1) << 31) - 1, NSP_ERR_UNSUPPORTED, "CSR: too many nonzeros");
   an.rowptr.assign(rowptr, rowptr + n + 1);
   an.col.assign(col, col + an.nnz);
-  for (int64_t i = 0; i < n; ++i) {
-    bool diag = false;
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      require(col[e] >= 0 && col[e] < n, NSP_ERR_INVALID_ARG, "CSR: column out of range");
-      if (e > rowptr[i]) require(col[e] > col[e - 1], NSP_ERR_INVALID_ARG, "CSR: columns not sorted/unique");
-      diag |= col[e] == i;
+  const int64_t vchunk = 16384, nvch = (n + vchunk - 1) / vchunk;
+  parallel_for(nvch, [&](int64_t c) {
+    for (int64_t i = c * vchunk; i < std::min(n, (c + 1) * vchunk); ++i) {
+      bool diag = false;
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        require(col[e] >= 0 && col[e] < n, NSP_ERR_INVALID_ARG, "CSR: column out of range");
+        if (e > rowptr[i]) require(col[e] > col[e - 1], NSP_ERR_INVALID_ARG, "CSR: columns not sorted/unique");
+        diag |= col[e] == i;
+      }
+      require(diag, NSP_ERR_INVALID_ARG, "CSR: missing diagonal entry");
     }
-    require(diag, NSP_ERR_INVALID_ARG, "CSR: missing diagonal entry");
-  }
+  });
   // symmetric pattern
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
-      const int32_t j = col[e];
-      const int32_t *b = col + rowptr[j], *en = col + rowptr[j + 1];
-      require(std::binary_search(b, en, (int32_t)i), NSP_ERR_INVALID_ARG, "CSR: pattern not symmetric");
-    }
+  parallel_for(nvch, [&](int64_t c) {
+    for (int64_t i = c * vchunk; i < std::min(n, (c + 1) * vchunk); ++i)
+      for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int32_t j = col[e];
+        const int32_t *b = col + rowptr[j], *en = col + rowptr[j + 1];
+        require(std::binary_search(b, en, (int32_t)i), NSP_ERR_INVALID_ARG, "CSR: pattern not symmetric");
+      }
+  });
   // partition
   require(P && P->part && P->nblocks >= 1, NSP_ERR_INVALID_ARG, "partition: null");
   const int32_t nb = P->nblocks;
@@ -177,21 +182,25 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
     }
     return gr;
   };
-  for (int32_t b = 0; b < nb; ++b) {
+  // orderings: every interior block and the interface, in parallel (task 0 = the interface;
+  // graph_of writes g2l only at the task's own, disjoint, unknowns)
+  std::vector<int64_t> ginit;
+  parallel_for(nb + 1, [&](int64_t t) {
+    if (t == 0) {   // the interface graph is the largest: started first
+      Graph gr = graph_of(gam, -1);
+      std::vector<int32_t> ord = nested_dissection(gr, nd_leaf());
+      ginit.resize(ord.size());
+      for (size_t q = 0; q < ord.size(); ++q) ginit[q] = gam[ord[q]];
+      return;
+    }
+    const int32_t b = (int32_t)t - 1;
     if (!P->perm && !nodes[b].empty()) {
       Graph gr = graph_of(nodes[b], b);
       std::vector<int32_t> ord = nested_dissection(gr, nd_leaf());
       init[b].resize(ord.size());
       for (size_t q = 0; q < ord.size(); ++q) init[b][q] = nodes[b][ord[q]];
     }
-  }
-  std::vector<int64_t> ginit;
-  {
-    Graph gr = graph_of(gam, -1);
-    std::vector<int32_t> ord = nested_dissection(gr, nd_leaf());
-    ginit.resize(ord.size());
-    for (size_t q = 0; q < ord.size(); ++q) ginit[q] = gam[ord[q]];
-  }
+  });
   // lower-triangle patterns in the initial orders
   auto pattern = [&](const std::vector<int64_t> &ord, int32_t label) {
     BlockPattern bp;
@@ -212,7 +221,7 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
   };
   {
     std::vector<BlockPattern> pats(nb);
-    for (int32_t b = 0; b < nb; ++b) pats[b] = pattern(init[b], b);
+    parallel_for(nb, [&](int64_t b) { pats[b] = pattern(init[b], (int32_t)b); });
     analyze_forest(pats, relax_level(), an.FI);
   }
   {
@@ -241,21 +250,37 @@ static void analyze(const nsp_csr *A, const int64_t *rowptr, const int32_t *col,
     an.i2u_G[t] = g2u[g];
     g2int[g] = t;
   }
+  // rows of A restricted to interior or interface columns: counts, then the entries, both
+  // in parallel over row chunks
   auto sub = [&](const std::vector<int64_t> &rows_g, bool cols_gamma, int32_t ncols) {
     HostSub h;
     h.nrows = (int32_t)rows_g.size();
     h.ncols = ncols;
     h.rowptr.assign(h.nrows + 1, 0);
-    for (int32_t r = 0; r < h.nrows; ++r) {
-      const int64_t g = rows_g[r];
-      for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
-        const bool cg = part[col[e]] < 0;
-        if (cg != cols_gamma) continue;
-        h.col.push_back((int32_t)g2int[col[e]]);
-        h.src.push_back(e);
+    const int64_t chunk = 4096, nch = (h.nrows + chunk - 1) / chunk;
+    parallel_for(nch, [&](int64_t c) {
+      for (int64_t r = c * chunk; r < std::min<int64_t>(h.nrows, (c + 1) * chunk); ++r) {
+        const int64_t g = rows_g[r];
+        int32_t cnt = 0;
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) cnt += (part[col[e]] < 0) == cols_gamma;
+        h.rowptr[r + 1] = cnt;
       }
-      h.rowptr[r + 1] = (int32_t)h.col.size();
-    }
+    });
+    for (int32_t r = 0; r < h.nrows; ++r) h.rowptr[r + 1] += h.rowptr[r];
+    h.col.resize(h.rowptr[h.nrows]);
+    h.src.resize(h.rowptr[h.nrows]);
+    parallel_for(nch, [&](int64_t c) {
+      for (int64_t r = c * chunk; r < std::min<int64_t>(h.nrows, (c + 1) * chunk); ++r) {
+        const int64_t g = rows_g[r];
+        int64_t q = h.rowptr[r];
+        for (int64_t e = rowptr[g]; e < rowptr[g + 1]; ++e) {
+          if ((part[col[e]] < 0) != cols_gamma) continue;
+          h.col[q] = (int32_t)g2int[col[e]];
+          h.src[q] = e;
+          ++q;
+        }
+      }
+    });
     return h;
   };
   an.A_I = sub(an.i2g_I, false, (int32_t)an.nI);

@@ -12,10 +12,15 @@
 #include "symbolic.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
+#include <cstdlib>
+#include <exception>
 #include <functional>
+#include <mutex>
 #include <numeric>
 #include <stdexcept>
+#include <thread>
 
 namespace nsp {
 
@@ -331,24 +336,24 @@ bool accept_merge(int relax, int64_t wc, int64_t wj, int64_t mj, int64_t nz) {
 
 }  // namespace
 
-void analyze_forest(const std::vector<BlockPattern> &blocks, int relax, Forest &f) {
+// Symbolic analysis of one block in block-local numbering (offsets from 0): supernodes,
+// their row structures, levels, panel / front / update-row offsets, relative maps and
+// assembly lists. analyze_forest concatenates the blocks.
+static void analyze_block(const BlockPattern &P, int relax, Forest &f) {
   f = Forest();
-  f.nblocks = (int32_t)blocks.size();
-  f.block_off.assign(f.nblocks + 1, 0);
-  for (int32_t b = 0; b < f.nblocks; ++b) f.block_off[b + 1] = f.block_off[b] + blocks[b].n;
-  f.n = f.block_off[f.nblocks];
+  f.nblocks = 1;
+  f.block_off = {0, (int64_t)P.n};
+  f.n = P.n;
   f.order.resize(f.n);
   f.sn_rowptr.push_back(0);
   f.asm_ptr.push_back(0);
-  std::vector<int32_t> pos;          // forest index -> position in the current front
-  pos.assign(f.n, -1);
+  std::vector<int32_t> pos(f.n, -1);   // block index -> position in the current front
   int64_t panel = 0, front = 0, upd = 0;
-
-  for (int32_t b = 0; b < f.nblocks; ++b) {
-    const BlockPattern &P = blocks[b];
+  const int32_t b = 0;
+  {
     const int32_t n = P.n;
-    const int64_t off = f.block_off[b];
-    if (n == 0) continue;
+    const int64_t off = 0;
+    if (n == 0) return;
     LocalSym L;
     local_symbolic(P, L);
     for (int32_t k = 0; k < n; ++k) f.order[off + k] = L.post[k];
@@ -492,7 +497,109 @@ void analyze_forest(const std::vector<BlockPattern> &blocks, int relax, Forest &
         f.flops_factor += r + r * (r + 1);
       }
     }
+    }
+  f.panel_size = panel;
+  f.front_size = front;
+  f.upd_rows = upd;
+}
+
+void parallel_for(int64_t count, const std::function<void(int64_t)> &body) {
+  int nt = (int)std::thread::hardware_concurrency();
+  if (const char *e = std::getenv("NSP_THREADS")) nt = std::atoi(e);
+  nt = (int)std::max<int64_t>(1, std::min<int64_t>({(int64_t)std::max(nt, 1), count, 64}));
+  if (nt <= 1) {
+    for (int64_t i = 0; i < count; ++i) body(i);
+    return;
   }
+  std::atomic<int64_t> next{0};
+  std::exception_ptr err;
+  std::mutex mu;
+  auto work = [&] {
+    for (int64_t i = next++; i < count; i = next++) {
+      try {
+        body(i);
+      } catch (...) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!err) err = std::current_exception();
+      }
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto &t : th) t.join();
+  if (err) std::rethrow_exception(err);
+}
+
+void analyze_forest(const std::vector<BlockPattern> &blocks, int relax, Forest &f) {
+  f = Forest();
+  f.nblocks = (int32_t)blocks.size();
+  f.block_off.assign(f.nblocks + 1, 0);
+  for (int32_t b = 0; b < f.nblocks; ++b) f.block_off[b + 1] = f.block_off[b] + blocks[b].n;
+  f.n = f.block_off[f.nblocks];
+  f.order.resize(f.n);
+  f.sn_rowptr.push_back(0);
+  f.asm_ptr.push_back(0);
+  // blocks are independent: analyze them in parallel, then concatenate in block order
+  std::vector<Forest> part(f.nblocks);
+  parallel_for(f.nblocks, [&](int64_t b) { analyze_block(blocks[b], relax, part[b]); });
+  // offsets of every block's pieces in the concatenation, then a parallel copy with shifts
+  const int32_t nb = f.nblocks;
+  std::vector<int64_t> sn0(nb + 1, 0), row0(nb + 1, 0), asm0(nb + 1, 0), upd0(nb + 1, 0),
+      pan0(nb + 1, 0), fr0(nb + 1, 0);
+  for (int32_t b = 0; b < nb; ++b) {
+    const Forest &q = part[b];
+    sn0[b + 1] = sn0[b] + q.nsn;
+    row0[b + 1] = row0[b] + (int64_t)q.rows.size();
+    asm0[b + 1] = asm0[b] + (int64_t)q.asm_dst.size();
+    upd0[b + 1] = upd0[b] + q.upd_rows;
+    pan0[b + 1] = pan0[b] + q.panel_size;
+    fr0[b + 1] = fr0[b] + q.front_size;
+    f.nnz_L += q.nnz_L;
+    f.flops_factor += q.flops_factor;
+  }
+  const int64_t nsn = sn0[nb];
+  f.nsn = (int32_t)nsn;
+  f.sn_first.resize(nsn);
+  f.sn_w.resize(nsn);
+  f.sn_m.resize(nsn);
+  f.sn_parent.resize(nsn);
+  f.sn_block.resize(nsn);
+  f.sn_level.resize(nsn);
+  f.sn_rowptr.resize(nsn + 1);
+  f.sn_panel.resize(nsn);
+  f.sn_front.resize(nsn);
+  f.sn_upd.resize(nsn);
+  f.asm_ptr.resize(nsn + 1);
+  f.rows.resize(row0[nb]);
+  f.relmap.resize(upd0[nb]);
+  f.asm_dst.resize(asm0[nb]);
+  f.asm_src.resize(asm0[nb]);
+  parallel_for(nb, [&](int64_t b) {
+    Forest &q = part[b];
+    const int64_t off = f.block_off[b], base = sn0[b];
+    for (int64_t k = 0; k < (int64_t)q.order.size(); ++k) f.order[off + k] = q.order[k];
+    for (int32_t J = 0; J < q.nsn; ++J) {
+      const int64_t g = base + J;
+      f.sn_first[g] = (int32_t)(off + q.sn_first[J]);
+      f.sn_w[g] = q.sn_w[J];
+      f.sn_m[g] = q.sn_m[J];
+      f.sn_parent[g] = q.sn_parent[J] < 0 ? -1 : (int32_t)(base + q.sn_parent[J]);
+      f.sn_block[g] = (int32_t)b;
+      f.sn_level[g] = q.sn_level[J];
+      f.sn_rowptr[g + 1] = row0[b] + q.sn_rowptr[J + 1];
+      f.sn_panel[g] = pan0[b] + q.sn_panel[J];
+      f.sn_front[g] = fr0[b] + q.sn_front[J];
+      f.sn_upd[g] = upd0[b] + q.sn_upd[J];
+      f.asm_ptr[g + 1] = asm0[b] + q.asm_ptr[J + 1];
+    }
+    for (size_t r = 0; r < q.rows.size(); ++r) f.rows[row0[b] + r] = (int32_t)(off + q.rows[r]);
+    std::copy(q.relmap.begin(), q.relmap.end(), f.relmap.begin() + upd0[b]);
+    std::copy(q.asm_dst.begin(), q.asm_dst.end(), f.asm_dst.begin() + asm0[b]);
+    std::copy(q.asm_src.begin(), q.asm_src.end(), f.asm_src.begin() + asm0[b]);
+    q = Forest();
+  });
+  const int64_t panel = pan0[nb], front = fr0[nb], upd = upd0[nb];
   f.panel_size = panel;
   f.front_size = front;
   f.upd_rows = upd;

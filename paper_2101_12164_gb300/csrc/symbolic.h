@@ -9,6 +9,7 @@
 // structure of m >= w rows whose first w entries are its own columns.
 #pragma once
 #include <cstdint>
+#include <functional>
 #include <vector>
 
 namespace nsp {
@@ -58,6 +59,10 @@ struct Graph {                            // symmetric adjacency, no self loops
   std::vector<int64_t> ptr;
   std::vector<int32_t> adj;
 };
+
+// body(i) for i in [0, count) on up to hardware_concurrency() host threads (NSP_THREADS
+// overrides; 1 runs serially); the first exception of a body is rethrown after all end.
+void parallel_for(int64_t count, const std::function<void(int64_t)> &body);
 
 // Nested-dissection order (new -> old) of a graph by level-structure bisection.
 std::vector<int32_t> nested_dissection(const Graph &g, int32_t leaf);
