@@ -263,7 +263,8 @@ nsp_status nsp_schur_apply(const nsp_handle *h, const void *X, void *Y, int32_t 
  *  - All calls share the array, so calls whose work overlaps on the GPU (other streams or
  *    other handles) race; the array keeps the last call's contents (every temporary is fully
  *    written before it is read, nothing needs clearing).
- * Asynchronous on the handle's stream like nsp_schur_apply. */
+ * Asynchronous on the handle's stream like nsp_schur_apply: it never runs the sweep
+ * autotuner (a width the handle has not tuned yet uses the default sweep grid). */
 #define NSP_NOALLOC_SCRATCH_BYTES (16u << 20)
 nsp_status nsp_schur_apply_noalloc(const nsp_handle *h, const void *X, void *Y, int32_t s);
 

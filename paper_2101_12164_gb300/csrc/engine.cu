@@ -769,7 +769,10 @@ struct Engine : EngineBase {
   }
 
   // ---- X = A_b^{-1} B over a forest (internal order, s columns): one persistent launch
-  void solve_forest(ForestData &F, const T *panel, const T *B, T *Ywk, T *Uwk, T *X, int sc) {
+  // tune = false (the allocation-free apply): no autotuning when no grid is cached yet, the
+  // default grid instead, so that the call never synchronizes
+  void solve_forest(ForestData &F, const T *panel, const T *B, T *Ywk, T *Uwk, T *X, int sc,
+                    bool tune = true) {
     F.vec_rows = sweep_vector_rows((int)sizeof(T));
     auto &P = F.plan(sc == 1, st);
     int grid = 0;
@@ -779,7 +782,7 @@ struct Engine : EngineBase {
       if (grid == kResidentGrid && F.h.nblocks < 2) grid = 0;
     } else if (it != P.tuned_grid.end()) {
       grid = it->second;
-    } else if (autotune_enabled() && !capturing()) {
+    } else if (tune && autotune_enabled() && !capturing()) {
       grid = tune_sweep(F, P, panel, B, Ywk, Uwk, X, sc);
       P.tuned_grid[sc] = grid;
     }
@@ -909,7 +912,7 @@ struct Engine : EngineBase {
     T *uw = take(std::max<int64_t>(FI.h.upd_rows, 1) * e);
     launch_gather_rows<T, T>(i2u_G.p, an.nG, (const T *)X, xi, sc, st);
     launch_spmm<T>(A_IG.dT(), xi, b, sc, T(1), nullptr, T(0), st);
-    solve_forest(FI, panelI.p, b, yw, uw, xw, sc);
+    solve_forest(FI, panelI.p, b, yw, uw, xw, sc, false);
     launch_spmm<T>(A_G.dT(), xi, yi, sc, T(1), nullptr, T(0), st);
     launch_spmm<T>(A_GI.dT(), xw, yi, sc, T(-1), yi, T(1), st);
     launch_scatter_rows<T, T>(i2u_G.p, an.nG, yi, (T *)Yv, sc, st);
