@@ -391,11 +391,19 @@ int64_t nsp_kernel_launches(void);
  * device status word: nonzero if a bounded wait of the kernel ran out, which never happens
  * on a working GPU). Asynchronous on `stream` (cudaStream_t, NULL = default stream).
  *   nsp_gram         : C (s1 x s2, doubles) = X^T Y, X n x s1, Y n x s2 (floats).
+ *   nsp_gram_compensated : the same product as the Nyström core forms K = Y^T Y and C = G^T Y
+ *                      (Algorithm 2 steps 5-6), where the Cholesky-QR needs more than FP32
+ *                      sums: FP32 pipes with compensated dot products (exact products and
+ *                      TwoSum error terms, Ogita-Rump-Oishi Dot2), accurate as if summed in
+ *                      twice FP32 precision; partials of row chunks added in FP64. Same work
+ *                      size query as nsp_gram.
  *   nsp_block_update : Out (n x s2) = scale * A M + beta * Cin, A n x s1 (floats), M s1 x s2
  *                      (doubles), Cin n x s2 or NULL (may alias Out).                       */
 int64_t nsp_gram_work_bytes(int64_t n, int32_t s1, int32_t s2);
 nsp_status nsp_gram(const float *X, const float *Y, int64_t n, int32_t s1, int32_t s2,
                     double *C, void *work, void *stream);
+nsp_status nsp_gram_compensated(const float *X, const float *Y, int64_t n, int32_t s1,
+                                int32_t s2, double *C, void *work, void *stream);
 int64_t nsp_block_update_work_bytes(int32_t s1, int32_t s2);
 nsp_status nsp_block_update(const float *A, const double *M, int64_t n, int32_t s1, int32_t s2,
                             float scale, const float *Cin, float beta, float *Out, void *work,

@@ -30,7 +30,8 @@ EXPORTS = ["nsp_default_params", "nsp_build", "nsp_rebuild", "nsp_apply", "nsp_s
            "nsp_solve_batched", "nsp_net_num_params", "nsp_net_create", "nsp_net_set_params",
            "nsp_net_get", "nsp_net_forward", "nsp_net_loss_grad", "nsp_net_zero_grad",
            "nsp_net_adam_step", "nsp_net_sketch", "nsp_net_destroy", "nsp_check_timeout_path",
-           "nsp_gram_work_bytes", "nsp_gram", "nsp_block_update_work_bytes", "nsp_block_update"]
+           "nsp_gram_work_bytes", "nsp_gram", "nsp_gram_compensated",
+           "nsp_block_update_work_bytes", "nsp_block_update"]
 
 
 class NspError(RuntimeError):
@@ -129,6 +130,7 @@ def lib():
             "nsp_check_timeout_path": (C.c_int, [P, C.c_int32, C.POINTER(C.c_int32)]),
             "nsp_gram_work_bytes": (C.c_int64, [C.c_int64, C.c_int32, C.c_int32]),
             "nsp_gram": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
+            "nsp_gram_compensated": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, P, P, P]),
             "nsp_block_update_work_bytes": (C.c_int64, [C.c_int32, C.c_int32]),
             "nsp_block_update": (C.c_int, [P, P, C.c_int64, C.c_int32, C.c_int32, C.c_float, P,
                                            C.c_float, P, P, P]),
@@ -371,9 +373,10 @@ def _status_word(work, nbytes):
     return int(w.view(torch.int32)[0])
 
 
-def nsp_gram(X, Y, C, work=None):
-    """C = X^T Y on the tensor cores (X n x s1, Y n x s2 float32 CUDA tensors, C s1 x s2
-    float64). Synchronizes and checks the kernel's status word."""
+def nsp_gram(X, Y, C, work=None, compensated=False):
+    """C = X^T Y (X n x s1, Y n x s2 float32 CUDA tensors, C s1 x s2 float64): on the tensor
+    cores, or with compensated FP32 sums (compensated=True, the Nyström core's Grams).
+    Synchronizes and checks the kernel's status word."""
     import torch
     n, s1 = X.shape
     s2 = Y.shape[1]
@@ -382,7 +385,8 @@ def nsp_gram(X, Y, C, work=None):
         raise NspError(1, "nsp_gram_work_bytes")
     if work is None or work.numel() * work.element_size() < nb:
         work = torch.empty(nb, dtype=torch.uint8, device=X.device)
-    _check(lib().nsp_gram(_ptr(X), _ptr(Y), n, s1, s2, _ptr(C), _ptr(work), _stream()), "nsp_gram")
+    fn = lib().nsp_gram_compensated if compensated else lib().nsp_gram
+    _check(fn(_ptr(X), _ptr(Y), n, s1, s2, _ptr(C), _ptr(work), _stream()), "nsp_gram")
     torch.cuda.synchronize()
     if _status_word(work, nb) != 0:
         raise NspError(6, "nsp_gram: a bounded device wait ran out")

@@ -2237,9 +2237,25 @@ nsp_status nsp_schur_apply_noalloc(const nsp_handle *h, const void *X, void *Y, 
   });
 }
 
+// partials of either Gram kernel, then the status word
+static size_t gram_partials_bytes(int64_t n, int32_t s1, int32_t s2) {
+  return nsp::gram_work_size(n, s1, s2) * sizeof(double);
+}
 int64_t nsp_gram_work_bytes(int64_t n, int32_t s1, int32_t s2) {
   if (n < 0 || s1 < 1 || s2 < 1 || s1 > 256 || s2 > 256) return -1;
-  return (int64_t)(nsp::tc_gram_chunks(n) * (size_t)s1 * s2 * sizeof(double)) + 256;
+  return (int64_t)gram_partials_bytes(n, s1, s2) + 256;
+}
+nsp_status nsp_gram_compensated(const float *X, const float *Y, int64_t n, int32_t s1,
+                                int32_t s2, double *C, void *work, void *stream) {
+  if (!X || !Y || !C || !work || n < 0 || s1 < 1 || s2 < 1 || s1 > 256 || s2 > 256)
+    return NSP_ERR_INVALID_ARG;
+  return guard([&] {
+    const cudaStream_t st = (cudaStream_t)stream;
+    auto *status = reinterpret_cast<nsp::DevStatus *>(static_cast<unsigned char *>(work) +
+                                                      gram_partials_bytes(n, s1, s2));
+    NSP_CUDA(cudaMemsetAsync(status, 0, sizeof(nsp::DevStatus), st));
+    nsp::launch_gram<float, double>(X, Y, n, s1, s2, C, static_cast<double *>(work), st);
+  });
 }
 nsp_status nsp_gram(const float *X, const float *Y, int64_t n, int32_t s1, int32_t s2,
                     double *C, void *work, void *stream) {
@@ -2247,8 +2263,8 @@ nsp_status nsp_gram(const float *X, const float *Y, int64_t n, int32_t s1, int32
     return NSP_ERR_INVALID_ARG;
   return guard([&] {
     const cudaStream_t st = (cudaStream_t)stream;
-    const size_t off = nsp::tc_gram_chunks(n) * (size_t)s1 * s2 * sizeof(double);
-    auto *status = reinterpret_cast<nsp::DevStatus *>(static_cast<unsigned char *>(work) + off);
+    auto *status = reinterpret_cast<nsp::DevStatus *>(static_cast<unsigned char *>(work) +
+                                                      gram_partials_bytes(n, s1, s2));
     NSP_CUDA(cudaMemsetAsync(status, 0, sizeof(nsp::DevStatus), st));
     nsp::launch_tc_gram(X, Y, n, s1, s2, C, static_cast<double *>(work), status, st);
   });

@@ -3,6 +3,7 @@
 // X^T Y, tall-skinny block updates, column norms, the Philox sketch generator and the FP64
 // vector kernels of the outer PCG.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -120,6 +121,80 @@ __global__ void __launch_bounds__(BT) k_gram_partial(const T *__restrict__ X,
     for (int j = 0; j < RT; ++j) {
       const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
       if (a < s1 && b < s2) work[((size_t)chunk * s1 + a) * s2 + b] = (double)acc[i][j];
+    }
+}
+
+// Gram of FP32 data with twice-working-precision accuracy on the FP32 pipes (the s x s Grams
+// of the Nyström core, K = Y^T Y and C = G^T Y, whose Cholesky-QR needs more than FP32 sums):
+// compensated dot products, Algorithm Dot2 of Ogita, Rump & Oishi ("Accurate sum and dot
+// product", SIAM J. Sci. Comput. 2005). Each product x y = p + e exactly (p = fl(x y),
+// e = fma(x, y, -p), Dekker / Veltkamp TwoProduct); the running sum s and the error term c
+// follow Knuth's TwoSum: t = s + p, z = t - s, c += ((s - (t - z)) + (p - z)) + e, s = t. The
+// chunk partial s + c is stored in FP64 and the chunks are added in FP64 in chunk order. The
+// _rn intrinsics keep the compiler from contracting the products into the sums.
+template <int RT>
+__global__ void __launch_bounds__(BT) k_gram_dot2(const float *__restrict__ X,
+                                                  const float *__restrict__ Y, int64_t n,
+                                                  int s1, int s2, int64_t rpc, double *work) {
+  constexpr int TS = 16 * RT;
+  __shared__ float Xs[GR][TS];
+  __shared__ float Ys[GR][TS];
+  const int chunk = blockIdx.x;
+  const int a0 = blockIdx.y * TS, b0 = blockIdx.z * TS;
+  const int64_t i0 = (int64_t)chunk * rpc;
+  const int64_t i1 = min(n, i0 + rpc);
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  float sh[RT][RT], sc[RT][RT];
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+#pragma unroll
+    for (int j = 0; j < RT; ++j) sh[i][j] = sc[i][j] = 0.f;
+  constexpr int NQ = GR * TS / BT;
+  for (int64_t ib = i0; ib < i1; ib += GR) {
+    float xv[NQ], yv[NQ];
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int q = tid + u * BT, r = q / TS, c = q % TS;
+      const int64_t row = ib + r;
+      xv[u] = (row < i1 && a0 + c < s1) ? X[(size_t)row * s1 + a0 + c] : 0.f;
+      yv[u] = (row < i1 && b0 + c < s2) ? Y[(size_t)row * s2 + b0 + c] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      const int q = tid + u * BT;
+      Xs[q / TS][q % TS] = xv[u];
+      Ys[q / TS][q % TS] = yv[u];
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int r = 0; r < GR; ++r) {
+      float xa[RT], yb[RT];
+#pragma unroll
+      for (int i = 0; i < RT; ++i) xa[i] = Xs[r][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < RT; ++j) yb[j] = Ys[r][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int j = 0; j < RT; ++j) {
+          const float p = __fmul_rn(xa[i], yb[j]);
+          const float e = __fmaf_rn(xa[i], yb[j], -p);
+          const float t = __fadd_rn(sh[i][j], p);
+          const float z = __fsub_rn(t, sh[i][j]);
+          const float err = __fadd_rn(__fsub_rn(sh[i][j], __fsub_rn(t, z)), __fsub_rn(p, z));
+          sc[i][j] = __fadd_rn(sc[i][j], __fadd_rn(err, e));
+          sh[i][j] = t;
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+#pragma unroll
+    for (int j = 0; j < RT; ++j) {
+      const int a = a0 + ty + 16 * i, b = b0 + tx + 16 * j;
+      if (a < s1 && b < s2)
+        work[((size_t)chunk * s1 + a) * s2 + b] = (double)sh[i][j] + (double)sc[i][j];
     }
 }
 
@@ -495,6 +570,20 @@ template <typename T, typename AccT>
 void launch_gram(const T *X, const T *Y, int64_t n, int s1, int s2, double *C, double *work,
                  cudaStream_t stream) {
   if (s1 <= 0 || s2 <= 0) return;
+  if constexpr (std::is_same<T, float>::value && std::is_same<AccT, double>::value) {
+    // FP32 data, FP64-class sums: compensated FP32 (same chunk count as the plain kernel, so
+    // the same partials buffer serves)
+    constexpr int RT = 4, TS = 16 * RT;
+    const int ch = gram_chunks(n, s1, s2);
+    const int64_t rpc = std::max<int64_t>(GR, ((n + ch - 1) / ch + GR - 1) / GR * GR);
+    dim3 grid(ch, ceil_div(s1, TS), ceil_div(s2, TS));
+    k_gram_dot2<RT><<<grid, BT, 0, stream>>>(X, Y, n, s1, s2, rpc, work);
+    NSP_LAUNCH_CHECK();
+    const int64_t ent = (int64_t)s1 * s2;
+    k_gram_reduce<<<reduce_grid(ent), BT, 0, stream>>>(work, ch, ent, C);
+    NSP_LAUNCH_CHECK();
+    return;
+  }
   switch (gram_rt(s1, s2)) {
     case 2: gram_rt_launch<T, AccT, 2>(X, Y, n, s1, s2, C, work, stream); break;
     case 4: gram_rt_launch<T, AccT, 4>(X, Y, n, s1, s2, C, work, stream); break;

@@ -241,10 +241,16 @@ __global__ void __launch_bounds__(TT, 1)
     for (int u = 0; u < AI; ++u) {
       const int q = tid + u * TT, r = q / (KS / 4), g = q % (KS / 4);
       const int64_t row = row0 + r;
+      const int col0 = c * KS + 4 * g;
+      if (row < n && (s1 & 3) == 0 && col0 + 3 < s1) {
+        const float4 x = __ldcg(reinterpret_cast<const float4 *>(A + (size_t)row * s1 + col0));
+        av[u][0] = x.x; av[u][1] = x.y; av[u][2] = x.z; av[u][3] = x.w;
+      } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int col = c * KS + 4 * g + k;
-        av[u][k] = (row < n && col < s1) ? __ldcg(&A[(size_t)row * s1 + col]) : 0.f;
+        for (int k = 0; k < 4; ++k) {
+          const int col = col0 + k;
+          av[u][k] = (row < n && col < s1) ? __ldcg(&A[(size_t)row * s1 + col]) : 0.f;
+        }
       }
     }
     const float4 *src = reinterpret_cast<const float4 *>(
@@ -292,20 +298,48 @@ __global__ void __launch_bounds__(TT, 1)
     if (c == nch - 1) {   // the tile's accumulators are complete: epilogue
       if (!tc::mbar_wait(&mbar[buf], (uint32_t)((j >> 1) & 1), MAX_SPINS)) ok = false;
       tc::fence_after();
+      // 32 columns per round: the C values (16-byte loads when rows are 16-byte aligned) are
+      // requested before the two TMEM loads, and one wait covers both
+      const bool vec = (s2 & 3) == 0;
       for (int t = 0; t < MT; ++t) {
         const int64_t row = row0 + t * 128 + 32 * warp + lane;
-        for (int c0 = 0; c0 < NP; c0 += 8) {
-          float v[8];
-          tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + t * NP + c0, v);
-          if (row < n && ok) {
+        const bool rok = row < n && ok;
+        for (int c0 = 0; c0 < NP; c0 += 32) {
+          float cv[32];
 #pragma unroll
-            for (int jj = 0; jj < 8; ++jj) {
-              const int col = c0 + jj;
-              if (col < s2) {
-                float o = scale * v[jj];
-                if (C) o += beta * C[(size_t)row * s2 + col];
-                Out[(size_t)row * s2 + col] = o;
-              }
+          for (int q = 0; q < 8; ++q) {
+            const int col = c0 + 4 * q;
+            if (C && rok && vec && col + 3 < s2) {
+              const float4 x = __ldcg(reinterpret_cast<const float4 *>(C + (size_t)row * s2 + col));
+              cv[4 * q] = x.x; cv[4 * q + 1] = x.y; cv[4 * q + 2] = x.z; cv[4 * q + 3] = x.w;
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                cv[4 * q + u] = (C && rok && col + u < s2) ? __ldcg(&C[(size_t)row * s2 + col + u]) : 0.f;
+            }
+          }
+          uint32_t r0[16], r1[16];
+          const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + t * NP + c0;
+          tc::tmem_ld16_nowait(ta, r0);
+          if (c0 + 16 < NP) tc::tmem_ld16_nowait(ta + 16, r1);
+          tc::tmem_wait_ld();
+          if (!rok) continue;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int col = c0 + 4 * q;
+            float o[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int jj = 4 * q + u;
+              const float acc = __uint_as_float(jj < 16 ? r0[jj] : r1[jj - 16]);
+              o[u] = scale * acc + (C ? beta * cv[jj] : 0.f);
+            }
+            if (vec && col + 3 < s2) {
+              *reinterpret_cast<float4 *>(Out + (size_t)row * s2 + col) = make_float4(o[0], o[1], o[2], o[3]);
+            } else {
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (col + u < s2) Out[(size_t)row * s2 + col + u] = o[u];
             }
           }
         }

@@ -93,3 +93,22 @@ def test_block_pcg_with_tensor_core_products_matches_simt(N, torch, monkeypatch)
     assert outs[0][0] == outs[1][0]
     assert colwise_err(outs[0][1], outs[1][1]) < 1e-4
     assert colwise_err(outs[0][2], outs[1][2]) < 1e-4
+
+
+@pytest.mark.parametrize("n,s1,s2", [(1000, 7, 13), (70001, 160, 160), (300000, 128, 128)])
+def test_compensated_gram_matches_exact_sums(N, torch, n, s1, s2):
+    # the Nyström core's Grams: products of FP32 values are exact in FP64 and the reference
+    # sums them in FP64 (typically ~sqrt(n) 2^-53 sum |p| off); the compensated FP32 kernel,
+    # typically ~sqrt(rows per chunk) 2^-48 sum |p| off, must be within 2^-36 sum |p|, while
+    # plain FP32 sums of these rows are ~sqrt(n) 2^-24 ~ 2^-16 sum |p| off
+    rng = np.random.default_rng(n + 3 * s1)
+    X = rng.standard_normal((n, s1)).astype(np.float32)
+    Y = rng.standard_normal((n, s2)).astype(np.float32)
+    Xd, Yd = torch.tensor(X, device="cuda"), torch.tensor(Y, device="cuda")
+    Cd = torch.empty(s1, s2, dtype=torch.float64, device="cuda")
+    N.nsp_gram(Xd, Yd, Cd, compensated=True)
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    ref = X64.T @ Y64
+    absum = np.abs(X64).T @ np.abs(Y64)
+    err = np.abs(Cd.cpu().numpy() - ref)
+    assert np.all(err <= 2.0 ** -36 * absum + 1e-300), float((err / absum).max())
