@@ -1,7 +1,9 @@
 // Small dense linear algebra on one CTA: the s x s steps of the breakdown-free block PCG
 // (Cholesky-QR with column drop, alpha/beta solves) and the Nyström core of Algorithm 2
 // steps 5-10 (Cholesky-QR of Y, EVD of C, T, EVD of T). s <= 256. Working sets live in
-// shared memory when they fit (s <= 88), otherwise in a global scratch area.
+// shared memory when they fit (s <= 88), otherwise in a global scratch area, except the
+// Cholesky factor of k_chol_drop and the two FP32 Jacobi matrices of the EVDs, which stay in
+// shared memory up to s = 160.
 //
 // Symmetric EVD: cyclic Jacobi (rotation of pair (p, q) from Golub & Van Loan's 2x2
 // symmetric Schur decomposition: tau = (a_qq - a_pp)/(2 a_pq), t = sign(tau)/(|tau| +
@@ -110,7 +112,7 @@ __device__ void jacobi(F *A, F *V, int s, int ld, int max_sweeps, F tol, F floor
   __shared__ int pp[128], qq[128];
   __shared__ int any;
   __shared__ F fro_sh;
-  __shared__ float red[CT];
+  __shared__ float red[CT / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   {  // ||A||_F (rotations keep it): off-diagonal entries below floor_rel ||A||_F are final
     float acc = 0.0f;
@@ -118,13 +120,15 @@ __device__ void jacobi(F *A, F *V, int s, int ld, int max_sweeps, F tol, F floor
       const float a = (float)A[(e / s) * ld + e % s];
       acc += a * a;
     }
-    red[tid] = acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+    if (lane == 0) red[warp] = acc;
     __syncthreads();
-    for (int h = CT / 2; h > 0; h >>= 1) {
-      if (tid < h) red[tid] += red[tid + h];
-      __syncthreads();
+    if (tid == 0) {
+      float t = 0.0f;
+      for (int w = 0; w < CT / 32; ++w) t += red[w];
+      fro_sh = (F)sqrtf(t);
     }
-    if (tid == 0) fro_sh = (F)sqrtf(red[0]);
     __syncthreads();
   }
   const F floor_abs = floor_rel * fro_sh;
@@ -265,11 +269,15 @@ __device__ void mgs_columns(double *V, int s, double *W) {
 // FP64-accurate EVD of the symmetric matrix held in Bm (s x s): on return the eigenvalues
 // are on the diagonal of Bm and the eigenvectors in the columns of V. W1 is s x s scratch,
 // also used for the two FP32 matrices of the first phase. All three may be shared memory.
-__device__ void eig_sym(double *Bm, int s, double *V, double *W1, bool polish) {
+// jac (may be null): shared memory for the two FP32 matrices of the first phase (2 s (s|1)
+// floats), used when the s x s FP64 buffers themselves are in global memory.
+__device__ void eig_sym(double *Bm, int s, double *V, double *W1, bool polish,
+                        float *jac = nullptr) {
   const int tid = threadIdx.x;
   const size_t ss = (size_t)s * s;
   const int ld = s | 1;  // odd leading dimension of the FP32 phase (s x ld floats fit in s x s doubles)
-  float *A32 = reinterpret_cast<float *>(W1), *V32 = reinterpret_cast<float *>(V);
+  float *A32 = jac ? jac : reinterpret_cast<float *>(W1);
+  float *V32 = jac ? jac + (size_t)s * ld : reinterpret_cast<float *>(V);
   for (size_t e = tid; e < ss; e += CT) {
     const int i = e / s, j = e % s;
     A32[i * ld + j] = (float)Bm[e];
@@ -277,13 +285,17 @@ __device__ void eig_sym(double *Bm, int s, double *V, double *W1, bool polish) {
   }
   __syncthreads();
   jacobi<float>(A32, V32, s, ld, 8, 1e-6f, 2e-7f);
-  float *T32 = A32;  // A32 is no longer needed: V32 moves there before V is widened in place
-  for (size_t e = tid; e < ss; e += CT) {
-    const int i = e / s, j = e % s;
-    T32[i * ld + j] = V32[i * ld + j];
+  if (jac) {
+    for (size_t e = tid; e < ss; e += CT) V[e] = (double)V32[(e / s) * ld + e % s];
+  } else {
+    float *T32 = A32;  // A32 is no longer needed: V32 moves there before V is widened in place
+    for (size_t e = tid; e < ss; e += CT) {
+      const int i = e / s, j = e % s;
+      T32[i * ld + j] = V32[i * ld + j];
+    }
+    __syncthreads();
+    for (size_t e = tid; e < ss; e += CT) V[e] = (double)T32[(e / s) * ld + e % s];
   }
-  __syncthreads();
-  for (size_t e = tid; e < ss; e += CT) V[e] = (double)T32[(e / s) * ld + e % s];
   __syncthreads();
   mgs_columns(V, s, W1);
   // W1 = C V ; Bm = V^T W1 (symmetric: upper triangle computed, mirrored)
@@ -303,8 +315,11 @@ struct Scratch {
   double *b0, *b1, *b2;  // three s x s buffers (smem or global)
 };
 
-__device__ Scratch scratch(double *smem, double *global, int s, bool use_smem) {
+// use_smem: 1 = all three buffers in shared memory, 2 = only b0 (the factor being
+// decomposed) in shared memory, 0 = all in global memory
+__device__ Scratch scratch(double *smem, double *global, int s, int use_smem) {
   const size_t ss = (size_t)s * s;
+  if (use_smem == 2) return Scratch{smem, global + ss, global + 2 * ss};
   double *base = use_smem ? smem : global;
   return Scratch{base, base + ss, base + 2 * ss};
 }
@@ -412,7 +427,7 @@ __global__ void k_sqrt_vec(const double *in, int s, double *out) {
 __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C, int s, int k,
                                                 double eps_rel, double drop_tol, double *Mix,
                                                 double *Sigma, int32_t *rank, double *gw,
-                                                int use_smem, int polish) {
+                                                int use_smem, int polish, int jac_smem) {
   extern __shared__ __align__(16) double dsm[];
   __shared__ int nk, r_keep;
   __shared__ int32_t msk[256], keepc[256], order[256];
@@ -449,7 +464,7 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   for (size_t i = tid; i < ss; i += CT) gRf[i] = S.b0[i];
   // step 6: symmetric C into b0
   __shared__ int c_ok;
-  __shared__ double red2[CT];
+  __shared__ double red2[CT / 32];
   for (size_t idx = tid; idx < ss; idx += CT) {
     const int i = idx / s, j = idx % s;
     S.b0[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
@@ -467,16 +482,15 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   {
     double a = 0.0;
     for (size_t i = tid; i < ss; i += CT) a += S.b1[i] * S.b1[i];
-    red2[tid] = a;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(FULL, a, o);
+    if ((tid & 31) == 0) red2[tid >> 5] = a;
     __syncthreads();
-    for (int h = CT / 2; h > 0; h >>= 1) {
-      if (tid < h) red2[tid] += red2[tid + h];
-      __syncthreads();
-    }
     if (tid == 0) {
-      double tr = 0.0;
+      double fro2 = 0.0, tr = 0.0;
+      for (int w = 0; w < CT / 32; ++w) fro2 += red2[w];
       for (int i = 0; i < s; ++i) tr += diag0[i];
-      c_ok = r_keep == s && tr > 0.0 && 1.0 / red2[0] >= eps_rel * tr;
+      c_ok = r_keep == s && tr > 0.0 && 1.0 / fro2 >= eps_rel * tr;
     }
     __syncthreads();
   }
@@ -507,7 +521,7 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
       S.b0[idx] = 0.5 * (C[i * s + j] + C[j * s + i]);
     }
     __syncthreads();
-    eig_sym(S.b0, s, S.b1, S.b2, polish != 0);
+    eig_sym(S.b0, s, S.b1, S.b2, polish != 0, jac_smem ? reinterpret_cast<float *>(dsm) : nullptr);
     if (tid == 0) {
       double dmax = 0.0;
       for (int j = 0; j < s; ++j) dmax = fmax(dmax, S.b0[j * s + j]);
@@ -544,7 +558,7 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
   for (size_t i = tid; i < ss; i += CT) S.b0[i] = S.b1[i];
   __syncthreads();
   // step 9: EVD of T: eigenvalues on b0's diagonal, W in b1
-  eig_sym(S.b0, s, S.b1, S.b2, polish != 0);
+  eig_sym(S.b0, s, S.b1, S.b2, polish != 0, jac_smem ? reinterpret_cast<float *>(dsm) : nullptr);
   for (int j = tid; j < s; j += CT) {
     evals[j] = S.b0[j * s + j];
     order[j] = j;
@@ -582,6 +596,17 @@ __global__ void __launch_bounds__(CT) k_nystrom(const double *K, const double *C
 }
 
 size_t smem_for(int s) { return s <= SMEM_S ? 3 * (size_t)s * s * sizeof(double) : 0; }
+// above SMEM_S: shared memory for one s x s FP64 factor (Cholesky kernels), or for the two
+// FP32 Jacobi matrices (Nyström core), when it fits in 210 KiB
+constexpr size_t kCoreSmemMax = 206 * 1024;
+size_t smem_factor(int s) {
+  const size_t b = (size_t)s * s * sizeof(double);
+  return s > SMEM_S && b <= kCoreSmemMax ? b : 0;
+}
+size_t smem_jacobi(int s) {
+  const size_t b = 2 * (size_t)s * (size_t)(s | 1) * sizeof(float);
+  return s > SMEM_S && b <= kCoreSmemMax ? b : 0;
+}
 
 template <typename K>
 void set_smem(K kernel, size_t bytes) {
@@ -594,9 +619,11 @@ size_t core_work_size(int s) { return 3 * (size_t)s * s + 64; }
 
 void launch_chol_drop(const double *C, int s, double drop_tol, double *Rinv, int32_t *mask,
                       int32_t *nkept, double *gwork, cudaStream_t stream, int batch) {
-  const size_t sm = smem_for(s);
+  size_t sm = smem_for(s);
+  int mode = sm > 0 ? 1 : 0;
+  if (!sm && (sm = smem_factor(s)) > 0) mode = 2;
   set_smem(k_chol_drop, sm);
-  k_chol_drop<<<batch, CT, sm, stream>>>(C, s, drop_tol, Rinv, mask, nkept, gwork, sm > 0);
+  k_chol_drop<<<batch, CT, sm, stream>>>(C, s, drop_tol, Rinv, mask, nkept, gwork, mode);
   NSP_LAUNCH_CHECK();
 }
 
@@ -625,10 +652,12 @@ size_t nystrom_work_size(int s) { return 5 * (size_t)s * s + 64; }
 void launch_nystrom_core(const double *K, const double *C, int s, int k, double eps_rel,
                          double drop_tol, double *Mix, double *Sigma, int32_t *rank,
                          double *work, cudaStream_t stream, int batch, int polish) {
-  const size_t sm = smem_for(s);
+  size_t sm = smem_for(s);
+  int jac = 0;
+  if (!sm && (sm = smem_jacobi(s)) > 0) jac = 1;
   set_smem(k_nystrom, sm);
   k_nystrom<<<batch, CT, sm, stream>>>(K, C, s, k, eps_rel, drop_tol, Mix, Sigma, rank, work,
-                                       sm > 0, polish);
+                                       jac ? 0 : (sm > 0), polish, jac);
   NSP_LAUNCH_CHECK();
 }
 

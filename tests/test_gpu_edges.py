@@ -56,6 +56,22 @@ def test_widest_sketch_block(N, torch):
     h.destroy()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_core_widths_with_shared_memory_factor(N, torch, prec):
+    # s = 136 (88 < s <= 160): the s x s Cholesky factor of the block-PCG steps and the FP32
+    # Jacobi matrices of the Nyström core live in shared memory, the other s x s buffers in
+    # global memory
+    A, part, _ = tiny_problem((70, 70), 16, (3.0, 1.0), seed=4)
+    h, D, M = _parity(N, torch, A, part, 16, 120, 16, prec=prec)
+    Z, S = h.get_basis()
+    if prec == "fp64":
+        assert np.allclose(S, M.Sigma, rtol=1e-7)
+        assert operator_err(Z, S, M.Z, M.Sigma) < 1e-5
+    else:
+        assert np.allclose(S, M.Sigma, rtol=1e-2)
+    h.destroy()
+
+
 def test_single_interior_block(N, torch):
     shape = (18, 14)
     A = F.diffusion_matrix(shape)
