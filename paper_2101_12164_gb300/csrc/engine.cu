@@ -374,6 +374,10 @@ struct ForestData {
     DBuf<int32_t> item_a, item_b, group_sn, sn_parent, need_f, units_f, units_b;
     DBuf<uint32_t> counters;  // cnt_f, self_f, done_b (nsn each), claim, abort, epoch, base
     DBuf<int32_t> res_blk_ptr, res_lvl_ptr, res_lvl_nwarp, res_job;   // block-resident schedule
+    DBuf<int64_t> vs_row_off;                                        // vector plans
+    DBuf<int32_t> vs_lvl_ptr, vs_bat_ptr, vs_pfvi, vs_pbvi, vs_pptr, vs_psrc;
+    DBuf<uint16_t> vs_pitem, vs_uitem, vs_citem;
+    DBuf<int4> vs_bat, vs_item;
     int32_t maxneed = 1;
     // right-hand-side count -> persistent grid of the dependency-driven sweep, or
     // kResidentGrid for the block-resident sweep (autotuner)
@@ -381,6 +385,7 @@ struct ForestData {
   };
   std::unique_ptr<Plan> plans[2];  // 0: block (s > 1), 1: vector (s = 1)
   int vec_rows = 128;
+  int elem_bytes = 4;   // element size of the handle (shared-memory sweep budget)
 
   Plan &plan(bool vector, cudaStream_t st) {
     auto &pp = plans[vector ? 1 : 0];
@@ -548,8 +553,207 @@ struct ForestData {
       P.d.res_lvl_ptr = P.res_lvl_ptr.p;
       P.d.res_lvl_nwarp = P.res_lvl_nwarp.p;
       P.d.res_job = P.res_job.p;
+      // shared-memory single-vector sweep: per-block row and update-row ranges (every index a
+      // block's supernodes touch must stay inside them) and, per height, batches of
+      // supernodes whose fronts and K-split partial sums fit the scratch
+      if (vector && nb > 0) build_vsm(P, bl, st);
     }
     return P;
+  }
+
+  // Batches of the shared-memory single-vector sweep (k_vsweep.cu) from the per-block,
+  // per-height supernode lists bl, for elements of elem_bytes. Each block's update rows live
+  // in a shared-memory pool: supernode J's rows occupy a slot from its height to its
+  // parent's height (inclusive), allocated first-fit in height order, so the pool holds the
+  // largest live set rather than every update row. Forward units: (K group, 4-row group)
+  // pairs, K split into ceil(w / 48) groups (at most kVsmKG); backward units: columns. The
+  // scratch of a batch (fronts, then the K groups' partial sums) takes what shared memory
+  // leaves, two CTAs per SM where that leaves at least kVsmScratch entries.
+  void build_vsm(Plan &P, const std::vector<std::vector<std::vector<int32_t>>> &bl,
+                 cudaStream_t st) {
+    const int nb = h.nblocks, nsn = h.nsn;
+    const int64_t eb = elem_bytes;
+    std::vector<int64_t> roff(nb + 1);
+    for (int b = 0; b <= nb; ++b) roff[b] = h.block_off[b];
+    // owner of every update row, and the containment checks
+    std::vector<int32_t> owner(h.upd_rows > 0 ? h.upd_rows : 1, -1);
+    for (int J = 0; J < nsn; ++J)
+      for (int64_t i = 0; i < h.sn_m[J] - h.sn_w[J]; ++i) owner[h.sn_upd[J] + i] = J;
+    bool ok = true;
+    int ldmax = 4;
+    for (int J = 0; J < nsn && ok; ++J) {
+      const int b = h.sn_block[J];
+      const int64_t rp = h.sn_rowptr[J];
+      ldmax = std::max(ldmax, (int)panel_ld(h.sn_m[J]));
+      if (h.sn_first[J] < roff[b] || h.sn_first[J] + h.sn_w[J] > roff[b + 1]) ok = false;
+      for (int k = 0; k < h.sn_m[J] && ok; ++k) {
+        if (k >= h.sn_w[J] && (h.rows[rp + k] < roff[b] || h.rows[rp + k] >= roff[b + 1]))
+          ok = false;
+        for (int64_t e = h.gptr[rp + k]; e < h.gptr[rp + k + 1]; ++e) {
+          const int64_t g = h.gsrc[e];
+          if (g < 0 || g >= h.upd_rows || owner[g] < 0 || h.sn_block[owner[g]] != b ||
+              h.sn_parent[owner[g]] != J)
+            ok = false;
+        }
+      }
+    }
+    if (!ok) return;
+    // update-row slots per block: live from height(J) to height(parent(J))
+    std::vector<int32_t> uslot(nsn, 0);
+    std::vector<int64_t> pool(nb, 0);
+    for (int b = 0; b < nb; ++b) {
+      std::vector<std::pair<int32_t, int32_t>> fr;   // free intervals [start, end), sorted
+      int32_t top = 0;
+      std::vector<std::vector<int32_t>> release(bl[b].size() + 1);
+      for (size_t l = 0; l < bl[b].size(); ++l) {
+        for (int J : bl[b][l]) {
+          const int32_t sz = h.sn_m[J] - h.sn_w[J];
+          const int par = h.sn_parent[J];
+          if (sz <= 0 || par < 0) continue;
+          int32_t at = -1;
+          for (auto &iv : fr)
+            if (iv.second - iv.first >= sz) {
+              at = iv.first;
+              iv.first += sz;
+              break;
+            }
+          if (at < 0) {
+            at = top;
+            top += sz;
+          }
+          uslot[J] = at;
+          release[std::min<size_t>(h.sn_level[par], bl[b].size())].push_back(J);
+        }
+        // slots whose last reader is this height become free for the next height
+        for (int J : release[l]) {
+          fr.push_back({uslot[J], uslot[J] + h.sn_m[J] - h.sn_w[J]});
+        }
+        std::sort(fr.begin(), fr.end());
+        std::vector<std::pair<int32_t, int32_t>> merged;
+        for (auto &iv : fr) {
+          if (iv.first >= iv.second) continue;
+          if (!merged.empty() && merged.back().second == iv.first) merged.back().second = iv.second;
+          else merged.push_back(iv);
+        }
+        fr.swap(merged);
+      }
+      pool[b] = top;
+    }
+    int64_t vu = 0;
+    for (int b = 0; b < nb; ++b)
+      vu = std::max(vu, ((roff[b + 1] - roff[b] + 3) & ~int64_t(3)) + ((pool[b] + 3) & ~int64_t(3)));
+    auto kg_of = [&](int J) { return std::min(kVsmKG, std::max(1, (h.sn_w[J] + 47) / 48)); };
+    int need_max = 4;
+    for (int J = 0; J < nsn; ++J) {
+      const int ld = (int)panel_ld(h.sn_m[J]), kg = kg_of(J);
+      need_max = std::max(need_max, ld + (kg > 1 ? kg * ld : 0));
+    }
+    int dev = 0, optin = 0, per_sm = 0;
+    NSP_CUDA(cudaGetDevice(&dev));
+    NSP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    NSP_CUDA(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    const int64_t two = ((int64_t)(per_sm / 2 - 1024) / eb - vu) & ~int64_t(3);
+    const int64_t one = ((int64_t)optin / eb - vu) & ~int64_t(3);
+    int64_t scr;
+    if (two >= std::max<int64_t>(need_max, kVsmScratch)) scr = two;
+    else if (one >= need_max) scr = std::min<int64_t>(one, 8 * (int64_t)kVsmScratch);
+    else return;
+    scr = std::min<int64_t>(scr, 1 << 20);
+    // flat per-batch arrays: per front position (fronts of a batch back to back, ld entries
+    // each) the forward v index (top rows, else -1), the backward source (v index of y_J, or
+    // -2 - v index of x for a row below, or -1 for padding), the item (relative to the
+    // batch's first) and the gather sources (pool slots, by position); per forward unit and
+    // per backward column the item
+    std::vector<int32_t> lvl(1, 0), bptr(1, 0), pfvi, pbvi, pptr(1, 0), psrc;
+    std::vector<uint16_t> pitem, uitem, citem;
+    std::vector<int4> bat, item;
+    for (int b = 0; b < nb; ++b) {
+      for (const auto &lev : bl[b]) {
+        if (lev.empty()) continue;
+        std::vector<int32_t> cur;
+        int64_t nf = 0, red = 0;
+        auto close = [&]() {
+          if (cur.empty()) return;
+          const int i0 = (int)item.size() / 4;
+          const int pos_base = (int)pfvi.size(), unit_base = (int)uitem.size(),
+                    col_base = (int)citem.size();
+          int fo = 0, ro = 0, uf = 0, ub = 0, any_red = 0;
+          for (size_t t = 0; t < cur.size(); ++t) {
+            const int J = cur[t], m = h.sn_m[J], w = h.sn_w[J], ld = (int)panel_ld(m);
+            const int kg = kg_of(J);
+            const int64_t rp = h.sn_rowptr[J], po = h.sn_panel[J];
+            const int fl = (int)(h.sn_first[J] - roff[b]);
+            item.push_back(int4{fo, kg > 1 ? ro : -1, kg, uslot[J]});
+            item.push_back(int4{uf, ub, m, w});
+            item.push_back(int4{fl, (int)(rp & 0xffffffff), (int)(rp >> 32), (int)(po & 0xffffffff)});
+            item.push_back(int4{(int)(po >> 32), J, 0, 0});
+            for (int k = 0; k < ld; ++k) {
+              pfvi.push_back(k < w ? fl + k : -1);
+              pbvi.push_back(k < w ? fl + k : k < m ? -2 - (int32_t)(h.rows[rp + k] - roff[b]) : -1);
+              pitem.push_back((uint16_t)t);
+              if (k < m)
+                for (int64_t e = h.gptr[rp + k]; e < h.gptr[rp + k + 1]; ++e) {
+                  const int64_t g = h.gsrc[e];
+                  const int C = owner[g];
+                  psrc.push_back(uslot[C] + (int32_t)(g - h.sn_upd[C]));
+                }
+              pptr.push_back((int32_t)psrc.size());
+            }
+            for (int q = 0; q < kg * (ld / 4); ++q) uitem.push_back((uint16_t)t);
+            for (int q = 0; q < w; ++q) citem.push_back((uint16_t)t);
+            fo += ld;
+            if (kg > 1) { ro += kg * ld; any_red = 1; }
+            uf += kg * (ld / 4);
+            ub += w;
+          }
+          bat.push_back(int4{i0, i0 + (int)cur.size(), fo, uf});
+          bat.push_back(int4{ub, any_red, pos_base, unit_base});
+          bat.push_back(int4{col_base, 0, 0, 0});
+          cur.clear();
+          nf = 0;
+          red = 0;
+        };
+        for (int J : lev) {
+          const int ld = (int)panel_ld(h.sn_m[J]), kg = kg_of(J);
+          const int need = ld + (kg > 1 ? kg * ld : 0);
+          if (nf + red + need > scr || cur.size() >= 65535) close();
+          cur.push_back(J);
+          nf += ld;
+          if (kg > 1) red += (int64_t)kg * ld;
+        }
+        close();
+        bptr.push_back((int)bat.size() / 3);
+      }
+      lvl.push_back((int)bptr.size() - 1);
+    }
+    if (item.empty() || psrc.size() >= (size_t)INT32_MAX || pfvi.size() >= (size_t)INT32_MAX) return;
+    if (psrc.empty()) psrc.push_back(0);
+    P.vs_row_off.upload(roff, st);
+    P.vs_lvl_ptr.upload(lvl, st);
+    P.vs_bat_ptr.upload(bptr, st);
+    P.vs_bat.upload(bat, st);
+    P.vs_item.upload(item, st);
+    P.vs_pfvi.upload(pfvi, st);
+    P.vs_pbvi.upload(pbvi, st);
+    P.vs_pptr.upload(pptr, st);
+    P.vs_psrc.upload(psrc, st);
+    P.vs_pitem.upload(pitem, st);
+    P.vs_uitem.upload(uitem, st);
+    P.vs_citem.upload(citem, st);
+    P.d.vs_row_off = P.vs_row_off.p;
+    P.d.vs_lvl_ptr = P.vs_lvl_ptr.p;
+    P.d.vs_bat_ptr = P.vs_bat_ptr.p;
+    P.d.vs_bat = P.vs_bat.p;
+    P.d.vs_item = P.vs_item.p;
+    P.d.vs_pfvi = P.vs_pfvi.p;
+    P.d.vs_pbvi = P.vs_pbvi.p;
+    P.d.vs_pptr = P.vs_pptr.p;
+    P.d.vs_psrc = P.vs_psrc.p;
+    P.d.vs_pitem = P.vs_pitem.p;
+    P.d.vs_uitem = P.vs_uitem.p;
+    P.d.vs_citem = P.vs_citem.p;
+    P.d.vs_elems = vu;
+    P.d.vs_scratch = (int32_t)scr;
   }
 
   void upload(cudaStream_t st) {
@@ -774,29 +978,41 @@ struct Engine : EngineBase {
   void solve_forest(ForestData &F, const T *panel, const T *B, T *Ywk, T *Uwk, T *X, int sc,
                     bool tune = true) {
     F.vec_rows = sweep_vector_rows((int)sizeof(T));
+    F.elem_bytes = (int)sizeof(T);
     auto &P = F.plan(sc == 1, st);
     int grid = 0;
     auto it = P.tuned_grid.find(sc);
     if (const int forced = forced_scheduler(); forced != 0) {
-      grid = forced > 0 ? 0 : kResidentGrid;
-      if (grid == kResidentGrid && F.h.nblocks < 2) grid = 0;
+      grid = forced > 0 ? 0 : forced == -2 ? kVsmGrid - 1 : kResidentGrid;
     } else if (it != P.tuned_grid.end()) {
       grid = it->second;
     } else if (tune && autotune_enabled() && !capturing()) {
       grid = tune_sweep(F, P, panel, B, Ywk, Uwk, X, sc);
       P.tuned_grid[sc] = grid;
     }
-    if (grid == kResidentGrid)
+    if (grid <= kVsmGrid) {   // kVsmGrid - 1 + c: c CTAs per SM
+      const int fits = sc == 1 ? vsm_sweep_fits<T>(P.d) : 0;
+      grid = fits == 0 ? kResidentGrid : std::max(grid, kVsmGrid - fits + 1);
+    }
+    if (grid == kResidentGrid && F.h.nblocks < 2) grid = 0;
+    if (grid <= kVsmGrid)
+      launch_vsm_sweep<T>(F.dev, P.d, panel, B, X, kVsmGrid - grid + 1, st);
+    else if (grid == kResidentGrid)
       launch_res_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st);
     else
       launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, grid);
   }
-  static constexpr int kResidentGrid = -1;
-  // NSP_SWEEP=resident / global forces one scheduler (measurements); unset: the autotuner
+  // grid codes besides persistent grid sizes: the block-resident sweep, and the shared-memory
+  // single-vector sweep with one (kVsmGrid) or two (kVsmGrid - 1) CTAs per SM
+  static constexpr int kResidentGrid = -1, kVsmGrid = -2;
+  // NSP_SWEEP=resident / global / smem forces one scheduler (measurements; smem: the
+  // shared-memory single-vector sweep where it fits, with as many CTAs per SM as fit, else
+  // resident); unset: the autotuner
   static int forced_scheduler() {
     const char *e = std::getenv("NSP_SWEEP");
     if (!e) return 0;
     if (e[0] == 'r') return -1;
+    if (e[0] == 's') return -2;
     if (e[0] == 'g') return 1;
     return 0;
   }
@@ -839,6 +1055,24 @@ struct Engine : EngineBase {
       tune_log.push_back({kResidentGrid, tot / 2});
       best_ms = tot;
       best = kResidentGrid;
+    }
+    const int vfits = (sc == 1 && F.h.nblocks >= 2) ? vsm_sweep_fits<T>(P.d) : 0;
+    for (int per_sm = 1; per_sm <= vfits; ++per_sm) {
+      float tot = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        NSP_CUDA(cudaEventRecord(e0, st));
+        launch_vsm_sweep<T>(F.dev, P.d, panel, B, X, per_sm, st);
+        NSP_CUDA(cudaEventRecord(e1, st));
+        NSP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+      }
+      tune_log.push_back({kVsmGrid - per_sm + 1, tot / 2});
+      if (tot < best_ms) {
+        best_ms = tot;
+        best = kVsmGrid - per_sm + 1;
+      }
     }
     for (int g = sms; g <= gmax; g += sms) {
       float tot = 0.f;
@@ -1726,6 +1960,7 @@ struct Engine : EngineBase {
   // record DEV_TIMEOUT. The plan's counters and the status word are then reset, so the
   // handle stays usable. Returns the status the sweep reported.
   nsp_status timeout_selftest(int max_spins) override {
+    FI.elem_bytes = (int)sizeof(T);
     auto &P = FI.plan(true, st);
     ensure_ws(1);
     sT.ensure(std::max(an.nI, an.nG));

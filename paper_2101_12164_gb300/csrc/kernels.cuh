@@ -50,6 +50,27 @@ struct SweepPlan {
   int32_t res_nblocks = 0;
   const int32_t *res_blk_ptr = nullptr, *res_lvl_ptr = nullptr, *res_lvl_nwarp = nullptr,
                 *res_job = nullptr;
+  // Vector plans, shared-memory sweep (k_vsweep.cu): block b's rows [vs_row_off[b],
+  // vs_row_off[b+1]); its heights [vs_lvl_ptr[b], vs_lvl_ptr[b+1]), height L's batches
+  // [vs_bat_ptr[L], vs_bat_ptr[L+1]). Batch q (vs_bat[3q..3q+2]): {first item, end item,
+  // front entries, forward units}, {backward columns, any K-split item, first position,
+  // first forward unit}, {first backward column, 0, 0, 0}. Item i (vs_item[4i..4i+3]):
+  // {front offset, partial-sum offset, K groups, update-row slot}, {first forward unit,
+  // first backward column, m, w}, {first row in the block, sn_rowptr low, high, sn_panel low},
+  // {sn_panel high, supernode, 0, 0} (offsets within the batch). Per front position (all
+  // batches back to back): vs_pfvi forward v index (-1: none), vs_pbvi backward source (v
+  // index of y_J; -2 - v index of x for a row below; -1: padding), vs_pitem item (relative),
+  // vs_pptr / vs_psrc its gather sources as slots of the block's shared-memory update-row
+  // pool. vs_uitem / vs_citem: the item of each forward unit / backward column. vs_elems =
+  // the largest block's rows + pool, each rounded up to 4 (0: no shared-memory sweep);
+  // vs_scratch = scratch entries per batch.
+  const int64_t *vs_row_off = nullptr;
+  const int32_t *vs_lvl_ptr = nullptr, *vs_bat_ptr = nullptr;
+  const int4 *vs_bat = nullptr, *vs_item = nullptr;
+  const int32_t *vs_pfvi = nullptr, *vs_pbvi = nullptr, *vs_pptr = nullptr, *vs_psrc = nullptr;
+  const uint16_t *vs_pitem = nullptr, *vs_uitem = nullptr, *vs_citem = nullptr;
+  int64_t vs_elems = 0;
+  int32_t vs_scratch = 0;
 };
 
 // ---- numeric factorization (k_factor.cu) -----------------------------------------
@@ -84,6 +105,17 @@ template <typename T>
 void launch_res_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y,
                       T *U, T *X, int s, DevStatus *st, cudaStream_t stream);
 constexpr int kResW = 32, kResM = 128;   // block mode: supernodes a warp runs (w, m bounds)
+// One right-hand side with each block's vectors (b, y, x in place, and its update rows) in
+// shared memory, one CTA per block of the vector plan's block-resident schedule; B, X in the
+// forest's internal order. vsm_sweep_fits: how many CTAs per SM (2, 1; 0: none) the largest
+// block's shared memory allows; per_sm (1 or 2, at most that) selects the register budget.
+constexpr int kVsmKG = 8;          // forward K groups of a CTA-sized supernode
+constexpr int kVsmScratch = 4096;  // default scratch entries per batch (fronts + partials)
+template <typename T>
+int vsm_sweep_fits(const SweepPlan &p);
+template <typename T>
+void launch_vsm_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *X,
+                      int per_sm, cudaStream_t stream);
 // rows of a forward tile in vector mode for elements of elem_bytes
 int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
