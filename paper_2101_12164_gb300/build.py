@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libnsp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["engine.cu", "k_factor.cu", "k_solve.cu", "k_rsweep.cu", "k_vsweep.cu", "k_tc.cu", "k_blas.cu", "k_core.cu", "k_batch.cu", "net.cu",
+SOURCES = ["engine.cu", "k_factor.cu", "k_solve.cu", "k_rsweep.cu", "k_vsweep.cu", "k_bsweep.cu", "k_tc.cu", "k_blas.cu", "k_core.cu", "k_batch.cu", "net.cu",
            "symbolic.cpp"]
 
 

@@ -377,6 +377,9 @@ struct ForestData {
     DBuf<int64_t> vs_row_off;                                        // vector plans
     DBuf<int32_t> vs_lvl_ptr, vs_bat_ptr, vs_pfvi, vs_pbvi, vs_pptr, vs_psrc;
     DBuf<uint16_t> vs_pitem, vs_uitem, vs_citem;
+    DBuf<int32_t> bs_lvl_ptr, bs_bat_ptr, bs_pfvi, bs_pbvi, bs_pptr, bs_psrc;   // block plans
+    DBuf<int4> bs_bat, bs_item;
+    DBuf<uint16_t> bs_uitem, bs_citem;
     DBuf<int4> vs_bat, vs_item;
     int32_t maxneed = 1;
     // right-hand-side count -> persistent grid of the dependency-driven sweep, or
@@ -557,8 +560,102 @@ struct ForestData {
       // block's supernodes touch must stay inside them) and, per height, batches of
       // supernodes whose fronts and K-split partial sums fit the scratch
       if (vector && nb > 0) build_vsm(P, bl, st);
+      if (!vector && nb > 0) build_bsm(P, bl, st);
     }
     return P;
+  }
+
+  // Batches of the column-sliced block sweep (k_bsweep.cu) from the per-block, per-height
+  // supernode lists bl: each batch's fronts (positions x kBsmCols elements of elem_bytes)
+  // fit kBsmScratchBytes. Per front position the B row (forward, top rows), the Y / X source
+  // (backward) and the gather sources (update rows); forward units (4-row group, 8-column
+  // group), backward units (4 panel columns, 8-column group).
+  void build_bsm(Plan &P, const std::vector<std::vector<std::vector<int32_t>>> &bl,
+                 cudaStream_t st) {
+    const int nb = h.nblocks;
+    const int maxpos = kBsmScratchBytes / (kBsmCols * elem_bytes);
+    if (h.n >= INT32_MAX - 2 || h.upd_rows >= INT32_MAX || (int64_t)h.gsrc.size() >= INT32_MAX)
+      return;
+    for (int J = 0; J < h.nsn; ++J)
+      if ((int)panel_ld(h.sn_m[J]) > maxpos) return;
+    std::vector<int32_t> lvl(1, 0), bptr(1, 0), pfvi, pbvi, pptr(1, 0), psrc;
+    std::vector<uint16_t> uitem, citem;
+    std::vector<int4> bat, item;
+    int positions = 0;
+    for (int b = 0; b < nb; ++b) {
+      for (const auto &lev : bl[b]) {
+        if (lev.empty()) continue;
+        std::vector<int32_t> cur;
+        int nf = 0;
+        auto close = [&]() {
+          if (cur.empty()) return;
+          const int i0 = (int)item.size() / 3;
+          const int pos_base = (int)pfvi.size(), unit_base = (int)uitem.size(),
+                    col_base = (int)citem.size();
+          int fo = 0, uf = 0, ub = 0;
+          for (size_t t = 0; t < cur.size(); ++t) {
+            const int J = cur[t], m = h.sn_m[J], w = h.sn_w[J], ld = (int)panel_ld(m);
+            const int64_t rp = h.sn_rowptr[J], po = h.sn_panel[J];
+            const int first = (int)h.sn_first[J], upd = (int)h.sn_upd[J];
+            item.push_back(int4{fo, uf, ub, m});
+            item.push_back(int4{w, first, upd, 0});
+            item.push_back(int4{(int)(po & 0xffffffff), (int)(po >> 32), 0, 0});
+            for (int k = 0; k < ld; ++k) {
+              pfvi.push_back(k < w ? first + k : -1);
+              pbvi.push_back(k < w ? first + k : k < m ? -2 - h.rows[rp + k] : -1);
+              if (k < m)
+                for (int64_t e = h.gptr[rp + k]; e < h.gptr[rp + k + 1]; ++e)
+                  psrc.push_back((int32_t)h.gsrc[e]);
+              pptr.push_back((int32_t)psrc.size());
+            }
+            const int nuf = (ld / 4) * 4, nub = ((w + 3) / 4) * 4;
+            for (int q = 0; q < nuf; ++q) uitem.push_back((uint16_t)t);
+            for (int q = 0; q < nub; ++q) citem.push_back((uint16_t)t);
+            fo += ld;
+            uf += nuf;
+            ub += nub;
+          }
+          positions = std::max(positions, fo);
+          bat.push_back(int4{i0, i0 + (int)cur.size(), fo, uf});
+          bat.push_back(int4{ub, 0, pos_base, unit_base});
+          bat.push_back(int4{col_base, 0, 0, 0});
+          cur.clear();
+          nf = 0;
+        };
+        for (int J : lev) {
+          const int ld = (int)panel_ld(h.sn_m[J]);
+          if (nf + ld > maxpos || cur.size() >= 65535) close();
+          cur.push_back(J);
+          nf += ld;
+        }
+        close();
+        bptr.push_back((int)bat.size() / 3);
+      }
+      lvl.push_back((int)bptr.size() - 1);
+    }
+    if (item.empty() || pfvi.size() >= (size_t)INT32_MAX || psrc.size() >= (size_t)INT32_MAX) return;
+    if (psrc.empty()) psrc.push_back(0);
+    P.bs_lvl_ptr.upload(lvl, st);
+    P.bs_bat_ptr.upload(bptr, st);
+    P.bs_bat.upload(bat, st);
+    P.bs_item.upload(item, st);
+    P.bs_pfvi.upload(pfvi, st);
+    P.bs_pbvi.upload(pbvi, st);
+    P.bs_pptr.upload(pptr, st);
+    P.bs_psrc.upload(psrc, st);
+    P.bs_uitem.upload(uitem, st);
+    P.bs_citem.upload(citem, st);
+    P.d.bs_lvl_ptr = P.bs_lvl_ptr.p;
+    P.d.bs_bat_ptr = P.bs_bat_ptr.p;
+    P.d.bs_bat = P.bs_bat.p;
+    P.d.bs_item = P.bs_item.p;
+    P.d.bs_pfvi = P.bs_pfvi.p;
+    P.d.bs_pbvi = P.bs_pbvi.p;
+    P.d.bs_pptr = P.bs_pptr.p;
+    P.d.bs_psrc = P.bs_psrc.p;
+    P.d.bs_uitem = P.bs_uitem.p;
+    P.d.bs_citem = P.bs_citem.p;
+    P.d.bs_positions = positions;
   }
 
   // Batches of the shared-memory single-vector sweep (k_vsweep.cu) from the per-block,
@@ -983,12 +1080,17 @@ struct Engine : EngineBase {
     int grid = 0;
     auto it = P.tuned_grid.find(sc);
     if (const int forced = forced_scheduler(); forced != 0) {
-      grid = forced > 0 ? 0 : forced == -2 ? kVsmGrid - 1 : kResidentGrid;
+      grid = forced > 0 ? 0 : forced == -2 ? (sc == 1 ? kVsmGrid - 1 : kBsmGrid) : kResidentGrid;
     } else if (it != P.tuned_grid.end()) {
       grid = it->second;
     } else if (tune && autotune_enabled() && !capturing()) {
       grid = tune_sweep(F, P, panel, B, Ywk, Uwk, X, sc);
       P.tuned_grid[sc] = grid;
+    }
+    if (grid == kBsmGrid && !(sc > 1 && bsm_sweep_fits<T>(P.d, sc))) grid = kResidentGrid;
+    if (grid == kBsmGrid) {
+      launch_bsm_sweep<T>(P.d, panel, B, Ywk, Uwk, X, sc, st);
+      return;
     }
     if (grid <= kVsmGrid) {   // kVsmGrid - 1 + c: c CTAs per SM
       const int fits = sc == 1 ? vsm_sweep_fits<T>(P.d) : 0;
@@ -1002,11 +1104,13 @@ struct Engine : EngineBase {
     else
       launch_sweep<T>(F.dev, P.d, panel, B, Ywk, Uwk, X, sc, dstat.p, st, grid);
   }
-  // grid codes besides persistent grid sizes: the block-resident sweep, and the shared-memory
-  // single-vector sweep with one (kVsmGrid) or two (kVsmGrid - 1) CTAs per SM
-  static constexpr int kResidentGrid = -1, kVsmGrid = -2;
-  // NSP_SWEEP=resident / global / smem forces one scheduler (measurements; smem: the
-  // shared-memory single-vector sweep where it fits, with as many CTAs per SM as fit, else
+  // grid codes besides persistent grid sizes: the block-resident sweep, the shared-memory
+  // single-vector sweep with one (kVsmGrid) or two (kVsmGrid - 1) CTAs per SM, and the
+  // column-sliced block sweep (kBsmGrid)
+  static constexpr int kResidentGrid = -1, kVsmGrid = -2, kBsmGrid = -4;
+  // NSP_SWEEP=resident / global / smem forces one scheduler (measurements; smem: for one
+  // right-hand side the shared-memory single-vector sweep where it fits, with as many CTAs per
+  // SM as fit, for several the column-sliced block sweep where it has a plan, else
   // resident); unset: the autotuner
   static int forced_scheduler() {
     const char *e = std::getenv("NSP_SWEEP");
@@ -1055,6 +1159,23 @@ struct Engine : EngineBase {
       tune_log.push_back({kResidentGrid, tot / 2});
       best_ms = tot;
       best = kResidentGrid;
+    }
+    if (sc > 1 && F.h.nblocks >= 2 && bsm_sweep_fits<T>(P.d, sc)) {
+      float tot = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        NSP_CUDA(cudaEventRecord(e0, st));
+        launch_bsm_sweep<T>(P.d, panel, B, Ywk, Uwk, X, sc, st);
+        NSP_CUDA(cudaEventRecord(e1, st));
+        NSP_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        NSP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        tot += ms;
+      }
+      tune_log.push_back({kBsmGrid, tot / 2});
+      if (tot < best_ms) {
+        best_ms = tot;
+        best = kBsmGrid;
+      }
     }
     const int vfits = (sc == 1 && F.h.nblocks >= 2) ? vsm_sweep_fits<T>(P.d) : 0;
     for (int per_sm = 1; per_sm <= vfits; ++per_sm) {

@@ -71,6 +71,20 @@ struct SweepPlan {
   const uint16_t *vs_pitem = nullptr, *vs_uitem = nullptr, *vs_citem = nullptr;
   int64_t vs_elems = 0;
   int32_t vs_scratch = 0;
+  // Block plans, column-sliced sweep (k_bsweep.cu): the same height / batch structure, with
+  // batch q (bs_bat[3q..3q+2]) = {first item, end item, front positions, forward units},
+  // {backward units, 0, first position, first forward unit}, {first backward unit, 0, 0, 0};
+  // item i (bs_item[3i..3i+2]) = {front offset, first forward unit, first backward unit, m},
+  // {w, first row, first update row, 0}, {sn_panel low, high, 0, 0}. Per front position:
+  // bs_pfvi forward row of B (top rows; -1: none), bs_pbvi backward source (row of Y for top
+  // rows; -2 - row of X below; -1: padding), bs_pptr / bs_psrc the gather sources (update
+  // rows). bs_uitem / bs_citem: item of each forward / backward unit. bs_positions = the
+  // largest batch's front positions (0: no plan).
+  const int32_t *bs_lvl_ptr = nullptr, *bs_bat_ptr = nullptr;
+  const int4 *bs_bat = nullptr, *bs_item = nullptr;
+  const int32_t *bs_pfvi = nullptr, *bs_pbvi = nullptr, *bs_pptr = nullptr, *bs_psrc = nullptr;
+  const uint16_t *bs_uitem = nullptr, *bs_citem = nullptr;
+  int32_t bs_positions = 0;
 };
 
 // ---- numeric factorization (k_factor.cu) -----------------------------------------
@@ -109,6 +123,15 @@ constexpr int kResW = 32, kResM = 128;   // block mode: supernodes a warp runs (
 // shared memory, one CTA per block of the vector plan's block-resident schedule; B, X in the
 // forest's internal order. vsm_sweep_fits: how many CTAs per SM (2, 1; 0: none) the largest
 // block's shared memory allows; per_sm (1 or 2, at most that) selects the register budget.
+// s > 1 (s a multiple of 4) with one CTA per (block, slice of kBsmCols columns), heights in
+// batches, no dependency waits (k_bsweep.cu); Y, U workspaces as launch_sweep's.
+constexpr int kBsmCols = 32;
+constexpr int kBsmScratchBytes = 192 * 1024;
+template <typename T>
+bool bsm_sweep_fits(const SweepPlan &p, int s);
+template <typename T>
+void launch_bsm_sweep(const SweepPlan &p, const T *panel, const T *B, T *Y, T *U, T *X, int s,
+                      cudaStream_t stream);
 constexpr int kVsmKG = 8;          // forward K groups of a CTA-sized supernode
 constexpr int kVsmScratch = 4096;  // default scratch entries per batch (fronts + partials)
 template <typename T>

@@ -117,12 +117,11 @@ def test_schur_apply_matches_oracle(N, torch, name, prec, s):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("s", [1, 7, 80, 160])
 def test_both_sweep_schedulers_match_oracle(N, torch, monkeypatch, sched, name, prec, s):
-    # the block-resident sweep (one CTA per block), the dependency-driven persistent sweep and,
-    # for one right-hand side, the sweep with each block's vectors in shared memory compute
-    # the same A_I^{-1} B and S_Gamma X; each is forced here (the autotuner would otherwise
-    # keep only the fastest)
-    if sched == "smem" and s != 1:
-        pytest.skip("the shared-memory sweep takes one right-hand side")
+    # the block-resident sweep (one CTA per block), the dependency-driven persistent sweep and
+    # the sweeps without dependency waits ("smem": for one right-hand side each block's
+    # vectors in shared memory, for several one CTA per block and 32-column slice, widths
+    # that are not a multiple of 4 falling back to the block-resident sweep) compute the same
+    # A_I^{-1} B and S_Gamma X; each is forced here (the autotuner keeps only the fastest)
     monkeypatch.setenv("NSP_SWEEP", sched)
     A, part, nsub = _case(name)
     D = O.DBBD(A, part, nsub)
