@@ -95,9 +95,20 @@ typedef enum { NSP_FORM_SGAMMA = 0, NSP_FORM_SI = 1 } nsp_inner_form;
  *                        interior order (see nsp_factor_solve). q must be 0
  *                        (NSP_ERR_UNSUPPORTED otherwise); nsp_get_intermediate is refused.
  *  NSP_VARIANT_M3_ADEF : M_{3A-DEF}: the deflation of NSP_VARIANT_M2_ADEF on span(Zh).
+ *  NSP_VARIANT_M1      : M1 = A_G^{-1} + Zb Sigma Zb^T (§4.1 eq. (prec1S)) with A_G = R^T R
+ *                        the handle's own Cholesky factor of A_G (R = L^T P^T for its fill-
+ *                        reducing order P, A_G's rows permuted by P factorized as L L^T):
+ *                        Nyström (Algorithm 1) of R^{-T} A_GI S_I^{-1} A_IG R^{-1}
+ *                        (eq. (lr_approximation_S-1_A-I)) from the sketch G: the block PCG of
+ *                        steps 2-4 runs on the sketch R^{-1} G, the Nyström core on (G,
+ *                        R^{-T} Y), and Zb = R^{-1} Ub. R^{-1} and R^{-T} are the backward and
+ *                        the forward half of the A_G sweep. M1 depends on R, hence on the
+ *                        ordering: two implementations with different orderings agree only
+ *                        where the Nyström approximation is exact (then M1 = S_G^{-1}). q must
+ *                        be 0 (NSP_ERR_UNSUPPORTED otherwise).
  * Single handles only: nsp_build_batched returns NSP_ERR_UNSUPPORTED for any but M2. */
 typedef enum { NSP_VARIANT_M2 = 0, NSP_VARIANT_M2_ADEF = 1, NSP_VARIANT_M3 = 2,
-               NSP_VARIANT_M3_ADEF = 3 } nsp_variant;
+               NSP_VARIANT_M3_ADEF = 3, NSP_VARIANT_M1 = 4 } nsp_variant;
 
 /* Sparse matrix in CSR. Full symmetric pattern (both triangles) with sorted column
  * indices and no duplicates. rowptr has n+1 entries. Host pointers unless on_device. */

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libnsp.so")
 
 NSP_FP64, NSP_FP32 = 0, 1
 NSP_OUTER_AUTO, NSP_OUTER_SCHUR, NSP_OUTER_FULL = 0, 1, 2
-NSP_VARIANT_M2, NSP_VARIANT_M2_ADEF, NSP_VARIANT_M3, NSP_VARIANT_M3_ADEF = 0, 1, 2, 3
+NSP_VARIANT_M2, NSP_VARIANT_M2_ADEF, NSP_VARIANT_M3, NSP_VARIANT_M3_ADEF, NSP_VARIANT_M1 = 0, 1, 2, 3, 4
 NSP_FORM_SGAMMA, NSP_FORM_SI = 0, 1
 STATUS = {0: "NSP_OK", 1: "NSP_ERR_INVALID_ARG", 2: "NSP_ERR_NOT_DBBD", 3: "NSP_ERR_NOT_SPD",
           4: "NSP_ERR_BREAKDOWN", 5: "NSP_ERR_NOT_CONVERGED", 6: "NSP_ERR_TIMEOUT",
@@ -211,7 +211,7 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                       "full": NSP_OUTER_FULL}[outer_form]
     prm.keep_intermediates = 1 if keep_intermediates else 0
     prm.variant = {"m2": NSP_VARIANT_M2, "m2_adef": NSP_VARIANT_M2_ADEF, "m3": NSP_VARIANT_M3,
-                   "m3_adef": NSP_VARIANT_M3_ADEF}[variant]
+                   "m3_adef": NSP_VARIANT_M3_ADEF, "m1": NSP_VARIANT_M1}[variant]
     prm.q = int(q)
     prm.inner_form = {"s_gamma": NSP_FORM_SGAMMA, "s_i": NSP_FORM_SI}[inner_form]
     if sketch is not None:

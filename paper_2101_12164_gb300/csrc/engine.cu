@@ -1241,6 +1241,27 @@ struct Engine : EngineBase {
   // ---- S_I V = A_I V - A_IG A_G^{-1} A_GI V (§4.1 eq. (SI)), interior order, sc columns
   int inner_form = NSP_FORM_SGAMMA;
   DBuf<T> siA, siB;
+  // Half sweeps of the A_G factor in the internal interface order (where A_G = L L^T):
+  // half = 1: O = L^{-1} V (R^{-T} in the caller's order), half = 2: O = L^{-T} V (R^{-1}).
+  // The column-sliced sweep where it has a plan for this width, else the block-resident one.
+  DBuf<T> G1;
+  void half_G(int half, const T *V, T *O, int sc) {
+    FG.vec_rows = sweep_vector_rows((int)sizeof(T));
+    FG.elem_bytes = (int)sizeof(T);
+    auto &P = FG.plan(sc == 1, st);
+    ensure_ws(sc);
+    if (sc > 1 && bsm_sweep_fits<T>(P.d, sc)) {
+      if (half == 1) launch_bsm_sweep<T>(P.d, panelG.p, V, O, UwG.p, nullptr, sc, st, 1);
+      else launch_bsm_sweep<T>(P.d, panelG.p, nullptr, const_cast<T *>(V), UwG.p, O, sc, st, 2);
+    } else {
+      if (half == 1)
+        launch_res_sweep<T>(FG.dev, P.d, panelG.p, V, O, UwG.p, nullptr, sc, dstat.p, st, 1);
+      else
+        launch_res_sweep<T>(FG.dev, P.d, panelG.p, nullptr, const_cast<T *>(V), UwG.p, O, sc,
+                            dstat.p, st, 2);
+    }
+  }
+
   void apply_SI(const T *V, T *O, int sc) {
     launch_spmm<T>(A_GI.dT(), V, siA.p, sc, T(1), nullptr, T(0), st);
     solve_G(siA.p, siB.p, sc);
@@ -1323,7 +1344,7 @@ struct Engine : EngineBase {
     require(s <= an.nG, NSP_ERR_INVALID_ARG, "k + p exceeds the interface size");
     require(prm.inner_form == NSP_FORM_SGAMMA || prm.inner_form == NSP_FORM_SI,
             NSP_ERR_INVALID_ARG, "unknown inner form");
-    require(prm.variant >= NSP_VARIANT_M2 && prm.variant <= NSP_VARIANT_M3_ADEF,
+    require(prm.variant >= NSP_VARIANT_M2 && prm.variant <= NSP_VARIANT_M1,
             NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
     variant = prm.variant;
     require(prm.q >= 0 && prm.q <= 16, NSP_ERR_INVALID_ARG, "power iterations q in [0, 16]");
@@ -1331,6 +1352,10 @@ struct Engine : EngineBase {
     // block PCG (S_I X = G_I, preconditioner A_I), without power iterations
     m3 = variant == NSP_VARIANT_M3 || variant == NSP_VARIANT_M3_ADEF;
     require(!m3 || prm.q == 0, NSP_ERR_UNSUPPORTED, "M3 takes no power iterations");
+    // M1 (§4.1): the same steps on the sketch R^{-1} G, the Nyström core on (G, R^{-T} Y) and
+    // Zb = R^{-1} Ub, with A_G = R^T R the handle's own factor
+    const bool m1 = variant == NSP_VARIANT_M1;
+    require(!m1 || prm.q == 0, NSP_ERR_UNSUPPORTED, "M1 takes no power iterations");
     keep = prm.keep_intermediates != 0;
     ensure_ws(s);
     const size_t ns = (size_t)an.nG * s;
@@ -1382,6 +1407,11 @@ struct Engine : EngineBase {
         launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
       }
       launch_gather_rows<double, T>(i2u_G.p, an.nG, g64.p, G.p, s, st);
+      if (m1) {   // keep G for the core; the block PCG runs on R^{-1} G
+        G1.ensure(ns);
+        NSP_CUDA(cudaMemcpyAsync(G1.p, G.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        half_G(2, G1.p, G.p, s);
+      }
       sync();
     }
     // q-power iteration (§2.1 eq. (power)): passes 0..q-1 apply B = A_GI S_I^{-1} A_IG to G
@@ -1460,9 +1490,14 @@ struct Engine : EngineBase {
     info.inner_active_cols = active;
     info.ms_inner = ms_since(t0);
     auto t1 = Clock::now();
-    // steps 5-10 (M3: on G_I and X = S_I^{-1} G_I, n_interior rows)
+    // M1: F = R^{-T} Y takes the place of Y from here on (into Y, through W)
+    if (m1) {
+      half_G(1, Y.p, W.p, s);
+      NSP_CUDA(cudaMemcpyAsync(Y.p, W.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    }
+    // steps 5-10 (M3: on G_I and X = S_I^{-1} G_I, n_interior rows; M1: on G and F)
     {
-      const T *Ys = m3 ? E.p : Y.p, *Gs = m3 ? Fh.p : G.p;
+      const T *Ys = m3 ? E.p : Y.p, *Gs = m3 ? Fh.p : m1 ? G1.p : G.p;
       const int64_t ny = m3 ? an.nI : an.nG;
       gram_acc64_n(Ys, Ys, ny, s, s, K.p);
       gram_acc64_n(Gs, Ys, ny, s, s, Cn.p);
@@ -1485,8 +1520,10 @@ struct Engine : EngineBase {
         // U = Y Mix (columns beyond the rank are zero, Sigma there is zero)
         block_update(Y.p, Mix.p, an.nG, s, k, T(1), nullptr, T(0), U.p);
       }
-      // step 11: Z = A_G^{-1} U; M2's low-rank term kept as Zs = Z Sigma^{1/2} in FP64
-      solve_G(U.p, Zt.p, k);
+      // step 11: Z = A_G^{-1} U (M1: Zb = R^{-1} Ub); the low-rank term kept as
+      // Zs = Z Sigma^{1/2} in FP64
+      if (m1) half_G(2, U.p, Zt.p, k);
+      else solve_G(U.p, Zt.p, k);
       launch_gather_rows<T, double>(nullptr, an.nG, Zt.p, Zs.p, k, st);
       launch_scale_cols(Zs.p, an.nG, k, Sigma.p, true, st);
       if (variant == NSP_VARIANT_M2_ADEF || variant == NSP_VARIANT_M3_ADEF)
@@ -2319,7 +2356,7 @@ static void validate_params(const nsp_params *prm, bool batched) {
   // the engine's next checks (k + p <= n_Gamma, then these) all answer NSP_ERR_INVALID_ARG
   nsp::require(prm->inner_form == NSP_FORM_SGAMMA || prm->inner_form == NSP_FORM_SI,
                NSP_ERR_INVALID_ARG, "unknown inner form");
-  nsp::require(prm->variant >= NSP_VARIANT_M2 && prm->variant <= NSP_VARIANT_M3_ADEF,
+  nsp::require(prm->variant >= NSP_VARIANT_M2 && prm->variant <= NSP_VARIANT_M1,
                NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
   nsp::require(prm->q >= 0 && prm->q <= 16, NSP_ERR_INVALID_ARG, "power iterations q in [0, 16]");
 }

@@ -15,7 +15,8 @@
 //             f_top from scratch, written to Y (rows < w) or U (f_bot - product);
 //   backward: (A) g = [y_J; -x(rows below)] for every supernode into scratch;
 //             (B) one unit per (4 panel columns, 8 slice columns): P[:, cols]^T g, to X.
-// Every K loop sums sequentially; the columns of a slice never meet another CTA's, the rows
+// half = 1 runs the forward sweep alone (Y = L^{-1} B), half = 2 the backward sweep alone
+// (X = L^{-T} Y). Every K loop sums sequentially; the columns of a slice never meet another CTA's, the rows
 // of a block never another block's, and a CTA reads its own global writes of an earlier
 // height only after a barrier.
 #include "sweep_tiles.cuh"
@@ -308,16 +309,16 @@ __device__ void bs_backward(const SweepPlan &p, const T *panel, const T *Y, T *X
 template <typename T>
 __global__ void __launch_bounds__(BT, 1)
     k_bsm_sweep(SweepPlan p, const T *__restrict__ panel, const T *B, T *Y, T *U, T *X, int s,
-                int nslices) {
+                int nslices, int half) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *scr = reinterpret_cast<T *>(smem_raw);
   const int b = blockIdx.x / nslices, sl = blockIdx.x - b * nslices;
   const int c0 = sl * BCS, ncq = min(BCS, s - c0) / 4;
   const int L0 = p.bs_lvl_ptr[b], L1 = p.bs_lvl_ptr[b + 1];
-  for (int L = L0; L < L1; ++L)
+  for (int L = L0; L < L1 && half != 2; ++L)
     for (int q = p.bs_bat_ptr[L]; q < p.bs_bat_ptr[L + 1]; ++q)
       bs_forward<T>(p, panel, B, Y, U, s, c0, ncq, scr, q);
-  for (int L = L1 - 1; L >= L0; --L)
+  for (int L = L1 - 1; L >= L0 && half != 1; --L)
     for (int q = p.bs_bat_ptr[L]; q < p.bs_bat_ptr[L + 1]; ++q)
       bs_backward<T>(p, panel, Y, X, s, c0, ncq, scr, q);
 }
@@ -332,9 +333,10 @@ bool bsm_sweep_fits(const SweepPlan &p, int s) {
 
 template <typename T>
 void launch_bsm_sweep(const SweepPlan &p, const T *panel, const T *B, T *Y, T *U, T *X, int s,
-                      cudaStream_t stream) {
+                      cudaStream_t stream, int half) {
   require(bsm_sweep_fits<T>(p, s), NSP_ERR_INVALID_ARG,
           "column-sliced block sweep: no plan for this width");
+  require(half >= 0 && half <= 2, NSP_ERR_INVALID_ARG, "column-sliced block sweep: bad half");
   const int nslices = (s + BCS - 1) / BCS;
   const size_t smem = (size_t)p.bs_positions * BCS * sizeof(T);
   static size_t attr = 0;
@@ -342,15 +344,16 @@ void launch_bsm_sweep(const SweepPlan &p, const T *panel, const T *B, T *Y, T *U
     ensure_dyn_smem(k_bsm_sweep<T>, smem);
     attr = smem;
   }
-  k_bsm_sweep<T><<<p.res_nblocks * nslices, BT, smem, stream>>>(p, panel, B, Y, U, X, s, nslices);
+  k_bsm_sweep<T><<<p.res_nblocks * nslices, BT, smem, stream>>>(p, panel, B, Y, U, X, s, nslices,
+                                                                  half);
   NSP_LAUNCH_CHECK();
 }
 
 template bool bsm_sweep_fits<float>(const SweepPlan &, int);
 template bool bsm_sweep_fits<double>(const SweepPlan &, int);
 template void launch_bsm_sweep<float>(const SweepPlan &, const float *, const float *, float *,
-                                      float *, float *, int, cudaStream_t);
+                                      float *, float *, int, cudaStream_t, int);
 template void launch_bsm_sweep<double>(const SweepPlan &, const double *, const double *,
-                                       double *, double *, double *, int, cudaStream_t);
+                                       double *, double *, double *, int, cudaStream_t, int);
 
 }  // namespace nsp

@@ -18,9 +18,11 @@ namespace nsp {
 namespace {
 
 // One CTA per block: forward heights upwards, then backward heights downwards.
+// half: 0 both sweeps, 1 the forward sweep only (y = L^{-1} b into Y), 2 the backward sweep
+// only (x = L^{-T} y from Y)
 template <typename T, int TC, int CM, int RM, bool VECTOR>
 __global__ void __launch_bounds__(ST, sizeof(T) == 8 ? 1 : 2)
-    k_res_sweep(SweepCtx c, const T *__restrict__ panel, const T *B, T *Y, T *U, T *X) {
+    k_res_sweep(SweepCtx c, const T *__restrict__ panel, const T *B, T *Y, T *U, T *X, int half) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *sm = reinterpret_cast<T *>(smem_raw);
   constexpr int NW = ST / 32, CPL = WarpCpl<T>::value;
@@ -31,7 +33,7 @@ __global__ void __launch_bounds__(ST, sizeof(T) == 8 ? 1 : 2)
   const int b = blockIdx.x;
   const int L0 = p.res_blk_ptr[b], L1 = p.res_blk_ptr[b + 1];
   const int wid = threadIdx.x >> 5;
-  for (int L = L0; L < L1; ++L) {
+  for (int L = L0; L < L1 && half != 2; ++L) {
     const int j0 = p.res_lvl_ptr[L], j1 = p.res_lvl_ptr[L + 1], jw = j0 + p.res_lvl_nwarp[L];
     for (int q = j0 + wid; q < jw; q += NW) {
       const int J = p.res_job[q];
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(ST, sizeof(T) == 8 ? 1 : 2)
       }
     }
   }
-  for (int L = L1 - 1; L >= L0; --L) {
+  for (int L = L1 - 1; L >= L0 && half != 1; --L) {
     const int j0 = p.res_lvl_ptr[L], j1 = p.res_lvl_ptr[L + 1], jw = j0 + p.res_lvl_nwarp[L];
     for (int q = j0 + wid; q < jw; q += NW) {
       const int J = p.res_job[q];
@@ -84,13 +86,13 @@ __global__ void __launch_bounds__(ST, sizeof(T) == 8 ? 1 : 2)
 
 template <typename T, int TC, int CM, int RM, bool VECTOR>
 void run_res(const SweepCtx &c, int nblocks, size_t smem, const T *panel, const T *B, T *Y, T *U,
-             T *X, cudaStream_t st) {
+             T *X, int half, cudaStream_t st) {
   static size_t attr = 0;
   if (smem > attr) {
     ensure_dyn_smem(k_res_sweep<T, TC, CM, RM, VECTOR>, smem);
     attr = smem;
   }
-  k_res_sweep<T, TC, CM, RM, VECTOR><<<nblocks, ST, smem, st>>>(c, panel, B, Y, U, X);
+  k_res_sweep<T, TC, CM, RM, VECTOR><<<nblocks, ST, smem, st>>>(c, panel, B, Y, U, X, half);
   NSP_LAUNCH_CHECK();
 }
 
@@ -106,7 +108,8 @@ size_t res_blk_smem() {
 
 template <typename T>
 void launch_res_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y,
-                      T *U, T *X, int s, DevStatus *st, cudaStream_t stream) {
+                      T *U, T *X, int s, DevStatus *st, cudaStream_t stream, int half) {
+  require(half >= 0 && half <= 2, NSP_ERR_INVALID_ARG, "block-resident sweep: bad half");
   require(p.res_nblocks > 0, NSP_ERR_INVALID_ARG, "block-resident sweep: no schedule");
   SweepCtx c{f, p, s, st, 0};
   if (s == 1) {
@@ -114,12 +117,12 @@ void launch_res_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, co
     const size_t ldmax = (size_t)((p.max_m + 3) & ~3) + 8;
     const size_t smem = sizeof(T) * std::max<size_t>(
         ldmax + (size_t)(ST / kVecRG + 1) * kVecRG * (16 / sizeof(T)), 8 * 32 * 33);
-    run_res<T, 1, 1, 1, true>(c, p.res_nblocks, smem, panel, B, Y, U, X, stream);
+    run_res<T, 1, 1, 1, true>(c, p.res_nblocks, smem, panel, B, Y, U, X, half, stream);
     return;
   }
   require(!p.vector, NSP_ERR_INVALID_ARG, "block plan needed for several right-hand sides");
 #define NSP_RES(TC_, CM_, RM_) \
-  run_res<T, TC_, CM_, RM_, false>(c, p.res_nblocks, res_blk_smem<T, TC_, CM_, RM_>(), panel, B, Y, U, X, stream)
+  run_res<T, TC_, CM_, RM_, false>(c, p.res_nblocks, res_blk_smem<T, TC_, CM_, RM_>(), panel, B, Y, U, X, half, stream)
   if (s <= 16) NSP_RES(16, 1, 4);
   else if (s <= 32) NSP_RES(16, 2, 4);
   else if (s <= 48) NSP_RES(16, 3, 4);
@@ -135,9 +138,9 @@ void launch_res_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, co
 
 template void launch_res_sweep<float>(const ForestDev &, const SweepPlan &, const float *,
                                       const float *, float *, float *, float *, int, DevStatus *,
-                                      cudaStream_t);
+                                      cudaStream_t, int);
 template void launch_res_sweep<double>(const ForestDev &, const SweepPlan &, const double *,
                                        const double *, double *, double *, double *, int,
-                                       DevStatus *, cudaStream_t);
+                                       DevStatus *, cudaStream_t, int);
 
 }  // namespace nsp

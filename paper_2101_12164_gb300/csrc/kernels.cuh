@@ -115,9 +115,11 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T
                  int max_spins = 0);
 // The same solve with one CTA per block of the forest and no cross-CTA dependency (the
 // plan's block-resident schedule), both sweeps of a block in its CTA. Grid = blocks.
+// half = 1: the forward sweep only, Y = L^{-1} B (with A_b = L L^T in the forest's order);
+// half = 2: the backward sweep only, X = L^{-T} Y (Y is then read, not written).
 template <typename T>
 void launch_res_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T *B, T *Y,
-                      T *U, T *X, int s, DevStatus *st, cudaStream_t stream);
+                      T *U, T *X, int s, DevStatus *st, cudaStream_t stream, int half = 0);
 constexpr int kResW = 32, kResM = 128;   // block mode: supernodes a warp runs (w, m bounds)
 // One right-hand side with each block's vectors (b, y, x in place, and its update rows) in
 // shared memory, one CTA per block of the vector plan's block-resident schedule; B, X in the
@@ -131,7 +133,7 @@ template <typename T>
 bool bsm_sweep_fits(const SweepPlan &p, int s);
 template <typename T>
 void launch_bsm_sweep(const SweepPlan &p, const T *panel, const T *B, T *Y, T *U, T *X, int s,
-                      cudaStream_t stream);
+                      cudaStream_t stream, int half = 0);
 constexpr int kVsmKG = 8;          // forward K groups of a CTA-sized supernode
 constexpr int kVsmScratch = 4096;  // default scratch entries per batch (fronts + partials)
 template <typename T>

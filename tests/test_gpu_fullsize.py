@@ -131,6 +131,25 @@ def test_fullsize_variants_match_oracle_iterations(N, torch, cfg1, variant, form
     h.destroy()
 
 
+def test_fullsize_m1_solves_like_m2(N, torch, cfg1):
+    # M1 (§4.1) at the benchmark size: the oracle's M1 needs a dense factor of A_G (n_Gamma
+    # in the tens of thousands here), so this checks the GPU form against the outer
+    # tolerance and against M2 from the same sketch, which §5 finds about as effective
+    P, D = cfg1
+    _, b = F.make_rhs(P, 1, 0)
+    G = F.make_sketch(P.n_gamma, P.s, 1, 0)
+    its = {}
+    for variant in ("m2", "m1"):
+        h = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                        precision="fp32", sketch=G, variant=variant)
+        bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+        xd = torch.zeros_like(bd)
+        its[variant] = h.solve(bd, xd, rtol=P.rtol, maxit=500)["it_pcg"]
+        assert O.relative_residual(P.A, xd.cpu().numpy(), b) < 1e-8
+        h.destroy()
+    assert its["m1"] <= its["m2"] + 5, its
+
+
 # ------------------------------------------------------------------ 128^3 (stored oracle)
 @pytest.fixture(scope="module")
 def cfg4():
