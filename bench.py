@@ -167,10 +167,12 @@ def sweep_algorithmic_bytes(info, s, wbytes):
     return 2 * info["nnz_L_interior"] * wbytes + 4 * info["n_interior"] * s * wbytes
 
 
-# DRAM bytes (read + write) of one interior-sweep launch from an ncu capture of the bench
-# workload (profiles/sweep_block_lognormal3d_64.md), keyed by (configuration, s); absent
-# until captured for the current kernel.
-SWEEP_TRAFFIC = {(1, 80): 768.0e6}
+# DRAM bytes (read + write) of one interior-sweep launch (the scheduler the autotuner keeps)
+# from an ncu capture of the bench workload (profiles/sweep_block_lognormal3d_64.md: the
+# dependency-driven sweep at 64^3; profiles/sweep_bsm_lognormal3d_64.md: the column-sliced
+# sweep at 128^3), keyed by (configuration, s, precision); absent until captured for the
+# current kernel.
+SWEEP_TRAFFIC = {(1, 80, "fp32"): 768.0e6, (4, 160, "fp32"): 11.89e9}
 
 
 def sub_nnz(P):
@@ -622,7 +624,7 @@ def main():
                            phase_ms={"factor": last["ms_factor"], "inner": last["ms_inner"],
                                      "core": last["ms_core"], "solve": last["ms_solve"]}),
             "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s",
-                         "frac": sweep_gbs / hbm, "traffic": SWEEP_TRAFFIC.get((args.config, s)),
+                         "frac": sweep_gbs / hbm, "traffic": SWEEP_TRAFFIC.get((args.config, s, args.precision)),
                          "kernel": "interior sweep (s=%d, %s): forward+backward supernodal "
                                    "sweep of every interior block, the dominant kernel of the "
                                    "S_Gamma block apply" % (s, args.precision),

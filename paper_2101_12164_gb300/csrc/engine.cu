@@ -1650,14 +1650,15 @@ struct Engine : EngineBase {
     launch_dot(vr.p, vz.p, n, d_rz, dwork.p, st);
     int it = 0;
     double rel = 1.0;
+    // r^T z of the current and of the next direction: the two slots swap roles each
+    // iteration (no copy)
+    double *rz_cur = d_rz, *rz_next = d_rznew;
     while (it < maxit) {
       A(vp.p, vq.p);
       launch_dot(vp.p, vq.p, n, d_pq, dwork.p, st);
-      launch_pcg_scalars(d_rz, nullptr, d_pq, d_alpha, nullptr, st);
-      launch_axpby(n, d_alpha, 1.0, vp.p, 1.0, x, st);
-      launch_axpby(n, d_alpha, -1.0, vq.p, 1.0, vr.p, st);
+      // alpha = r^T z / p^T q, x += alpha p, r -= alpha q, r^T r: one fused pass
+      launch_pcg_step(n, rz_cur, d_pq, d_alpha, vp.p, vq.p, x, vr.p, d_rr, dwork.p, st);
       ++it;
-      launch_dot(vr.p, vr.p, n, d_rr, dwork.p, st);
       // alpha_j, beta_{j-1} (the ratio that formed this direction) and r^T r in one copy
       NSP_CUDA(cudaMemcpyAsync(hscal + 2, d_alpha, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
       sync();
@@ -1666,11 +1667,9 @@ struct Engine : EngineBase {
       rel = std::sqrt(std::max(hscal[4], 0.0)) / fn;
       if (!(rel > rtol)) break;
       M(vr.p, vz.p);
-      launch_dot(vr.p, vz.p, n, d_rznew, dwork.p, st);
-      launch_pcg_scalars(d_rznew, d_rz, nullptr, nullptr, d_beta, st);
-      launch_axpby(n, d_beta, 1.0, vp.p, 0.0, vp.p, st);         // p = beta p
-      launch_axpby(n, nullptr, 1.0, vz.p, 1.0, vp.p, st);        // p += z
-      NSP_CUDA(cudaMemcpyAsync(d_rz, d_rznew, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      launch_dot(vr.p, vz.p, n, rz_next, dwork.p, st);
+      launch_pcg_direction(n, rz_next, rz_cur, d_beta, vz.p, vp.p, st);   // p = z + beta p
+      std::swap(rz_cur, rz_next);
     }
     *rel_out = rel;
     return it;

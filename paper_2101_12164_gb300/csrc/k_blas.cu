@@ -497,6 +497,44 @@ __global__ void k_scale_cols(double *X, int64_t n, int s, const double *scale, i
   X[idx] *= take_sqrt ? sqrt(f) : f;
 }
 
+// One PCG step after q = A p: alpha = rz / pq (block 0 records it), x += alpha p,
+// r -= alpha q, and this chunk's partial sum of r.r; the same chunks, per-thread order and
+// tree as k_dot_partial, the same roundings as two k_axpby launches and a dot.
+__global__ void __launch_bounds__(BT) k_pcg_step(int64_t n, int64_t rpc, const double *rz,
+                                                 const double *pq, double *alpha_out,
+                                                 const double *p, const double *q, double *x,
+                                                 double *r, double *work) {
+  __shared__ double red[BT];
+  const double a = *rz / *pq;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *alpha_out = a;
+  const int64_t i0 = (int64_t)blockIdx.x * rpc, i1 = min(n, i0 + rpc);
+  double acc = 0.0;
+  for (int64_t i = i0 + threadIdx.x; i < i1; i += BT) {
+    x[i] = fma(a, p[i], x[i]);
+    const double ri = fma(-a, q[i], r[i]);
+    r[i] = ri;
+    acc += ri * ri;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = BT / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) work[blockIdx.x] = red[0];
+}
+
+// p = z + beta p with beta = rz_new / rz_old (block 0 records it); the roundings of
+// p = beta p followed by p = z + p
+__global__ void k_pcg_direction(int64_t n, const double *rz_new, const double *rz_old,
+                                double *beta_out, const double *z, double *p) {
+  const double b = *rz_new / *rz_old;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *beta_out = b;
+  if (i >= n) return;
+  p[i] = __dadd_rn(z[i], __dmul_rn(b, p[i]));
+}
+
 __global__ void k_pcg_scalars(const double *rz_new, const double *rz_old, const double *pq,
                               double *alpha, double *beta) {
   if (threadIdx.x != 0) return;
@@ -672,6 +710,25 @@ void launch_scale_cols(double *X, int64_t n, int s, const double *scale, bool ta
                        cudaStream_t stream) {
   if (n * s <= 0) return;
   k_scale_cols<<<ceil_div(n * s, BT), BT, 0, stream>>>(X, n, s, scale, take_sqrt ? 1 : 0);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_pcg_step(int64_t n, const double *rz, const double *pq, double *alpha,
+                     const double *p, const double *q, double *x, double *r, double *rr,
+                     double *work, cudaStream_t stream) {
+  const int64_t cs = std::max<int64_t>(1, std::min<int64_t>(2 * 152, (n + 1023) / 1024));
+  const int64_t rpc = (n + cs - 1) / cs;
+  k_pcg_step<<<(int)cs, BT, 0, stream>>>(n, std::max<int64_t>(rpc, 1), rz, pq, alpha, p, q, x,
+                                          r, work);
+  NSP_LAUNCH_CHECK();
+  k_sum<<<1, BT, 0, stream>>>(work, (int)cs, rr);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_pcg_direction(int64_t n, const double *rz_new, const double *rz_old, double *beta,
+                          const double *z, double *p, cudaStream_t stream) {
+  k_pcg_direction<<<ceil_div(std::max<int64_t>(n, 1), BT), BT, 0, stream>>>(n, rz_new, rz_old,
+                                                                             beta, z, p);
   NSP_LAUNCH_CHECK();
 }
 

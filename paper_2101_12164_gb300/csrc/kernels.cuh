@@ -213,6 +213,14 @@ void launch_dot(const double *x, const double *y, int64_t n, double *result, dou
                 cudaStream_t stream);
 void launch_axpby(int64_t n, const double *a_ptr, double a_sign, const double *x, double b,
                   double *y, cudaStream_t stream);   // y = (a_sign * *a_ptr) x + b y
+// Fused PCG vector steps (FP64): alpha = *rz / *pq, x += alpha p, r -= alpha q, *rr = r.r
+// (alpha recorded in *alpha); and p = z + beta p with beta = *rz_new / *rz_old (recorded in
+// *beta). Bit-identical to launch_pcg_scalars + launch_axpby + launch_dot.
+void launch_pcg_step(int64_t n, const double *rz, const double *pq, double *alpha,
+                     const double *p, const double *q, double *x, double *r, double *rr,
+                     double *work, cudaStream_t stream);
+void launch_pcg_direction(int64_t n, const double *rz_new, const double *rz_old, double *beta,
+                          const double *z, double *p, cudaStream_t stream);
 void launch_pcg_scalars(const double *rz_new, const double *rz_old, const double *pq,
                         double *alpha, double *beta, cudaStream_t stream);
 
