@@ -286,6 +286,8 @@ def run_reference(args, P, G, b):
 
 
 WORKLOADS = {
+    2: "aniso2d_batch: 64 independent 2D 5-point anisotropic problems, side U{100..400}, "
+       "ratio log-U[1,1e3], 8-64 subdomains, k=32, p=8",
     4: "aniso3d_128: 3D 7-point anisotropic diffusion 128^3 (n=2097152), axis scales "
        "(1, 1, 1e-3), lognormal a (ell=8, sigma=1.5), 256 subdomains, k=128, p=32",
     1: "lognormal3d_64: 3D 7-point diffusion 64^3 (n=262144), lognormal a (ell=8, sigma=2), "
@@ -595,6 +597,48 @@ def main():
                   "sweep_ms": sw1, "sweep_frac_hbm": sb1 / (sw1 * 1e-3) / 1e9 / hbm}
         h1.destroy()
 
+    # ---- the batched workload (64 independent 2D problems in one batched handle, §8(a) A8)
+    # beside it: 1 warm-up + 3 timed steps of the same batched step as `--config 2`
+    batched = None
+    if args.config == 4:
+        specs = F.batched_problem_specs()
+        probs = [F.problem_from_spec(sp) for sp in specs]
+        bb = np.concatenate([F.make_rhs(Pm, 2, i)[1] for i, Pm in enumerate(probs)])
+        vb_d = torch.tensor(np.concatenate([Pm.A.data for Pm in probs]), dtype=torch.float64,
+                            device=dev)
+        bb_d = torch.tensor(bb, dtype=torch.float64, device=dev)
+        xb_d = torch.zeros_like(bb_d)
+        hb = N.nsp_build_batched([(Pm.A, Pm.part, Pm.nsub) for Pm in probs], k=probs[0].k,
+                                 p=probs[0].p, eps_inner=probs[0].eps_inner,
+                                 precision=args.precision, seed=seed)
+
+        def stepb():
+            hb.rebuild(vb_d, on_device=True)
+            return hb.solve_batched(bb_d, xb_d, rtol=probs[0].rtol, maxit=1000)
+
+        stepb()
+        torch.cuda.synchronize()
+        tb = []
+        for i in range(3):
+            flush.fill_(float(i))
+            a0.record(stream)
+            lb = stepb()
+            a1.record(stream)
+            torch.cuda.synchronize()
+            tb.append(a0.elapsed_time(a1))
+        xb = xb_d.cpu().numpy()
+        off = np.concatenate([[0], np.cumsum([Pm.n for Pm in probs])])
+        resb = [float(np.linalg.norm(bb[off[i]:off[i + 1]] - Pm.A @ xb[off[i]:off[i + 1]])
+                      / np.linalg.norm(bb[off[i]:off[i + 1]])) for i, Pm in enumerate(probs)]
+        batched = {"workload": WORKLOADS[2], "matrices": len(probs),
+                   "unknowns": int(off[-1]), "ms_per_step": float(np.mean(tb)),
+                   "it_inner_range": [int(min(d["it_inner"] for d in lb)),
+                                      int(max(d["it_inner"] for d in lb))],
+                   "it_pcg_range": [int(min(d["it_pcg"] for d in lb)),
+                                    int(max(d["it_pcg"] for d in lb))],
+                   "final_residual_max": float(max(resb))}
+        hb.destroy()
+
     out = None
     if rank == 0:
         cpu = None
@@ -640,6 +684,7 @@ def main():
             "other_variant": variant_line,
             "plain_fp64": fp64_line,
             "second_workload": second,
+            "batched_workload": batched,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(8 * (P.A.nnz + P.n)),
                     "d2h_bytes_per_step": int(8 * P.n),
@@ -768,9 +813,7 @@ def main_batched(args, F, world, rank, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-            "config": {"workload": "aniso2d_batch: 64 independent 2D 5-point anisotropic "
-                                   "problems, side U{100..400}, ratio log-U[1,1e3], 8-64 "
-                                   "subdomains, k=32, p=8",
+            "config": {"workload": WORKLOADS[2],
                        "matrices": len(probs), "n_total": n_tot,
                        "n_gamma_total": int(info0["n_gamma"]),
                        "precision": args.precision, "parallelism": "replicas%d" % world,
