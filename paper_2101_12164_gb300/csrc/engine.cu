@@ -91,6 +91,15 @@ static int vec_cols() {
   return v >= 1 ? v : kSweepVectorCols;
 }
 
+// Block tiles of 32 rows instead of 64 in the dependency-driven sweeps of single-tree forests
+// (A_G), whose top supernodes form a long chain: twice the tiles work on each of them at once
+// (128^3, s = 160: 5.67 -> 4.45 ms per A_G sweep; 16-row tiles 4.62 ms). NSP_GTILE=64
+// restores 64 (measurements).
+static int narrow_tiles() {
+  const char *e = std::getenv("NSP_GTILE");
+  return e && std::atoi(e) == 64 ? kSweepBlockRows : kSweepBlockRowsNarrow;
+}
+
 static int relax_level() {
   const char *e = std::getenv("NSP_RELAX");
   return e ? std::atoi(e) : 2;
@@ -389,6 +398,8 @@ struct ForestData {
   std::unique_ptr<Plan> plans[2];  // 0: block (s > 1), 1: vector (s = 1)
   int vec_rows = 128;
   int elem_bytes = 4;   // element size of the handle (shared-memory sweep budget)
+  // rows (forward) / columns (backward) of a block tile of the dependency-driven sweep
+  int blk_rows = kSweepBlockRows;
 
   Plan &plan(bool vector, cudaStream_t st) {
     auto &pp = plans[vector ? 1 : 0];
@@ -396,8 +407,8 @@ struct ForestData {
     pp = std::make_unique<Plan>();
     Plan &P = *pp;
     const int nsn = h.nsn;
-    const int tf = vector ? vec_rows : kSweepBlockRows;
-    const int tb = vector ? vec_cols() : kSweepBlockRows;
+    const int tf = vector ? vec_rows : blk_rows;
+    const int tb = vector ? vec_cols() : blk_rows;
     std::vector<int32_t> ia, ib, gs, uf(nsn, 0), ub(nsn, 0), need(nsn, 0);
     auto small = [&](int J) { return vector && h.sn_m[J] <= kSmallM && h.sn_w[J] <= kSmallW; };
     // Subtrees of small supernodes run as one item each (one CTA, no dependency wait inside):
@@ -499,6 +510,7 @@ struct ForestData {
     P.d.nfwd = nfwd;
     P.d.max_m = mm;
     P.d.vec_cols = tb;
+    P.d.blk_rows = vector ? kSweepBlockRows : blk_rows;
     P.d.vector = vector;
     P.d.item_a = P.item_a.p;
     P.d.item_b = P.item_b.p;
@@ -1076,6 +1088,7 @@ struct Engine : EngineBase {
                     bool tune = true) {
     F.vec_rows = sweep_vector_rows((int)sizeof(T));
     F.elem_bytes = (int)sizeof(T);
+    F.blk_rows = F.h.nblocks == 1 ? narrow_tiles() : kSweepBlockRows;
     auto &P = F.plan(sc == 1, st);
     int grid = 0;
     auto it = P.tuned_grid.find(sc);

@@ -260,6 +260,17 @@ int launch_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, const T
   require(!p.vector, NSP_ERR_INVALID_ARG, "block plan needed for several right-hand sides");
 #define NSP_BLK(TC_, CM_, RM_) \
   dispatch<T, TC_, CM_, RM_, false>(c, blk_smem<T, TC_, CM_, RM_>(), panel, B, Y, U, X, stream, &grid)
+  if (p.blk_rows == kSweepBlockRowsNarrow) {   // 32-row tiles: 32 column threads x 8 row threads
+    if (s <= 32) NSP_BLK(32, 1, 4);
+    else if (s <= 64) NSP_BLK(32, 2, 4);
+    else if (s <= 96) NSP_BLK(32, 3, 4);
+    else if (s <= 128) NSP_BLK(32, 4, 4);
+    else if (s <= 160) NSP_BLK(32, 5, 4);
+    else if (s <= 256) NSP_BLK(32, 8, 4);
+    else throw Error(NSP_ERR_UNSUPPORTED, "more than 256 right-hand sides");
+    return grid;
+  }
+  require(p.blk_rows == kSweepBlockRows, NSP_ERR_INVALID_ARG, "sweep plan tile rows");
   if (s <= 16) NSP_BLK(16, 1, 4);
   else if (s <= 32) NSP_BLK(16, 2, 4);
   else if (s <= 48) NSP_BLK(16, 3, 4);

@@ -39,6 +39,7 @@ struct CsrDev {
 struct SweepPlan {
   int32_t nitems = 0, nfwd = 0, max_m = 0;
   int32_t vec_cols = 0;  // columns per backward tile in vector mode (set by the plan)
+  int32_t blk_rows = 64; // rows / columns of a block tile (kSweepBlockRows or kSweepBlockRowsNarrow)
   bool vector = false;
   const int32_t *item_a = nullptr, *item_b = nullptr, *group_sn = nullptr;
   const int32_t *sn_parent = nullptr, *need_f = nullptr, *units_f = nullptr, *units_b = nullptr;
@@ -144,6 +145,8 @@ void launch_vsm_sweep(const ForestDev &f, const SweepPlan &p, const T *panel, co
 // rows of a forward tile in vector mode for elements of elem_bytes
 int sweep_vector_rows(int elem_bytes);
 constexpr int kSweepBlockRows = 64;   // rows (forward) / columns (backward) per block tile
+constexpr int kSweepBlockRowsNarrow = 32;   // the same for single-tree forests (A_G): twice the
+                                            // tiles per supernode along the tree's top chain
 constexpr int kSweepVectorCols = 16;  // default columns per backward tile in vector mode
 constexpr int kSmallM = 96, kSmallW = 32, kGroup = 8;
 // item_b of a subtree item: kSubtreeTag - L, item_a = offset of its L-entry member list
