@@ -665,6 +665,7 @@ def main():
                            nnz_L_interior=info0["nnz_L_interior"],
                            nnz_L_gamma=info0["nnz_L_gamma"],
                            step_ms_min=float(np.min(step_ms)),
+                           step_ms_each=[round(float(t), 3) for t in step_ms],
                            phase_ms={"factor": last["ms_factor"], "inner": last["ms_inner"],
                                      "core": last["ms_core"], "solve": last["ms_solve"]}),
             "roofline": {"bound": "hbm", "achieved": sweep_gbs, "peak": hbm, "unit": "GB/s",
