@@ -947,8 +947,11 @@ struct Engine : EngineBase {
   DBuf<int32_t> full_rowptr, full_col;   // A in caller order (FP64 residual)
   DBuf<int64_t> i2g_I, i2g_G, i2u_I, i2u_G;
   DBuf<double> Aval;
-  DBuf<T> panelI, panelG, front;
-  DBuf<DevStatus> dstat;
+  DBuf<T> panelI, panelG, front, frontG;   // fronts of the interior and the A_G factors
+  DBuf<DevStatus> dstat, dstatG;   // device status words (dstatG: the A_G factorization)
+  // the A_G factorization runs on its own stream beside the interior one (factorize)
+  cudaStream_t fstream = nullptr;
+  cudaEvent_t fev[2] = {nullptr, nullptr};
   DevStatus *hstat = nullptr;            // pinned
   double *hscal = nullptr;               // pinned scalars
   int32_t *hint = nullptr;               // pinned ints
@@ -993,8 +996,10 @@ struct Engine : EngineBase {
     Aval.alloc(an.nnz);
     panelI.alloc(FI.h.panel_size);
     panelG.alloc(FG.h.panel_size);
-    front.alloc(std::max(FI.h.front_size, FG.h.front_size));
+    front.alloc(std::max<int64_t>(FI.h.front_size, 1));
+    frontG.alloc(std::max<int64_t>(FG.h.front_size, 1));
     dstat.alloc(1);
+    dstatG.alloc(1);
     NSP_CUDA(cudaMallocHost(&hstat, sizeof(DevStatus)));
     NSP_CUDA(cudaMallocHost(&hscal, 16 * sizeof(double)));
     NSP_CUDA(cudaMallocHost(&hint, 16 * sizeof(int32_t)));
@@ -1011,6 +1016,9 @@ struct Engine : EngineBase {
   }
   ~Engine() override {
     if (gstream) cudaStreamDestroy(gstream);
+    if (fstream) cudaStreamDestroy(fstream);
+    for (cudaEvent_t e : fev)
+      if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : gev)
       if (e) cudaEventDestroy(e);
     if (h_any) cudaFreeHost(h_any);
@@ -1054,25 +1062,40 @@ struct Engine : EngineBase {
     A_GI.refresh(Aval.p, st);
     A_G.refresh(Aval.p, st);
     NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
-    factor_forest(FI, panelI.p);
-    check_factor_status(-1);
-    factor_forest(FG, panelG.p);
-    check_factor_status(an.nblocks);  // a failure in the A_G factor reports block nblocks
+    NSP_CUDA(cudaMemsetAsync(dstatG.p, 0, sizeof(DevStatus), st));
+    // The interior and the A_G factors are independent: A_G's (one tree whose top levels hold
+    // one or two large fronts each, so few CTAs are busy) runs on a second stream beside the
+    // interior one, each with its own fronts and status word, joined before the checks.
+    if (!fstream) {   // high priority: A_G's chain of large fronts is the critical path
+      int lo = 0, hi = 0;
+      NSP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+      NSP_CUDA(cudaStreamCreateWithPriority(&fstream, cudaStreamNonBlocking, hi));
+      NSP_CUDA(cudaEventCreateWithFlags(&fev[0], cudaEventDisableTiming));
+      NSP_CUDA(cudaEventCreateWithFlags(&fev[1], cudaEventDisableTiming));
+    }
+    NSP_CUDA(cudaEventRecord(fev[0], st));
+    NSP_CUDA(cudaStreamWaitEvent(fstream, fev[0], 0));
+    factor_forest(FG, panelG.p, frontG.p, dstatG.p, fstream);
+    factor_forest(FI, panelI.p, front.p, dstat.p, st);
+    NSP_CUDA(cudaEventRecord(fev[1], fstream));
+    NSP_CUDA(cudaStreamWaitEvent(st, fev[1], 0));
+    check_factor_status(dstat.p, -1);
+    check_factor_status(dstatG.p, an.nblocks);  // a failure in the A_G factor reports block nblocks
     info.ms_factor = ms_since(t0);
   }
 
-  void factor_forest(ForestData &F, T *panel) {
+  void factor_forest(ForestData &F, T *panel, T *fronts, DevStatus *status, cudaStream_t s) {
     for (int l = 0; l < F.h.nlevels; ++l) {
       const int c0 = F.h.level_ptr[l], c1 = F.h.level_ptr[l + 1], ns = F.level_small[l];
-      launch_factor_level<T>(F.dev, F.level_sn.p + c0, ns, Aval.p, front.p, panel, dstat.p, st,
+      launch_factor_level<T>(F.dev, F.level_sn.p + c0, ns, Aval.p, fronts, panel, status, s,
                              false);
-      launch_factor_level<T>(F.dev, F.level_sn.p + c0 + ns, c1 - c0 - ns, Aval.p, front.p,
-                             panel, dstat.p, st, true);
+      launch_factor_level<T>(F.dev, F.level_sn.p + c0 + ns, c1 - c0 - ns, Aval.p, fronts,
+                             panel, status, s, true);
     }
   }
 
-  void check_factor_status(int block_override) {
-    NSP_CUDA(cudaMemcpyAsync(hstat, dstat.p, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  void check_factor_status(const DevStatus *status, int block_override) {
+    NSP_CUDA(cudaMemcpyAsync(hstat, status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
     sync();
     if (hstat->code == DEV_NOT_SPD) {
       info.failed_block = block_override >= 0 ? block_override : hstat->aux;
