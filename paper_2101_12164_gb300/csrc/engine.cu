@@ -1015,6 +1015,7 @@ struct Engine : EngineBase {
     info.failed_block = -1;
   }
   ~Engine() override {
+    if (fstream) cudaStreamSynchronize(fstream);   // no kernel may outlive the buffers
     if (gstream) cudaStreamDestroy(gstream);
     if (fstream) cudaStreamDestroy(fstream);
     for (cudaEvent_t e : fev)
@@ -1078,10 +1079,22 @@ struct Engine : EngineBase {
     factor_forest(FG, panelG.p, frontG.p, dstatG.p, fstream);
     factor_forest(FI, panelI.p, front.p, dstat.p, st);
     NSP_CUDA(cudaEventRecord(fev[1], fstream));
-    NSP_CUDA(cudaStreamWaitEvent(st, fev[1], 0));
     check_factor_status(dstat.p, -1);
-    check_factor_status(dstatG.p, an.nblocks);  // a failure in the A_G factor reports block nblocks
+    // the A_G factor is joined where it is first needed (join_fg), so that the work of the
+    // build that needs only the interior factor overlaps its last fronts
+    fg_pending = true;
     info.ms_factor = ms_since(t0);
+  }
+
+  // Orders the handle's stream after the A_G factorization and checks its status (a failure
+  // in the A_G factor reports block nblocks). Called before every use of the A_G factor and
+  // at the end of a build.
+  bool fg_pending = false;
+  void join_fg() {
+    if (!fg_pending) return;
+    fg_pending = false;
+    NSP_CUDA(cudaStreamWaitEvent(st, fev[1], 0));
+    check_factor_status(dstatG.p, an.nblocks);
   }
 
   void factor_forest(ForestData &F, T *panel, T *fronts, DevStatus *status, cudaStream_t s) {
@@ -1257,6 +1270,7 @@ struct Engine : EngineBase {
     solve_forest(FI, panelI.p, B, Yw.p, Uw.p, X, sc);
   }
   void solve_G(const T *B, T *X, int sc) {
+    join_fg();
     ensure_ws(sc);
     solve_forest(FG, panelG.p, B, YwG.p, UwG.p, X, sc);
   }
@@ -1282,6 +1296,7 @@ struct Engine : EngineBase {
   // The column-sliced sweep where it has a plan for this width, else the block-resident one.
   DBuf<T> G1;
   void half_G(int half, const T *V, T *O, int sc) {
+    join_fg();
     FG.vec_rows = sweep_vector_rows((int)sizeof(T));
     FG.elem_bytes = (int)sizeof(T);
     auto &P = FG.plan(sc == 1, st);
@@ -1566,6 +1581,7 @@ struct Engine : EngineBase {
         build_adef(prm.drop_tol);
       sync();
     }
+    join_fg();
     info.ms_core = ms_since(t1);
   }
 
@@ -1956,6 +1972,7 @@ struct Engine : EngineBase {
       binfo[g].ms_core = ms_since(t1);
       rank = std::max(rank, rk[g]);
     }
+    join_fg();
     info.ms_inner = ms_in;
     info.ms_core = ms_since(t1);
   }
@@ -2244,6 +2261,7 @@ struct Engine : EngineBase {
   void get_factor(int block, int64_t *order, double *L, int64_t nb) override {
     require(block >= 0 && block <= an.nblocks, NSP_ERR_INVALID_ARG, "block id");
     const bool g = block == an.nblocks;
+    join_fg();
     const Forest &F = g ? FG.h : FI.h;
     const int b = g ? 0 : block;
     const int64_t off = F.block_off[b], n_b = F.block_off[b + 1] - off;
