@@ -121,7 +121,8 @@ def test_both_sweep_schedulers_match_oracle(N, torch, monkeypatch, sched, name, 
     # the sweeps without dependency waits ("smem": for one right-hand side each block's
     # vectors in shared memory, for several one CTA per block and 32-column slice, widths
     # that are not a multiple of 4 falling back to the block-resident sweep) compute the same
-    # A_I^{-1} B and S_Gamma X; each is forced here (the autotuner keeps only the fastest)
+    # A_I^{-1} B, A_G^{-1} B and S_Gamma X; each is forced here (the autotuner keeps only the
+    # fastest)
     monkeypatch.setenv("NSP_SWEEP", sched)
     A, part, nsub = _case(name)
     D = O.DBBD(A, part, nsub)
@@ -137,8 +138,12 @@ def test_both_sweep_schedulers_match_oracle(N, torch, monkeypatch, sched, name, 
     Xg = torch.tensor(X, dtype=dt, device="cuda")
     Yg = torch.empty_like(Xg)
     h.schur_apply(Xg, Yg)
+    Zg = torch.empty_like(Xg)
+    h.factor_solve(1, Xg, Zg)
     torch.cuda.synchronize()
     err = colwise_err(Xd.double().cpu().numpy().reshape(D.n_I, s), D.solve_I(B))
+    assert err < tol, err
+    err = colwise_err(Zg.double().cpu().numpy().reshape(D.n_G, s), D.solve_G(X))
     assert err < tol, err
     err = colwise_err(Yg.double().cpu().numpy().reshape(D.n_G, s), D.apply_S_gamma(X))
     assert err < (1e-9 if prec == "fp64" else 1e-3), err
