@@ -1089,6 +1089,12 @@ struct Engine : EngineBase {
   // Orders the handle's stream after the A_G factorization and checks its status (a failure
   // in the A_G factor reports block nblocks). Called before every use of the A_G factor and
   // at the end of a build.
+  static constexpr int kFewFronts = 4;
+  // NSP_BIGCLUSTER=0 keeps 8-CTA clusters for every large front (measurements)
+  static bool big_fronts_enabled() {
+    const char *e = std::getenv("NSP_BIGCLUSTER");
+    return !(e && e[0] == '0');
+  }
   bool fg_pending = false;
   void join_fg() {
     if (!fg_pending) return;
@@ -1100,10 +1106,12 @@ struct Engine : EngineBase {
   void factor_forest(ForestData &F, T *panel, T *fronts, DevStatus *status, cudaStream_t s) {
     for (int l = 0; l < F.h.nlevels; ++l) {
       const int c0 = F.h.level_ptr[l], c1 = F.h.level_ptr[l + 1], ns = F.level_small[l];
-      launch_factor_level<T>(F.dev, F.level_sn.p + c0, ns, Aval.p, fronts, panel, status, s,
-                             false);
-      launch_factor_level<T>(F.dev, F.level_sn.p + c0 + ns, c1 - c0 - ns, Aval.p, fronts,
-                             panel, status, s, true);
+      // fronts below kBigFront rows one CTA each; larger ones a cluster each, of 16 CTAs
+      // where the level holds at most kFewFronts of them (the top of a single tree)
+      const int nbig = c1 - c0 - ns;
+      launch_factor_level<T>(F.dev, F.level_sn.p + c0, ns, Aval.p, fronts, panel, status, s, 0);
+      launch_factor_level<T>(F.dev, F.level_sn.p + c0 + ns, nbig, Aval.p, fronts, panel, status,
+                             s, nbig <= kFewFronts && big_fronts_enabled() ? 2 : 1);
     }
   }
 

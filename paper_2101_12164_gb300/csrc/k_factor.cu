@@ -385,16 +385,82 @@ __global__ void __cluster_dims__(CLUSTER, 1, 1) __launch_bounds__(FT, FactorOcc<
   factor_front<T, CLUSTER>(f, level_sn[blockIdx.x / CLUSTER], Aval, front, panel, st, sm);
 }
 
+// Levels with few large fronts (the top of the A_G tree): clusters of 16 CTAs (a size the
+// hardware allows only on request), with a dynamic shared-memory request that leaves room for
+// one CTA per SM, so that each front gets twice the SMs of an 8-CTA cluster.
+constexpr int CLUSTER_BIG = 16;
+constexpr size_t kBigFrontPad = 120 * 1024;   // dynamic shared memory, unused: one CTA per SM
+
+template <typename T>
+__global__ void __launch_bounds__(FT, 1)
+    k_factor_cluster16(ForestDev f, const int32_t *level_sn, const double *Aval, T *front,
+                       T *panel, DevStatus *st) {
+  __shared__ FactorSmem<T> sm;
+  factor_front<T, CLUSTER_BIG>(f, level_sn[blockIdx.x / CLUSTER_BIG], Aval, front, panel, st, sm);
+}
+
+// whether a 16-CTA cluster of k_factor_cluster16 can be resident on this device
+template <typename T>
+bool big_clusters_ok() {
+  static int ok = -1;
+  if (ok >= 0) return ok == 1;
+  ok = 0;
+  if (cudaFuncSetAttribute(k_factor_cluster16<T>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                           1) != cudaSuccess ||
+      cudaFuncSetAttribute(k_factor_cluster16<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kBigFrontPad) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CLUSTER_BIG, 1, 1);
+  cfg.blockDim = dim3(FT, 1, 1);
+  cfg.dynamicSmemBytes = kBigFrontPad;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = CLUSTER_BIG;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_factor_cluster16<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ok = clusters >= 1 ? 1 : 0;
+  return ok == 1;
+}
+
 }  // namespace
 
 int factor_cluster_size() { return CLUSTER; }
 
 template <typename T>
+bool factor_big_clusters_available() {
+  return big_clusters_ok<T>();
+}
+
+template <typename T>
 void launch_factor_level(const ForestDev &f, const int32_t *level_sn, int count,
                          const double *Aval, T *front, T *panel, DevStatus *st,
-                         cudaStream_t stream, bool clustered) {
+                         cudaStream_t stream, int mode) {
   if (count <= 0) return;
-  if (clustered) {
+  if (mode == 2 && big_clusters_ok<T>()) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(count * CLUSTER_BIG, 1, 1);
+    cfg.blockDim = dim3(FT, 1, 1);
+    cfg.dynamicSmemBytes = kBigFrontPad;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = CLUSTER_BIG;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    NSP_CUDA(cudaLaunchKernelEx(&cfg, k_factor_cluster16<T>, f, level_sn, Aval, front, panel, st));
+  } else if (mode >= 1) {
     k_factor_cluster<T><<<count * CLUSTER, FT, 0, stream>>>(f, level_sn, Aval, front, panel, st);
   } else {
     k_factor<T><<<count, FT, 0, stream>>>(f, level_sn, Aval, front, panel, st);
@@ -402,9 +468,11 @@ void launch_factor_level(const ForestDev &f, const int32_t *level_sn, int count,
   NSP_LAUNCH_CHECK();
 }
 
+template bool factor_big_clusters_available<float>();
+template bool factor_big_clusters_available<double>();
 template void launch_factor_level<float>(const ForestDev &, const int32_t *, int, const double *,
-                                         float *, float *, DevStatus *, cudaStream_t, bool);
+                                         float *, float *, DevStatus *, cudaStream_t, int);
 template void launch_factor_level<double>(const ForestDev &, const int32_t *, int, const double *,
-                                          double *, double *, DevStatus *, cudaStream_t, bool);
+                                          double *, double *, DevStatus *, cudaStream_t, int);
 
 }  // namespace nsp

@@ -92,11 +92,14 @@ struct SweepPlan {
 // Multifrontal partial Cholesky of the supernodes level_sn[0..count) (one CTA each), then
 // the panel [inv(L_JJ); L_J2 inv(L_JJ)] (column-major, leading dimension panel_ld(m)).
 // A non-positive pivot records DEV_NOT_SPD with the supernode's block id.
-// clustered: each front is factorized by a cluster of factor_cluster_size() CTAs.
 template <typename T>
 void launch_factor_level(const ForestDev &f, const int32_t *level_sn, int count,
                          const double *Aval, T *front, T *panel, DevStatus *st,
-                         cudaStream_t stream, bool clustered);
+                         cudaStream_t stream, int mode);
+// mode: 0 one CTA per front, 1 a cluster of factor_cluster_size() CTAs per front, 2 a cluster
+// of 16 CTAs, one per SM, per front (where factor_big_clusters_available(), else mode 1)
+template <typename T>
+bool factor_big_clusters_available();
 int factor_cluster_size();
 constexpr int kBigFront = 192;   // fronts with m >= kBigFront use the cluster kernel
 
