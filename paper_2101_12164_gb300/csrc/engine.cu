@@ -1089,12 +1089,14 @@ struct Engine : EngineBase {
   // Orders the handle's stream after the A_G factorization and checks its status (a failure
   // in the A_G factor reports block nblocks). Called before every use of the A_G factor and
   // at the end of a build.
+  // NSP_BIGCLUSTER=0 keeps 8-CTA clusters for every large front; =n uses 16-CTA clusters on
+  // levels with at most n large fronts (measurements; default kFewFronts)
   static constexpr int kFewFronts = 4;
-  // NSP_BIGCLUSTER=0 keeps 8-CTA clusters for every large front (measurements)
-  static bool big_fronts_enabled() {
+  static int few_fronts() {
     const char *e = std::getenv("NSP_BIGCLUSTER");
-    return !(e && e[0] == '0');
+    return e ? std::max(0, std::atoi(e)) : kFewFronts;
   }
+  static bool big_fronts_enabled() { return few_fronts() > 0; }
   bool fg_pending = false;
   void join_fg() {
     if (!fg_pending) return;
@@ -1111,7 +1113,7 @@ struct Engine : EngineBase {
       const int nbig = c1 - c0 - ns;
       launch_factor_level<T>(F.dev, F.level_sn.p + c0, ns, Aval.p, fronts, panel, status, s, 0);
       launch_factor_level<T>(F.dev, F.level_sn.p + c0 + ns, nbig, Aval.p, fronts, panel, status,
-                             s, nbig <= kFewFronts && big_fronts_enabled() ? 2 : 1);
+                             s, nbig <= few_fronts() ? 2 : 1);
     }
   }
 
