@@ -965,6 +965,24 @@ struct Engine : EngineBase {
   DBuf<double> K, Cn, Mix, Sigma, nys_work, Zs;
   DBuf<int32_t> mask, nkept, drank;
   DBuf<double> g64, ri_buf, zi_buf;
+  // The sketch into g64: the caller's, or `count` Gaussian values drawn from prm.seed, unless
+  // g64 already holds that very draw (a rebuild with the same seed draws the same sketch).
+  uint64_t g64_seed = 0;
+  size_t g64_count = 0;   // Gaussian values of g64_seed held in g64 (0: none)
+  void draw_sketch(const nsp_params &prm, size_t count) {
+    const size_t cap = g64.n;
+    g64.ensure(count);
+    if (g64.n != cap) g64_count = 0;   // reallocated: nothing held
+    if (prm.sketch) {
+      NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, count * sizeof(double), cudaMemcpyDefault, st));
+      g64_count = 0;
+      return;
+    }
+    if (g64_count == count && g64_seed == prm.seed) return;
+    launch_gaussian<double>(prm.seed, (int64_t)count, g64.p, st);
+    g64_seed = prm.seed;
+    g64_count = count;
+  }
   bool keep = false;
   // outer PCG vectors (FP64)
   DBuf<double> vb, vx, vr, vz, vp, vq, vt, vu, vf, dwork, dscal;
@@ -1452,21 +1470,11 @@ struct Engine : EngineBase {
     // (n_interior x s, interior order) goes straight into the block-PCG right-hand side Fh
     if (m3) {
       const size_t nis = (size_t)an.nI * s;
-      g64.ensure(nis);
-      if (prm.sketch) {
-        NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, nis * sizeof(double), cudaMemcpyDefault, st));
-      } else {
-        launch_gaussian<double>(prm.seed, (int64_t)nis, g64.p, st);
-      }
+      draw_sketch(prm, nis);
       launch_gather_rows<double, T>(i2u_I.p, an.nI, g64.p, Fh.p, s, st);
       sync();
     } else {
-      g64.ensure(ns);
-      if (prm.sketch) {
-        NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyDefault, st));
-      } else {
-        launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
-      }
+      draw_sketch(prm, ns);
       launch_gather_rows<double, T>(i2u_G.p, an.nG, g64.p, G.p, s, st);
       if (m1) {   // keep G for the core; the block PCG runs on R^{-1} G
         G1.ensure(ns);
@@ -1904,12 +1912,7 @@ struct Engine : EngineBase {
     bactive.ensure(nseg);
     bscal.ensure(16 * (size_t)nseg);
     NSP_CUDA(cudaMemsetAsync(dstat.p, 0, sizeof(DevStatus), st));
-    g64.ensure(ns);
-    if (prm.sketch) {
-      NSP_CUDA(cudaMemcpyAsync(g64.p, prm.sketch, ns * sizeof(double), cudaMemcpyDefault, st));
-    } else {
-      launch_gaussian<double>(prm.seed, (int64_t)ns, g64.p, st);
-    }
+    draw_sketch(prm, ns);
     launch_gather_rows<double, T>(i2u_G.p, an.nG, g64.p, G.p, s, st);
     // block PCG for every matrix at once (per-matrix scalars, one sweep per operator)
     schur_apply(G.p, Fh.p, s, false);
