@@ -599,6 +599,7 @@ struct ForestData {
         if (lev.empty()) continue;
         std::vector<int32_t> cur;
         int nf = 0;
+        int64_t nsrc = 0;
         auto close = [&]() {
           if (cur.empty()) return;
           const int i0 = (int)item.size() / 3;
@@ -628,17 +629,26 @@ struct ForestData {
             ub += nub;
           }
           positions = std::max(positions, fo);
+          const int sb = pptr[pos_base];
           bat.push_back(int4{i0, i0 + (int)cur.size(), fo, uf});
           bat.push_back(int4{ub, 0, pos_base, unit_base});
-          bat.push_back(int4{col_base, 0, 0, 0});
+          bat.push_back(int4{col_base, sb, (int)psrc.size() - sb, 0});
           cur.clear();
           nf = 0;
+          nsrc = 0;
         };
+        // a batch's plan data is staged in shared memory: at most kBsmMaxItems supernodes
+        // and kBsmMaxSources gather sources per batch
         for (int J : lev) {
           const int ld = (int)panel_ld(h.sn_m[J]);
-          if (nf + ld > maxpos || cur.size() >= 65535) close();
+          const int64_t rp = h.sn_rowptr[J];
+          const int64_t js = h.gptr[rp + h.sn_m[J]] - h.gptr[rp];
+          if (js > kBsmMaxSources) return;
+          if (nf + ld > maxpos || (int)cur.size() >= kBsmMaxItems || nsrc + js > kBsmMaxSources)
+            close();
           cur.push_back(J);
           nf += ld;
+          nsrc += js;
         }
         close();
         bptr.push_back((int)bat.size() / 3);

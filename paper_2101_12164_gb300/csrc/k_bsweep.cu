@@ -33,13 +33,87 @@ constexpr int BCQ = BCS / 4;            // column quads per position
 struct BsItem {
   int fo, uf, ub, m, w, first, upd;
   int64_t po;
-  __device__ void load(const int4 *items, int i) {
-    const int4 a = __ldg(&items[3 * i]), b = __ldg(&items[3 * i + 1]), c = __ldg(&items[3 * i + 2]);
+  __device__ void load(const int4 *items, int i) {   // the batch's shared-memory copy
+    const int4 a = items[3 * i], b = items[3 * i + 1], c = items[3 * i + 2];
     fo = a.x; uf = a.y; ub = a.z; m = a.w;
     w = b.x; first = b.y; upd = b.z;
     po = (int64_t)(uint32_t)c.x | ((int64_t)c.y << 32);
   }
 };
+
+// Shared-memory copies of a batch's plan data (item records, per-position data, unit items,
+// gather sources), staged once at the start of the batch in one round of loads.
+constexpr int kMetaPos = 1536 + 16;                       // positions (+1), padded
+constexpr int kMetaUnits = 1536 + 3 * kBsmMaxItems + 16;  // forward or backward units
+struct BsMeta {
+  int4 *items;       // 3 x kBsmMaxItems
+  int32_t *pptr;     // kMetaPos: gather-source offsets, relative to the batch's first source
+  int32_t *pvi;      // kMetaPos: B / Y / X rows
+  uint16_t *uit;     // kMetaUnits: item (relative) of each unit
+  int32_t *psrc;     // kBsmMaxSources
+};
+constexpr size_t kMetaBytes =
+    16 * 3 * kBsmMaxItems + 4 * 2 * kMetaPos + 2 * kMetaUnits + 4 * kBsmMaxSources;
+static_assert(kMetaPos > kBsmScratchBytes / (kBsmCols * 4), "a batch's positions (+1) fit");
+static_assert(kMetaUnits >= kBsmScratchBytes / (kBsmCols * 4), "a batch's units fit");
+static_assert(kBsmScratchBytes + 16 + kMetaBytes <= 227 * 1024, "fronts + plan data fit");
+__device__ __forceinline__ BsMeta meta_at(unsigned char *base) {
+  BsMeta M;
+  M.items = reinterpret_cast<int4 *>(base);
+  M.pptr = reinterpret_cast<int32_t *>(M.items + 3 * kBsmMaxItems);
+  M.pvi = M.pptr + kMetaPos;
+  M.psrc = M.pvi + kMetaPos;
+  M.uit = reinterpret_cast<uint16_t *>(M.psrc + kBsmMaxSources);
+  return M;
+}
+
+// every load of the staging issued before any shared-memory store
+__device__ __forceinline__ void bs_stage_meta(const BsMeta &M, const int4 *items, int i0, int ni,
+                                              const int32_t *pptr, const int32_t *pvi, int pb,
+                                              int nf, const uint16_t *uit, int ubase, int nu,
+                                              const int32_t *psrc, int sb, int nsrc) {
+  const int tid = threadIdx.x;
+  constexpr int KP = (kMetaPos + BT - 1) / BT, KU = (kMetaUnits + BT - 1) / BT,
+                KS = (kBsmMaxSources + BT - 1) / BT;
+  static_assert(3 * kBsmMaxItems <= BT, "one item word per thread");
+  const int4 it = tid < 3 * ni ? __ldg(&items[3 * i0 + tid]) : make_int4(0, 0, 0, 0);
+  int32_t vp[KP], vv[KP], vs[KS];
+  uint16_t vu[KU];
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int j = tid + k * BT;
+    vp[k] = (pptr && j <= nf) ? __ldg(&pptr[pb + j]) : 0;
+    vv[k] = j < nf ? __ldg(&pvi[pb + j]) : 0;
+  }
+#pragma unroll
+  for (int k = 0; k < KU; ++k) {
+    const int j = tid + k * BT;
+    vu[k] = j < nu ? __ldg(&uit[ubase + j]) : (uint16_t)0;
+  }
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const int j = tid + k * BT;
+    vs[k] = j < nsrc ? __ldg(&psrc[sb + j]) : 0;
+  }
+  if (tid < 3 * ni) M.items[tid] = it;
+#pragma unroll
+  for (int k = 0; k < KP; ++k) {
+    const int j = tid + k * BT;
+    if (pptr && j <= nf) M.pptr[j] = vp[k] - sb;
+    if (j < nf) M.pvi[j] = vv[k];
+  }
+#pragma unroll
+  for (int k = 0; k < KU; ++k) {
+    const int j = tid + k * BT;
+    if (j < nu) M.uit[j] = vu[k];
+  }
+#pragma unroll
+  for (int k = 0; k < KS; ++k) {
+    const int j = tid + k * BT;
+    if (j < nsrc) M.psrc[j] = vs[k];
+  }
+  __syncthreads();
+}
 
 template <typename T>
 struct V4;
@@ -90,10 +164,13 @@ constexpr int BNR = 8;   // position quads per thread in flight in the gathers
 
 template <typename T>
 __device__ void bs_forward(const SweepPlan &p, const T *panel, const T *B, T *Y, T *U, int s,
-                           int c0, int ncq, T *fs, int q) {
-  const int4 B0 = __ldg(&p.bs_bat[3 * q]), B1 = __ldg(&p.bs_bat[3 * q + 1]);
+                           int c0, int ncq, T *fs, const BsMeta &M, int q) {
+  const int4 B0 = __ldg(&p.bs_bat[3 * q]), B1 = __ldg(&p.bs_bat[3 * q + 1]),
+             B2 = __ldg(&p.bs_bat[3 * q + 2]);
   const int i0 = B0.x, nf = B0.z, nu = B0.w, pb = B1.z, ubase = B1.w;
   const int tid = threadIdx.x;
+  bs_stage_meta(M, p.bs_item, i0, B0.y - i0, p.bs_pptr, p.bs_pfvi, pb, nf, p.bs_uitem, ubase, nu,
+                p.bs_psrc, B2.y, B2.z);
   // (A) fronts: flat over (position, column quad), BNR in flight per thread
   const int nt = nf * BCQ;
   for (int t0 = tid; t0 < nt; t0 += BNR * BT) {
@@ -106,9 +183,9 @@ __device__ void bs_forward(const SweepPlan &p, const T *panel, const T *B, T *Y,
 #pragma unroll
       for (int i = 0; i < 4; ++i) val[h].a[i] = T(0);
       if (t < nt && cq < ncq) {
-        e[h] = __ldg(&p.bs_pptr[pb + pp]);
-        ee[h] = __ldg(&p.bs_pptr[pb + pp + 1]);
-        const int row = __ldg(&p.bs_pfvi[pb + pp]);
+        e[h] = M.pptr[pp];
+        ee[h] = M.pptr[pp + 1];
+        const int row = M.pvi[pp];
         if (row >= 0) val[h].ld(B + (size_t)row * s + c0 + 4 * cq);
       }
     }
@@ -116,7 +193,7 @@ __device__ void bs_forward(const SweepPlan &p, const T *panel, const T *B, T *Y,
     while (more) {
       int32_t src[BNR];
 #pragma unroll
-      for (int h = 0; h < BNR; ++h) src[h] = e[h] < ee[h] ? __ldg(&p.bs_psrc[e[h]]) : -1;
+      for (int h = 0; h < BNR; ++h) src[h] = e[h] < ee[h] ? M.psrc[e[h]] : -1;
       more = false;
 #pragma unroll
       for (int h = 0; h < BNR; ++h)
@@ -140,7 +217,7 @@ __device__ void bs_forward(const SweepPlan &p, const T *panel, const T *B, T *Y,
   // group are consecutive units
   for (int u = tid; u < nu; u += BT) {
     BsItem I;
-    I.load(p.bs_item, i0 + __ldg(&p.bs_uitem[ubase + u]));
+    I.load(M.items, M.uit[u]);
     const int lu = u - I.uf, rg = lu >> 2, cg = lu & 3;
     if (2 * cg >= ncq) continue;   // beyond the slice's last column
     const int w = I.w, m = I.m, ld = (m + 3) & ~3, row = 4 * rg;
@@ -216,11 +293,13 @@ __device__ void bs_forward(const SweepPlan &p, const T *panel, const T *B, T *Y,
 
 template <typename T>
 __device__ void bs_backward(const SweepPlan &p, const T *panel, const T *Y, T *X, int s, int c0,
-                            int ncq, T *gs, int q) {
+                            int ncq, T *gs, const BsMeta &M, int q) {
   const int4 B0 = __ldg(&p.bs_bat[3 * q]), B1 = __ldg(&p.bs_bat[3 * q + 1]),
              B2 = __ldg(&p.bs_bat[3 * q + 2]);
   const int i0 = B0.x, nf = B0.z, nc = B1.x, pb = B1.z, cbase = B2.x;
   const int tid = threadIdx.x;
+  bs_stage_meta(M, p.bs_item, i0, B0.y - i0, nullptr, p.bs_pbvi, pb, nf, p.bs_citem, cbase, nc,
+                p.bs_psrc, 0, 0);
   // (A) g = [y_J; -x(rows below); 0 padding], flat over (position, column quad)
   const int nt = nf * BCQ;
   for (int t0 = tid; t0 < nt; t0 += BNR * BT) {
@@ -231,7 +310,7 @@ __device__ void bs_backward(const SweepPlan &p, const T *panel, const T *Y, T *X
 #pragma unroll
       for (int i = 0; i < 4; ++i) val[h].a[i] = T(0);
       if (t < nt && cq < ncq) {
-        const int vi = __ldg(&p.bs_pbvi[pb + pp]);
+        const int vi = M.pvi[pp];
         if (vi >= 0) {
           val[h].ldcg(Y + (size_t)vi * s + c0 + 4 * cq);
         } else if (vi < -1) {
@@ -251,7 +330,7 @@ __device__ void bs_backward(const SweepPlan &p, const T *panel, const T *Y, T *X
   // (B) unit = (item, 4 panel columns, 8 slice columns): x[cols] = P[:, cols]^T g
   for (int u = tid; u < nc; u += BT) {
     BsItem I;
-    I.load(p.bs_item, i0 + __ldg(&p.bs_citem[cbase + u]));
+    I.load(M.items, M.uit[u]);
     const int lu = u - I.ub, qg = lu >> 2, cg = lu & 3;
     if (2 * cg >= ncq) continue;
     const int w = I.w, ld = (I.m + 3) & ~3, col = 4 * qg;
@@ -305,22 +384,24 @@ __device__ void bs_backward(const SweepPlan &p, const T *panel, const T *Y, T *X
   __syncthreads();
 }
 
-// CTA = (block, column slice); shared memory: the batch scratch (positions x kBsmCols)
+// CTA = (block, column slice); shared memory: the batch scratch (positions x kBsmCols), then
+// the batch's plan data (BsMeta)
 template <typename T>
 __global__ void __launch_bounds__(BT, 1)
     k_bsm_sweep(SweepPlan p, const T *__restrict__ panel, const T *B, T *Y, T *U, T *X, int s,
                 int nslices, int half) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *scr = reinterpret_cast<T *>(smem_raw);
+  const BsMeta M = meta_at(smem_raw + (((size_t)p.bs_positions * BCS * sizeof(T) + 15) & ~(size_t)15));
   const int b = blockIdx.x / nslices, sl = blockIdx.x - b * nslices;
   const int c0 = sl * BCS, ncq = min(BCS, s - c0) / 4;
   const int L0 = p.bs_lvl_ptr[b], L1 = p.bs_lvl_ptr[b + 1];
   for (int L = L0; L < L1 && half != 2; ++L)
     for (int q = p.bs_bat_ptr[L]; q < p.bs_bat_ptr[L + 1]; ++q)
-      bs_forward<T>(p, panel, B, Y, U, s, c0, ncq, scr, q);
+      bs_forward<T>(p, panel, B, Y, U, s, c0, ncq, scr, M, q);
   for (int L = L1 - 1; L >= L0 && half != 1; --L)
     for (int q = p.bs_bat_ptr[L]; q < p.bs_bat_ptr[L + 1]; ++q)
-      bs_backward<T>(p, panel, Y, X, s, c0, ncq, scr, q);
+      bs_backward<T>(p, panel, Y, X, s, c0, ncq, scr, M, q);
 }
 
 }  // namespace
@@ -338,7 +419,7 @@ void launch_bsm_sweep(const SweepPlan &p, const T *panel, const T *B, T *Y, T *U
           "column-sliced block sweep: no plan for this width");
   require(half >= 0 && half <= 2, NSP_ERR_INVALID_ARG, "column-sliced block sweep: bad half");
   const int nslices = (s + BCS - 1) / BCS;
-  const size_t smem = (size_t)p.bs_positions * BCS * sizeof(T);
+  const size_t smem = (((size_t)p.bs_positions * BCS * sizeof(T) + 15) & ~(size_t)15) + kMetaBytes;
   static size_t attr = 0;
   if (smem > attr) {
     ensure_dyn_smem(k_bsm_sweep<T>, smem);

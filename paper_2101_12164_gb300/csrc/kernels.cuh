@@ -74,7 +74,8 @@ struct SweepPlan {
   int32_t vs_scratch = 0;
   // Block plans, column-sliced sweep (k_bsweep.cu): the same height / batch structure, with
   // batch q (bs_bat[3q..3q+2]) = {first item, end item, front positions, forward units},
-  // {backward units, 0, first position, first forward unit}, {first backward unit, 0, 0, 0};
+  // {backward units, 0, first position, first forward unit}, {first backward unit, first
+  // gather source, gather sources, 0};
   // item i (bs_item[3i..3i+2]) = {front offset, first forward unit, first backward unit, m},
   // {w, first row, first update row, 0}, {sn_panel low, high, 0, 0}. Per front position:
   // bs_pfvi forward row of B (top rows; -1: none), bs_pbvi backward source (row of Y for top
@@ -132,7 +133,9 @@ constexpr int kResW = 32, kResM = 128;   // block mode: supernodes a warp runs (
 // s > 1 (s a multiple of 4) with one CTA per (block, slice of kBsmCols columns), heights in
 // batches, no dependency waits (k_bsweep.cu); Y, U workspaces as launch_sweep's.
 constexpr int kBsmCols = 32;
-constexpr int kBsmScratchBytes = 192 * 1024;
+constexpr int kBsmScratchBytes = 192 * 1024;   // fronts of a batch
+constexpr int kBsmMaxItems = 128;              // supernodes per batch
+constexpr int kBsmMaxSources = 2560;           // gather sources per batch
 template <typename T>
 bool bsm_sweep_fits(const SweepPlan &p, int s);
 template <typename T>
