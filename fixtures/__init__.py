@@ -13,7 +13,7 @@ Nothing in this package computes any step of the preconditioner itself.
 from .seeds import substream_seed, rng_for, MASTER_SEED
 from .grids import grid_coords, diffusion_matrix
 from .fields import gaussian_field, gaussian_grid_field, lognormal_field, lognormal_grid_field
-from .partition import nd_partition, interior_nd_order
+from .partition import nd_partition, interior_nd_order, interface_partition
 from .configs import (CONFIGS, Problem, make_problem, make_rhs, make_sketch, make_probe,
                       sample_rows,
                       batched_problem_specs, problem_from_spec)
@@ -21,7 +21,7 @@ from .configs import (CONFIGS, Problem, make_problem, make_rhs, make_sketch, mak
 __all__ = [
     "substream_seed", "rng_for", "MASTER_SEED", "grid_coords", "diffusion_matrix",
     "gaussian_field", "gaussian_grid_field", "lognormal_field", "lognormal_grid_field",
-    "nd_partition", "interior_nd_order",
+    "nd_partition", "interior_nd_order", "interface_partition",
     "CONFIGS", "Problem", "make_problem", "make_rhs", "make_sketch", "make_probe",
     "sample_rows",
     "batched_problem_specs", "problem_from_spec",

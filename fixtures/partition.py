@@ -87,3 +87,41 @@ def interior_nd_order(shape, boxes, leaf=16):
     """Concatenated nested-dissection orders of all subdomain boxes (block by block)."""
     shape = tuple(int(s) for s in shape)
     return np.concatenate([_box_nd_order(list(lo), list(hi), shape, leaf) for lo, hi in boxes])
+
+
+def interface_partition(A_G, coords, nblocks):
+    """A DBBD partition of the interface matrix A_Gamma itself (its own §2.3 eq. (perm_A)
+    form), for the recursive treatment of A_Gamma.
+
+    Recursive coordinate bisection of the interface nodes' coordinates (median split of the
+    widest axis, depth-first numbering) gives nblocks boxes; every edge of A_Gamma that joins
+    two boxes puts its endpoint in the higher-numbered box on the second-level separator
+    (label -1), so no edge is left between interior nodes of different boxes.
+    Returns part2 (int32, n_Gamma entries in A_Gamma's row order).
+    """
+    import scipy.sparse as sp
+    levels = int(round(np.log2(nblocks)))
+    if 1 << levels != nblocks:
+        raise ValueError("nblocks must be a power of two")
+    coords = np.asarray(coords, dtype=np.float64)
+    n = coords.shape[0]
+    box = np.zeros(n, dtype=np.int32)
+
+    def rec(idx, depth, label):
+        if depth == levels:
+            box[idx] = label
+            return label + 1
+        c = coords[idx]
+        ax = int(np.argmax(c.max(axis=0) - c.min(axis=0)))
+        order = idx[np.argsort(c[:, ax], kind="stable")]
+        h = len(order) // 2
+        label = rec(order[:h], depth + 1, label)
+        return rec(order[h:], depth + 1, label)
+
+    rec(np.arange(n), 0, 0)
+    C = sp.coo_matrix(A_G)
+    cut = box[C.row] != box[C.col]
+    hi = np.where(box[C.row[cut]] > box[C.col[cut]], C.row[cut], C.col[cut])
+    part = box.copy()
+    part[hi] = -1
+    return part

@@ -18,6 +18,9 @@ Everything here is plain, slow and follows the paper step by step in float64:
                              optionally with q power iterations (§2.1 eq. (power)).
 * ``build_m1``             : the variant M1 of §4.1 with a dense R_Gamma (small interfaces).
 * ``build_m3``             : the variant M3 of §4.3 (Nyström on S_I^{-1}), and M_{3A-DEF}.
+* ``recursive_gamma``      : the recursive treatment of A_Gamma (concluding section): A_Gamma^{-1}
+                             replaced by a block elimination of A_Gamma's own DBBD split whose
+                             Schur solve is that split's M2 (``NestedGammaInverse``).
 * ``M2ADEF``               : the adapted-deflation variant M_{2A-DEF} of §4.3 (defined
                              like eq. (deflation_comp_from_low_rank) and eq.
                              (our_two_level_preconditioner), moved through Z = A_G^{-1} U).
@@ -380,6 +383,57 @@ def build_m3(dbbd, G_I, k, eps_inner=0.1, eps_rel=1e-10, maxit=500, drop_tol=1e-
     if variant != "M3":
         raise ValueError(variant)
     return M2(dbbd, Zh, Sigma), info
+
+
+# ----------------------------------------------------------------------------------------
+# Recursive treatment of A_Gamma (concluding section: the systems with A_Gamma replaced by
+# systems with a much smaller matrix). Reading: A_Gamma gets a DBBD split of its own (§2.3
+# eq. (perm_A) applied to A_Gamma, interior blocks C_i and a second-level interface Gamma_2),
+# and A_Gamma^{-1} is replaced by the block elimination of §2.3 eq. (A_LDLT) for that split
+# whose Schur-complement solve is the two-level preconditioner M2 of that split (Algorithm 2
+# on A_Gamma). Only C_i and C_Gamma_2 are factorized.
+# ----------------------------------------------------------------------------------------
+class NestedGammaInverse:
+    """x = A_Gamma~^{-1} b for A_Gamma = [[C_I, C_IG2], [C_G2I, C_G2]] (rows of A_Gamma split by
+    the DBBD ``d2``): y = C_I^{-1} b_I, x_G2 = M2' (b_G2 - C_G2I y), x_I = C_I^{-1} (b_I - C_IG2
+    x_G2), with M2' the two-level preconditioner of S_C = C_G2 - C_G2I C_I^{-1} C_IG2. It is
+    A_Gamma^{-1} exactly when M2' = S_C^{-1}."""
+
+    def __init__(self, d2, m2):
+        self.d2, self.m2 = d2, m2
+
+    def apply(self, B):
+        d2 = self.d2
+        B = np.asarray(B, dtype=np.float64)
+        bI, bG = B[d2.interior], B[d2.gamma]
+        y = d2.solve_I(bI)
+        xG = self.m2.apply(bG - d2.A_GI @ y)
+        xI = d2.solve_I(bI - d2.A_IG @ xG)
+        X = np.empty_like(B)
+        X[d2.interior] = xI
+        X[d2.gamma] = xG
+        return X
+
+
+def recursive_gamma(dbbd, part2, nblocks2, G2, k2, eps_inner=0.1, eps_rel=1e-10, maxit=500,
+                    drop_tol=1e-12):
+    """The DBBD ``dbbd`` with A_Gamma^{-1} replaced by the nested two-level inverse.
+
+    part2: DBBD partition of A_Gamma (rows in dbbd.gamma order; labels in [0, nblocks2) or
+    -1 for Gamma_2); G2: the nested sketch (n_Gamma_2 x (k2 + p2), Gamma_2 unknowns in
+    increasing row order of A_Gamma). Algorithm 2 runs on A_Gamma's split (S_Gamma form).
+    Returns (dbbd', info): dbbd' is a shallow copy whose solve_G applies the nested inverse
+    (apply_S_gamma is unchanged: S_Gamma stays exact); build_m2(dbbd', ...) is then the
+    recursive M2 = A_Gamma~^{-1} + Z Sigma Z^T with Z = A_Gamma~^{-1} U, and
+    solve(dbbd', ...) its outer PCG. Only the S_Gamma inner form is meant for dbbd'.
+    """
+    import copy
+    d2 = DBBD(dbbd.A_G, part2, nblocks2)
+    m2, info2 = build_m2(d2, G2, k2, eps_inner, "S_gamma", eps_rel, maxit, drop_tol)
+    inv = NestedGammaInverse(d2, m2)
+    out = copy.copy(dbbd)
+    out.solve_G = inv.apply
+    return out, dict(d2=d2, m2=m2, inverse=inv, it_inner=info2["it_inner"], info=info2)
 
 
 # ----------------------------------------------------------------------------------------
