@@ -156,6 +156,32 @@ typedef struct {
                                 (steps 2-4) and the columns are orthonormalized after it by
                                 Cholesky-QR (a column whose pivot falls below drop_tol of its
                                 squared norm becomes zero). Batched handles: q = 0 only      */
+  /* Recursive treatment of A_G (concluding section: the systems with A_G replaced by systems
+   * with a much smaller matrix). gamma_levels = 0 (default): A_G is factorized directly.
+   * gamma_levels = 1: A_G gets a DBBD split of its own (§2.3 eq. (perm_A) applied to A_G:
+   * interior blocks C_i, a second-level interface G2) and every A_G^{-1} of the build and of
+   * the preconditioner (the block-PCG preconditioner of step 3, Z = A_G^{-1} U of step 11, the
+   * A_G^{-1} r of each M2 application, nsp_factor_solve(which = 1)) becomes the block
+   * elimination of §2.3 eq. (A_LDLT) for that split whose Schur-complement solve is the M2 of
+   * the split, M2' (Algorithm 2 on A_G, S_Gamma form, with gamma_k, gamma_p, gamma_eps_inner,
+   * the sketch gamma_sketch or one drawn from seed + 1, and the handle's other parameters):
+   *   y = C_I^{-1} b_I,  x_G2 = M2' (b_G2 - C_G2I y),  x_I = C_I^{-1} (b_I - C_IG2 x_G2).
+   * Only the C_i and C_G2 are factorized. It equals A_G^{-1} when M2' = S_C^{-1} (the Schur
+   * complement of C_I in A_G). Requires the M2 variant, the S_Gamma inner form and q = 0
+   * (NSP_ERR_UNSUPPORTED otherwise; batched handles: gamma_levels = 0 only). The split is
+   * fixed at nsp_build: nsp_rebuild refuses a change of gamma_levels and reads neither
+   * gamma_part nor gamma_nblocks. nsp_get_factor refuses the A_G block of such a handle.   */
+  int32_t gamma_levels;      /* 0 or 1                                                     */
+  int32_t gamma_nblocks;     /* interior blocks of A_G's split (>= 1)                       */
+  const int32_t *gamma_part; /* host, n_Gamma labels in the caller's Gamma order (increasing
+                                index in A): [0, gamma_nblocks), or -1 for G2; no entry of
+                                A_G may couple two different blocks (NSP_ERR_NOT_DBBD)     */
+  int32_t gamma_k;           /* Nyström rank of M2' (> 0)                                  */
+  int32_t gamma_p;           /* oversampling of M2' (>= 0), gamma_k + gamma_p <= n_G2, 256 */
+  double gamma_eps_inner;    /* relative tolerance of M2''s block PCG                       */
+  const double *gamma_sketch;/* optional sketch of M2', host, n_G2 x (gamma_k + gamma_p)
+                                row-major, G2 unknowns in increasing index in A; NULL =
+                                drawn from seed + 1                                         */
 } nsp_params;
 
 typedef struct {
@@ -183,12 +209,17 @@ typedef struct {
    * same numbers: its iterates equal the Schur form's). 0 when no iteration ran; batched
    * handles leave them 0.                                                                  */
   double lambda_min_est, lambda_max_est, kappa_est;
+  /* gamma_levels = 1: size of the second-level interface G2, block-PCG iterations and
+   * Nyström rank of M2' at the last build (0 otherwise)                                    */
+  int64_t n_gamma2;
+  int32_t it_inner_gamma, rank_gamma;
 } nsp_info;
 
 typedef struct nsp_handle nsp_handle;
 
 /* Defaults: k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=1e-12 (FP64) /
- * 1e-6 (FP32), max_inner_it=500, precision=NSP_FP32, AUTO outer form, seed=210112164. */
+ * 1e-6 (FP32), max_inner_it=500, precision=NSP_FP32, AUTO outer form, seed=210112164,
+ * gamma_levels=0 (gamma_k=16, gamma_p=8, gamma_eps_inner=0.1, no gamma_part/gamma_sketch). */
 void nsp_default_params(nsp_params *prm);
 
 /* Algorithm 2 end to end: analysis of A's pattern and the partition (host), numeric

@@ -55,7 +55,10 @@ class nsp_params(C.Structure):
                 ("max_inner_it", C.c_int32), ("seed", C.c_uint64), ("sketch", C.c_void_p),
                 ("precision", C.c_int32), ("outer_form", C.c_int32), ("inner_form", C.c_int32),
                 ("keep_intermediates", C.c_int32), ("stream", C.c_void_p),
-                ("variant", C.c_int32), ("q", C.c_int32)]
+                ("variant", C.c_int32), ("q", C.c_int32),
+                ("gamma_levels", C.c_int32), ("gamma_nblocks", C.c_int32),
+                ("gamma_part", C.c_void_p), ("gamma_k", C.c_int32), ("gamma_p", C.c_int32),
+                ("gamma_eps_inner", C.c_double), ("gamma_sketch", C.c_void_p)]
 
 
 class nsp_net_shape(C.Structure):
@@ -75,7 +78,8 @@ class nsp_info(C.Structure):
                 ("ms_factor", C.c_double), ("ms_inner", C.c_double), ("ms_core", C.c_double),
                 ("ms_solve", C.c_double), ("it_power", C.c_int32),
                 ("lambda_min_est", C.c_double), ("lambda_max_est", C.c_double),
-                ("kappa_est", C.c_double)]
+                ("kappa_est", C.c_double), ("n_gamma2", C.c_int64),
+                ("it_inner_gamma", C.c_int32), ("rank_gamma", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -198,7 +202,8 @@ def nsp_default_params():
 def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
                 max_inner_it=500, seed=210112164, sketch=None, precision="fp32",
                 outer_form="auto", keep_intermediates=False, stream=None, keep=None,
-                variant="m2", q=0, inner_form="s_gamma"):
+                variant="m2", q=0, inner_form="s_gamma", gamma_part=None, gamma_nblocks=0,
+                gamma_k=16, gamma_p=8, gamma_eps_inner=0.1, gamma_sketch=None):
     prm = nsp_default_params()
     prm.k, prm.p = int(k), int(p)
     prm.eps_inner, prm.eps_trunc_rel = float(eps_inner), float(eps_trunc_rel)
@@ -224,6 +229,25 @@ def make_params(k=16, p=10, eps_inner=0.1, eps_trunc_rel=1e-10, drop_tol=None,
         if keep is not None:
             keep.append(sk)
         prm.sketch = _ptr(sk)
+    # recursive A_G: its own DBBD split (labels in the caller's Gamma order) and M2' settings
+    if gamma_part is not None:
+        gp = np.ascontiguousarray(gamma_part, dtype=np.int32)
+        if keep is not None:
+            keep.append(gp)
+        prm.gamma_levels, prm.gamma_nblocks = 1, int(gamma_nblocks)
+        prm.gamma_part = _ptr(gp)
+    if gamma_sketch is not None:
+        gs = np.ascontiguousarray(gamma_sketch, dtype=np.float64)
+        if gamma_part is not None:
+            rows = int((np.asarray(gamma_part) < 0).sum())
+            if gs.size < rows * (int(gamma_k) + int(gamma_p)):
+                raise ValueError("gamma_sketch holds %d values; the build reads %d x %d"
+                                 % (gs.size, rows, int(gamma_k) + int(gamma_p)))
+        if keep is not None:
+            keep.append(gs)
+        prm.gamma_sketch = _ptr(gs)
+    prm.gamma_k, prm.gamma_p = int(gamma_k), int(gamma_p)
+    prm.gamma_eps_inner = float(gamma_eps_inner)
     prm.stream = _stream() if stream is None else stream
     return prm
 
@@ -443,6 +467,7 @@ class Handle:
         prm = make_params(keep=keep, **kw) if kw else None
         if prm is not None:
             prm.stream = self.prm.stream
+            prm.gamma_levels = self.prm.gamma_levels   # the A_G split is fixed at the build
         st = lib().nsp_rebuild(self._handle(), _ptr(val), 1 if on_device else 0,
                                C.byref(prm) if prm is not None else None)
         _check(st, "nsp_rebuild")

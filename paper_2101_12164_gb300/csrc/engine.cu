@@ -940,6 +940,7 @@ struct EngineBase {
   virtual nsp_status timeout_selftest(int max_spins) = 0;
   virtual void schur_apply_noalloc(const void *X, void *Y, int s, unsigned char *scratch) = 0;
   virtual void factor_solve_user(int which, const void *B, void *X, int s) = 0;
+  virtual void attach_gamma(const nsp_params &prm) = 0;
   virtual void get_basis(double *Z, double *Sigma, int32_t *rank) = 0;
   virtual void get_intermediate(int which, double *out) = 0;
   virtual void get_factor(int block, int64_t *order, double *L, int64_t nb) = 0;
@@ -1101,6 +1102,19 @@ struct Engine : EngineBase {
       NSP_CUDA(cudaStreamCreateWithPriority(&fstream, cudaStreamNonBlocking, hi));
       NSP_CUDA(cudaEventCreateWithFlags(&fev[0], cudaEventDisableTiming));
       NSP_CUDA(cudaEventCreateWithFlags(&fev[1], cudaEventDisableTiming));
+    }
+    if (gnest) {   // recursive A_G: the nested handle factorizes A_G's blocks and G2 block
+      factor_forest(FI, panelI.p, front.p, dstat.p, st);
+      check_factor_status(dstat.p, -1);
+      launch_gather_values<double>(gnest_src.p, (int64_t)gnest_src.n, Aval.p, gnest_val.p, st);
+      try {
+        gnest->factorize(gnest_val.p, true);
+      } catch (const Error &e) {   // a failed nested block reports the A_G block
+        info.failed_block = an.nblocks;
+        throw;
+      }
+      info.ms_factor = ms_since(t0);
+      return;
     }
     NSP_CUDA(cudaEventRecord(fev[0], st));
     NSP_CUDA(cudaStreamWaitEvent(fstream, fev[0], 0));
@@ -1308,9 +1322,132 @@ struct Engine : EngineBase {
     solve_forest(FI, panelI.p, B, Yw.p, Uw.p, X, sc);
   }
   void solve_G(const T *B, T *X, int sc) {
+    if (gnest) {
+      gnest->nested_inverse(B, X, sc);
+      return;
+    }
     join_fg();
     ensure_ws(sc);
     solve_forest(FG, panelG.p, B, YwG.p, UwG.p, X, sc);
+  }
+
+  // ---- Recursive treatment of A_G (concluding section: systems with A_G replaced by systems
+  // with a much smaller matrix). The nested handle gnest is an Engine on A_G itself, rows and
+  // columns in this handle's internal Gamma order, split by the caller's gamma_part into
+  // interior blocks C_i and a second-level interface G2; its Algorithm 2 gives M2' for the
+  // Schur complement S_C = C_G2 - C_G2I C_I^{-1} C_IG2, and A_G^{-1} is replaced by the block
+  // elimination of §2.3 eq. (A_LDLT) with M2' as the Schur solve (nested_inverse).
+  std::unique_ptr<Engine<T>> gnest;
+  DBuf<int64_t> gnest_src;             // nested CSR entry -> index into A's values
+  DBuf<double> gnest_val;              // nested CSR values
+  std::vector<int64_t> gnest_row;      // caller sketch row j (G2 in increasing index) -> row
+  std::vector<double> gnest_sketch;    // the caller's nested sketch in the nested order
+  void attach_gamma(const nsp_params &prm) override {
+    const HostSub &S = an.A_G;         // rows: internal Gamma order; columns: the same order
+    std::vector<int64_t> rp(an.nG + 1, 0), src;
+    std::vector<int32_t> col;
+    src.reserve(S.col.size());
+    col.reserve(S.col.size());
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int32_t r = 0; r < S.nrows; ++r) {
+      row.clear();
+      for (int32_t q = S.rowptr[r]; q < S.rowptr[r + 1]; ++q) row.push_back({S.col[q], S.src[q]});
+      std::sort(row.begin(), row.end());
+      for (const auto &e : row) {
+        col.push_back(e.first);
+        src.push_back(e.second);
+      }
+      rp[r + 1] = (int64_t)col.size();
+    }
+    // labels in the nested order (internal Gamma index t <- caller Gamma index i2u_G[t])
+    std::vector<int32_t> part2(an.nG);
+    for (int64_t t = 0; t < an.nG; ++t) part2[t] = prm.gamma_part[an.i2u_G[t]];
+    static const double unused_value = 0.0;   // the nested analysis reads the pattern only
+    nsp_csr c{an.nG, rp.data(), col.data(), &unused_value, 0};
+    nsp_partition P2{prm.gamma_nblocks, part2.data(), nullptr};
+    gnest.reset(new Engine<T>(&c, rp.data(), col.data(), &P2, st));
+    gnest_src.upload(src, st);
+    gnest_val.alloc(src.size());
+    // the nested caller order of G2 is increasing t; the caller's is increasing index in A
+    std::vector<int64_t> u2t(an.nG), pos(an.nG, -1);
+    for (int64_t t = 0; t < an.nG; ++t) u2t[an.i2u_G[t]] = t;
+    int64_t q = 0;
+    for (int64_t t = 0; t < an.nG; ++t)
+      if (part2[t] < 0) pos[t] = q++;
+    gnest_row.clear();
+    for (int64_t u = 0; u < an.nG; ++u)
+      if (prm.gamma_part[u] < 0) gnest_row.push_back(pos[u2t[u]]);
+    // the full A_G factor is not needed: its panels and fronts are released
+    panelG.release();
+    frontG.release();
+    info.nnz_L_gamma = gnest->FI.h.nnz_L + gnest->FG.h.nnz_L;
+    info.n_gamma2 = gnest->an.nG;
+    NSP_CUDA(cudaStreamSynchronize(st));   // the uploads read host vectors of this scope
+  }
+  // M2' of the nested handle (Algorithm 2 on A_G's split) with the handle's parameters
+  void construct_gamma(const nsp_params &prm) {
+    nsp_params p2 = prm;
+    p2.k = prm.gamma_k;
+    p2.p = prm.gamma_p;
+    p2.eps_inner = prm.gamma_eps_inner;
+    p2.seed = prm.seed + 1;
+    p2.sketch = nullptr;
+    p2.keep_intermediates = 0;
+    p2.gamma_levels = 0;
+    p2.gamma_sketch = nullptr;
+    const int s2 = prm.gamma_k + prm.gamma_p;
+    require(s2 <= gnest->an.nG, NSP_ERR_INVALID_ARG, "gamma_k + gamma_p exceeds the size of G2");
+    if (prm.gamma_sketch) {
+      gnest_sketch.assign((size_t)gnest->an.nG * s2, 0.0);
+      for (size_t j = 0; j < gnest_row.size(); ++j)
+        std::memcpy(&gnest_sketch[(size_t)gnest_row[j] * s2], prm.gamma_sketch + j * s2,
+                    s2 * sizeof(double));
+      p2.sketch = gnest_sketch.data();
+    }
+    gnest->construct(p2);
+    gnest->prepare_nested();
+    info.it_inner_gamma = gnest->info.it_inner;
+    info.rank_gamma = gnest->rank;
+  }
+  // (on the nested handle) Zsig = Zt Sigma, the low-rank term of M2' in the handle precision
+  DBuf<T> nz_sig, nz_bI, nz_bG, nz_y, nz_r, nz_z;
+  DBuf<double> nz_dg, nz_c;
+  void prepare_nested() {
+    if (rank <= 0) return;
+    std::vector<double> sig(k), dg((size_t)k * k, 0.0);
+    NSP_CUDA(cudaMemcpyAsync(sig.data(), Sigma.p, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    for (int j = 0; j < k; ++j) dg[(size_t)j * k + j] = sig[j];
+    nz_dg.upload(dg, st);
+    nz_sig.ensure((size_t)an.nG * k);
+    block_update(Zt.p, nz_dg.p, an.nG, k, k, T(1), nullptr, T(0), nz_sig.p);
+    sync();
+  }
+  // (on the nested handle) X = A_G~^{-1} B, B and X in this handle's caller order (= the
+  // outer handle's internal Gamma order), sc columns:
+  //   y = C_I^{-1} b_I, r = b_G2 - C_G2I y, x_G2 = C_G2^{-1} r + Zt Sigma Zt^T r,
+  //   x_I = C_I^{-1} (b_I - C_IG2 x_G2)
+  void nested_inverse(const T *B, T *X, int sc) {
+    const size_t ni = (size_t)an.nI * sc, ng = (size_t)an.nG * sc;
+    nz_bI.ensure(ni);
+    nz_y.ensure(ni);
+    nz_bG.ensure(ng);
+    nz_r.ensure(ng);
+    nz_z.ensure(ng);
+    launch_gather_rows<T, T>(i2g_I.p, an.nI, B, nz_bI.p, sc, st);
+    launch_gather_rows<T, T>(i2g_G.p, an.nG, B, nz_bG.p, sc, st);
+    solve_I(nz_bI.p, nz_y.p, sc);
+    launch_spmm<T>(A_GI.dT(), nz_y.p, nz_r.p, sc, T(-1), nz_bG.p, T(1), st);
+    solve_G(nz_r.p, nz_z.p, sc);
+    if (rank > 0) {
+      nz_c.ensure((size_t)k * sc);
+      gram_n(Zt.p, nz_r.p, an.nG, k, sc, nz_c.p);                      // Zt^T r
+      block_update(nz_sig.p, nz_c.p, an.nG, k, sc, T(1), nz_z.p, T(1), nz_z.p);
+    }
+    launch_spmm<T>(A_IG.dT(), nz_z.p, nz_bI.p, sc, T(-1), nz_bI.p, T(1), st);
+    solve_I(nz_bI.p, nz_y.p, sc);
+    launch_scatter_rows<T, T>(i2g_I.p, an.nI, nz_y.p, X, sc, st);
+    launch_scatter_rows<T, T>(i2g_G.p, an.nG, nz_z.p, X, sc, st);
   }
 
   // ---- S_Gamma X (with_AG) or A_GI A_I^{-1} A_IG X (internal Gamma order)
@@ -1334,6 +1471,7 @@ struct Engine : EngineBase {
   // The column-sliced sweep where it has a plan for this width, else the block-resident one.
   DBuf<T> G1;
   void half_G(int half, const T *V, T *O, int sc) {
+    require(!gnest, NSP_ERR_UNSUPPORTED, "half sweeps need the A_G factor (gamma_levels = 0)");
     join_fg();
     FG.vec_rows = sweep_vector_rows((int)sizeof(T));
     FG.elem_bytes = (int)sizeof(T);
@@ -1446,6 +1584,7 @@ struct Engine : EngineBase {
     const bool m1 = variant == NSP_VARIANT_M1;
     require(!m1 || prm.q == 0, NSP_ERR_UNSUPPORTED, "M1 takes no power iterations");
     keep = prm.keep_intermediates != 0;
+    if (gnest) construct_gamma(prm);
     ensure_ws(s);
     const size_t ns = (size_t)an.nG * s;
     // block-PCG vector length: n_Gamma (S_Gamma form) or n_interior (S_I form)
@@ -2284,6 +2423,7 @@ struct Engine : EngineBase {
   void get_factor(int block, int64_t *order, double *L, int64_t nb) override {
     require(block >= 0 && block <= an.nblocks, NSP_ERR_INVALID_ARG, "block id");
     const bool g = block == an.nblocks;
+    require(!(g && gnest), NSP_ERR_UNSUPPORTED, "A_G is not factorized (gamma_levels = 1)");
     join_fg();
     const Forest &F = g ? FG.h : FI.h;
     const int b = g ? 0 : block;
@@ -2375,6 +2515,10 @@ void nsp_default_params(nsp_params *prm) {
   prm->inner_form = NSP_FORM_SGAMMA;
   prm->keep_intermediates = 0;
   prm->stream = nullptr;
+  prm->gamma_levels = 0;
+  prm->gamma_k = 16;
+  prm->gamma_p = 8;
+  prm->gamma_eps_inner = 0.1;
 }
 
 const char *nsp_last_error(void) { return nsp::g_last_error.c_str(); }
@@ -2419,7 +2563,11 @@ static void validate_params(const nsp_params *prm, bool batched) {
   nsp::require(prm != nullptr, NSP_ERR_INVALID_ARG, "params");
   nsp::require(prm->precision == NSP_FP64 || prm->precision == NSP_FP32, NSP_ERR_INVALID_ARG,
                "precision");
+  nsp::require(prm->gamma_levels == 0 || prm->gamma_levels == 1, NSP_ERR_INVALID_ARG,
+               "gamma_levels must be 0 or 1");
   if (batched) {
+    nsp::require(prm->gamma_levels == 0, NSP_ERR_UNSUPPORTED,
+                 "batched handles factorize A_G directly (gamma_levels = 0)");
     nsp::require(prm->variant == NSP_VARIANT_M2, NSP_ERR_UNSUPPORTED,
                  "batched handles build M2 only");
     nsp::require(prm->q == 0, NSP_ERR_UNSUPPORTED, "batched handles take no power iterations");
@@ -2435,6 +2583,22 @@ static void validate_params(const nsp_params *prm, bool batched) {
   nsp::require(prm->variant >= NSP_VARIANT_M2 && prm->variant <= NSP_VARIANT_M1,
                NSP_ERR_INVALID_ARG, "unknown preconditioner variant");
   nsp::require(prm->q >= 0 && prm->q <= 16, NSP_ERR_INVALID_ARG, "power iterations q in [0, 16]");
+  if (prm->gamma_levels == 1) {
+    nsp::require(prm->variant == NSP_VARIANT_M2 && prm->inner_form == NSP_FORM_SGAMMA &&
+                     prm->q == 0,
+                 NSP_ERR_UNSUPPORTED,
+                 "the recursive A_G takes the M2 variant, the S_Gamma inner form and q = 0");
+    nsp::require(prm->gamma_k > 0 && prm->gamma_p >= 0, NSP_ERR_INVALID_ARG,
+                 "gamma_k > 0 and gamma_p >= 0 required");
+    nsp::require(prm->gamma_k + prm->gamma_p <= 256, NSP_ERR_UNSUPPORTED, "gamma_k + gamma_p > 256");
+  }
+}
+
+// the A_G split of a recursive build (nsp_build only: nsp_rebuild keeps the build's split)
+static void validate_gamma_split(const nsp_params *prm) {
+  if (prm->gamma_levels == 1)
+    nsp::require(prm->gamma_part && prm->gamma_nblocks >= 1, NSP_ERR_INVALID_ARG,
+                 "gamma_levels = 1 needs gamma_part and gamma_nblocks >= 1");
 }
 
 nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params *prm,
@@ -2445,6 +2609,7 @@ nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params 
   nsp_status s = guard([&] {
     nsp::validate_csr(A);
     validate_params(prm, false);
+    validate_gamma_split(prm);
     h->prm = *prm;
     std::vector<int64_t> rp;
     std::vector<int32_t> ci;
@@ -2459,6 +2624,7 @@ nsp_status nsp_build(const nsp_csr *A, const nsp_partition *P, const nsp_params 
       cip = ci.data();
     }
     h->eng.reset(make_engine(A, rpp, cip, P, prm));
+    if (prm->gamma_levels == 1) h->eng->attach_gamma(*prm);
     h->eng->factorize(A->val, A->on_device != 0);
     h->eng->construct(h->prm);
   });
@@ -2568,6 +2734,8 @@ nsp_status nsp_rebuild(nsp_handle *h, const double *val, int32_t on_device, cons
   return guard([&] {
     if (prm) {
       nsp::require(prm->precision == h->prm.precision, NSP_ERR_INVALID_ARG, "precision change");
+      nsp::require(prm->gamma_levels == h->prm.gamma_levels, NSP_ERR_INVALID_ARG,
+                   "gamma_levels change");
       validate_params(prm, h->batch > 0);
       void *stream = h->prm.stream;
       h->prm = *prm;

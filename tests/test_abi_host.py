@@ -154,3 +154,19 @@ def test_parameters_checked_on_the_host_before_device_work():
     # valid requests pass the checks (then build, or fail later at the device on a CPU machine)
     for f in (dict(), dict(variant=3), dict(q=2), dict(inner_form=1)):
         assert _build_status(N, A, part, 2, **f) not in (1, 9), f
+    # the recursive A_G: gamma_levels in {0, 1}; a split is required; M2, S_Gamma form, q = 0;
+    # single handles only
+    gp = np.zeros(int((part < 0).sum()), dtype=np.int32)
+    g = dict(gamma_levels=1, gamma_nblocks=1, gamma_part=N._ptr(gp))
+    assert _build_status(N, A, part, 2, gamma_levels=2) == 1
+    assert _build_status(N, A, part, 2, gamma_levels=1) == 1                 # no split
+    assert _build_status(N, A, part, 2, **dict(g, gamma_nblocks=0)) == 1
+    assert _build_status(N, A, part, 2, **dict(g, gamma_k=0)) == 1
+    assert _build_status(N, A, part, 2, **dict(g, gamma_k=200, gamma_p=100)) == 9
+    for f in (dict(variant=1), dict(variant=2), dict(variant=4), dict(inner_form=1), dict(q=1)):
+        assert _build_status(N, A, part, 2, **dict(g, **f)) == 9, f
+    assert _build_status(N, A, part, 2, batched=True, **g) == 9
+    gv = np.array([0, 0, 0, -1, 1, 1, 1, 1], dtype=np.int32)   # the 8-node interface line
+    assert gv.size == gp.size
+    assert _build_status(N, A, part, 2, gamma_levels=1, gamma_nblocks=2, gamma_part=N._ptr(gv),
+                         gamma_k=1, gamma_p=0) not in (1, 9)
