@@ -172,7 +172,7 @@ def sweep_algorithmic_bytes(info, s, wbytes):
 # dependency-driven sweep at 64^3; profiles/sweep_bsm_lognormal3d_64.md: the column-sliced
 # sweep at 128^3), keyed by (configuration, s, precision); absent until captured for the
 # current kernel.
-SWEEP_TRAFFIC = {(1, 80, "fp32"): 768.0e6, (4, 160, "fp32"): 11.89e9}
+SWEEP_TRAFFIC = {(1, 80, "fp32"): 768.0e6, (4, 160, "fp32"): 11.87e9}
 
 
 def sub_nnz(P):
@@ -545,10 +545,21 @@ def main():
         h3.destroy()
         return dict(kw, ms_per_step=float(np.mean(v_ms)), it_inner=last["it_inner"],
                     it_power=last["it_power"], it_pcg=last["it_pcg"], final_residual=v_res,
+                    it_inner_gamma=last["it_inner_gamma"],
                     phase_ms={"factor": last["ms_factor"], "inner": last["ms_inner"],
                               "core": last["ms_core"], "solve": last["ms_solve"]})
 
     variant_line = time_variant(variant="m2_adef" if args.variant == "m2" else "m2")
+    # the recursive treatment of A_Gamma: A_Gamma split into 64 blocks by coordinate
+    # bisection of the interface nodes, its Schur solve M2' of rank 32 (16 oversampling)
+    recursive_line = None
+    if args.variant == "m2":
+        g_idx = P.gamma
+        part2 = F.interface_partition(P.A[g_idx][:, g_idx], P.coords[g_idx], 64)
+        recursive_line = time_variant(variant="m2", gamma_part=part2, gamma_nblocks=64,
+                                      gamma_k=32, gamma_p=16, gamma_eps_inner=P.eps_inner)
+        recursive_line.pop("gamma_part")
+        recursive_line["n_gamma2"] = int((part2 < 0).sum())
     # the plain FP64 GPU form (FP64 factors, inner block PCG and sweeps) of the timed step
     fp64_line = time_variant(variant=args.variant, precision="fp64")
     extra = {}
@@ -683,6 +694,7 @@ def main():
             "gram": gram,
             "errors_vs_oracle": errors,
             "other_variant": variant_line,
+            "gamma_recursive": recursive_line,
             "plain_fp64": fp64_line,
             "second_workload": second,
             "batched_workload": batched,

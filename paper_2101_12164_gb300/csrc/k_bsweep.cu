@@ -230,22 +230,50 @@ __device__ void bs_forward(const SweepPlan &p, const T *panel, const T *B, T *Y,
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
     int k = 0;
-    for (; k + 7 < kmax; k += 8) {
+    if constexpr (sizeof(T) == 4) {
+      // eight panel rows of K in flight as a ring: each is reloaded for the next chunk of
+      // eight as soon as its products are issued, so the loads overlap the FMAs
+      const int kfull = kmax & ~7;
       V4<T> pv[8];
+      if (kfull > 0) {
 #pragma unroll
-      for (int t = 0; t < 8; ++t) pv[t].ld(P + (size_t)(k + t) * ld);
+        for (int t = 0; t < 8; ++t) pv[t].ld(P + (size_t)t * ld);
+      }
+      for (; k < kfull; k += 8) {
+        const bool more = k + 8 < kfull;
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        V4<T> f0, f1;
-        f0.lds(F + (size_t)(k + t) * BCS);
-        f1.lds(F + (size_t)(k + t) * BCS + 4);
+        for (int t = 0; t < 8; ++t) {
+          V4<T> f0, f1;
+          f0.lds(F + (size_t)(k + t) * BCS);
+          f1.lds(F + (size_t)(k + t) * BCS + 4);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < 4; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            acc[i][j] += pv[t].a[i] * f0.a[j];
-            acc[i][4 + j] += pv[t].a[i] * f1.a[j];
-          }
+            for (int j = 0; j < 4; ++j) {
+              acc[i][j] += pv[t].a[i] * f0.a[j];
+              acc[i][4 + j] += pv[t].a[i] * f1.a[j];
+            }
+          if (more) pv[t].ld(P + (size_t)(k + 8 + t) * ld);
+        }
+      }
+    } else {   // FP64: the ring needs more registers than 128 (spills); chunks of eight
+      for (; k + 7 < kmax; k += 8) {
+        V4<T> pv[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) pv[t].ld(P + (size_t)(k + t) * ld);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          V4<T> f0, f1;
+          f0.lds(F + (size_t)(k + t) * BCS);
+          f1.lds(F + (size_t)(k + t) * BCS + 4);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              acc[i][j] += pv[t].a[i] * f0.a[j];
+              acc[i][4 + j] += pv[t].a[i] * f1.a[j];
+            }
+        }
       }
     }
     for (; k < kmax; ++k) {
@@ -342,31 +370,73 @@ __device__ void bs_backward(const SweepPlan &p, const T *panel, const T *Y, T *X
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
-    // P_top is lower triangular: rows >= col; eight rows of the four columns in flight
-    for (int k = col; k < ld; k += 8) {
-      const bool hi = k + 4 < ld;
+    if constexpr (sizeof(T) == 4) {
+      // P_top is lower triangular: rows >= col. Eight rows of the four columns in flight as a
+      // ring of two quads per column: a quad is reloaded for the next chunk of eight rows as
+      // soon as its products are issued
       V4<T> pc[8];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (i < ncol) {
-          pc[i].ld(Pc + (size_t)i * ld + k);
-          if (hi) pc[4 + i].ld(Pc + (size_t)i * ld + k + 4);
-        }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        if (t >= 4 && !hi) break;
-        V4<T> g0, g1;
-        g0.lds(G + (size_t)(k + t) * BCS);
-        g1.lds(G + (size_t)(k + t) * BCS + 4);
+      {
+        const bool hi = col + 4 < ld;
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-          if (i < ncol)
+          if (i < ncol) {
+            pc[i].ld(Pc + (size_t)i * ld + col);
+            if (hi) pc[4 + i].ld(Pc + (size_t)i * ld + col + 4);
+          }
+      }
+      for (int k = col; k < ld; k += 8) {
+        const bool hi = k + 4 < ld, more = k + 8 < ld, more_hi = k + 12 < ld;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-              const T pk = pc[(t >> 2) * 4 + i].a[t & 3];
-              acc[i][j] += pk * g0.a[j];
-              acc[i][4 + j] += pk * g1.a[j];
-            }
+        for (int h = 0; h < 2; ++h) {
+          if (h == 1 && !hi) break;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            V4<T> g0, g1;
+            g0.lds(G + (size_t)(k + 4 * h + t) * BCS);
+            g1.lds(G + (size_t)(k + 4 * h + t) * BCS + 4);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (i < ncol)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  const T pk = pc[4 * h + i].a[t];
+                  acc[i][j] += pk * g0.a[j];
+                  acc[i][4 + j] += pk * g1.a[j];
+                }
+          }
+          if (h == 0 ? more : more_hi) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+              if (i < ncol) pc[4 * h + i].ld(Pc + (size_t)i * ld + k + 8 + 4 * h);
+          }
+        }
+      }
+    } else {   // FP64: chunks of eight rows (the ring spills at 128 registers)
+      for (int k = col; k < ld; k += 8) {
+        const bool hi = k + 4 < ld;
+        V4<T> pc[8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (i < ncol) {
+            pc[i].ld(Pc + (size_t)i * ld + k);
+            if (hi) pc[4 + i].ld(Pc + (size_t)i * ld + k + 4);
+          }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          if (t >= 4 && !hi) break;
+          V4<T> g0, g1;
+          g0.lds(G + (size_t)(k + t) * BCS);
+          g1.lds(G + (size_t)(k + t) * BCS + 4);
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (i < ncol)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                const T pk = pc[(t >> 2) * 4 + i].a[t & 3];
+                acc[i][j] += pk * g0.a[j];
+                acc[i][4 + j] += pk * g1.a[j];
+              }
+        }
       }
     }
     const bool two = 2 * cg + 1 < ncq;
