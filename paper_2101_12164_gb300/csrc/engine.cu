@@ -1994,7 +1994,8 @@ struct Engine : EngineBase {
   Chunks chG, chF, chU;                   // Gamma rows, internal full rows, caller rows
   DBuf<double> bwork, bscal, bK, bC, bSig;
   DBuf<int32_t> bactive;
-  std::vector<int32_t> h_active;
+  DBuf<int32_t> bits_in, bact_in, bgo, bpass;   // inner block-PCG bookkeeping of a batch
+  DBuf<double> brat_in;
   std::vector<int64_t> seg_nG;            // interface size of every matrix
 
   void setup_batch(const std::vector<int64_t> &mat_off) override {
@@ -2070,13 +2071,23 @@ struct Engine : EngineBase {
     NSP_CUDA(cudaMemsetAsync(E.p, 0, ns * sizeof(T), st));
     NSP_CUDA(cudaMemcpyAsync(R.p, Fh.p, ns * sizeof(T), cudaMemcpyDeviceToDevice, st));
     solve_G(R.p, W.p, s);
-    h_active.assign(nseg, 1);
-    std::vector<int32_t> its(nseg, 0), act_cols(nseg, s);
+    // Per-matrix bookkeeping on the device (k_seg_inner_decide, which also masks the matrices
+    // that stopped): the first iteration runs eagerly, so that every plan and workspace of the
+    // loop exists, the others as a device-driven CUDA graph loop with no host decision.
+    bits_in.ensure(nseg);
+    brat_in.ensure(nseg);
+    bact_in.ensure(nseg);
+    bgo.ensure(1);
+    bpass.ensure(2);
+    std::vector<int32_t> its(nseg, 0), act_cols(nseg, s), ones(nseg, 1);
     std::vector<double> rat(nseg, 1.0);
-    NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    std::vector<double> hr(nseg);
-    std::vector<int32_t> hk(nseg);
-    for (int it = 0; it < prm.max_inner_it; ++it) {
+    NSP_CUDA(cudaMemcpyAsync(bactive.p, ones.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NSP_CUDA(cudaMemcpyAsync(bits_in.p, its.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NSP_CUDA(cudaMemcpyAsync(bact_in.p, act_cols.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    NSP_CUDA(cudaMemcpyAsync(brat_in.p, rat.data(), nseg * sizeof(double), cudaMemcpyHostToDevice, st));
+    NSP_CUDA(cudaMemsetAsync(bpass.p, 0, 2 * sizeof(int32_t), st));
+    // Q = S W, P and Q made S-orthonormal, E += P alpha, R -= Q alpha, then the stopping rule
+    auto first_half = [&](cudaGraphConditionalHandle h, int set_cond) {
       schur_apply(W.p, Z.p, s, true);
       launch_seg_gram<T, T>(W.p, Z.p, s, s, chG.d, Cg.p, bwork.p, st);
       launch_chol_drop(Cg.p, s, prm.drop_tol, Rinv.p, mask.p, nkept.p, Lwork.p, st, nseg);
@@ -2087,25 +2098,33 @@ struct Engine : EngineBase {
       launch_seg_block_update<T>(Q.p, alpha.p, s, s, T(-1), R.p, T(1), R.p, chG.d, bactive.p, st);
       launch_seg_colsq<T>(R.p, s, chG.d, colsq.p, bwork.p, st);
       launch_max_ratio(colsq.p, bnorm.p, s, ratio.p, st, nseg);
-      NSP_CUDA(cudaMemcpyAsync(hr.data(), ratio.p, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
-      NSP_CUDA(cudaMemcpyAsync(hk.data(), nkept.p, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      sync();
-      int any = 0;
-      for (int g = 0; g < nseg; ++g) {
-        if (!h_active[g]) continue;
-        if (hk[g] == 0) { h_active[g] = 0; act_cols[g] = 0; continue; }
-        its[g] += 1;
-        rat[g] = hr[g];
-        act_cols[g] = hk[g];
-        if (!(hr[g] > prm.eps_inner)) h_active[g] = 0;
-        any |= h_active[g];
-      }
-      if (!any) break;
-      NSP_CUDA(cudaMemcpyAsync(bactive.p, h_active.data(), nseg * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+      launch_seg_inner_decide(ratio.p, nkept.p, prm.eps_inner, nseg, bactive.p, bits_in.p,
+                              brat_in.p, bact_in.p, bgo.p, bpass.p, prm.max_inner_it, h,
+                              set_cond, st);
+    };
+    // the next directions W = A_G^{-1} R - P Q^T A_G^{-1} R of the matrices still active
+    auto second_half = [&]() {
       solve_G(R.p, Z.p, s);
       launch_seg_gram<T, T>(Q.p, Z.p, s, s, chG.d, beta.p, bwork.p, st);
       launch_seg_block_update<T>(P.p, beta.p, s, s, T(-1), Z.p, T(1), W.p, chG.d, bactive.p, st);
+    };
+    if (prm.max_inner_it > 0) {
+      first_half(cudaGraphConditionalHandle(0), 0);
+      NSP_CUDA(cudaMemcpyAsync(hint, bgo.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+      sync();
+      if (hint[0]) {
+        device_while(
+            [&](cudaGraphConditionalHandle h) {
+              second_half();
+              first_half(h, 1);
+            },
+            bpass.p);
+      }
     }
+    NSP_CUDA(cudaMemcpyAsync(its.data(), bits_in.p, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NSP_CUDA(cudaMemcpyAsync(act_cols.data(), bact_in.p, nseg * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NSP_CUDA(cudaMemcpyAsync(rat.data(), brat_in.p, nseg * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
     check_status();
     auto t1 = Clock::now();
     launch_spmm<T>(A_G.dT(), E.p, Y.p, s, T(1), nullptr, T(0), st);
@@ -2158,17 +2177,78 @@ struct Engine : EngineBase {
 
   // Outer PCG of every matrix at once. The per-matrix bookkeeping (step counts, stopping
   // test, masks) lives on the device, so an iteration is a fixed sequence of launches with no
-  // host decision; after one eager iteration (which allocates every workspace and builds the
-  // sweep plans) kGraphIters iterations are captured into a CUDA graph and replayed until no
-  // matrix is active. Matrices that stop early are masked (alpha = 0), so replayed
-  // iterations beyond their stop leave them unchanged.
-  static constexpr int kGraphIters = 4;
+  // host decision; matrices that stop early are masked (alpha = 0).
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   DBuf<double> bfn, brel;
   DBuf<int32_t> bits, bany;
   int32_t *h_any = nullptr;
-  int64_t graph_replays = 0;
+
+  // ---- Device-driven loops (CUDA graph conditional nodes): body(h) is captured once into
+  // the body graph of a WHILE node whose conditional h the body's last kernel sets, so the
+  // passes run back to back with no host decision; the body runs at least once. Captured and
+  // launched on the engine's own non-blocking stream (the caller's may be the legacy default
+  // stream, which cannot be captured), ordered after the handle's stream by events. Every
+  // workspace, sweep plan and tuned grid the body uses must already exist (an eager pass
+  // first), and the body must end every pass count at a bound (its kernels decide). `passes`
+  // is a device counter the body increments once per pass: the launches of every pass are
+  // added to the launch counter from it.
+  template <class Body>
+  void device_while(Body &&body, int32_t *passes) {
+    if (!gstream) {
+      NSP_CUDA(cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking));
+      NSP_CUDA(cudaEventCreateWithFlags(&gev[0], cudaEventDisableTiming));
+      NSP_CUDA(cudaEventCreateWithFlags(&gev[1], cudaEventDisableTiming));
+    }
+    NSP_CUDA(cudaMemcpyAsync(hint + 9, passes, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    sync();
+    const int32_t p0 = hint[9];
+    cudaStream_t main_st = st;
+    NSP_CUDA(cudaEventRecord(gev[0], main_st));
+    NSP_CUDA(cudaStreamWaitEvent(gstream, gev[0], 0));
+    struct Scope {   // restores the handle's stream and frees the graph on every exit
+      cudaStream_t &ref, saved;
+      cudaGraph_t graph = nullptr;
+      cudaGraphExec_t exec = nullptr;
+      ~Scope() {
+        ref = saved;
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+      }
+    } sc{st, main_st};
+    st = gstream;
+    NSP_CUDA(cudaGraphCreate(&sc.graph, 0));
+    cudaGraphConditionalHandle h = 0;
+    NSP_CUDA(cudaGraphConditionalHandleCreate(&h, sc.graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    NSP_CUDA(cudaGraphAddNode(&node, sc.graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    const int64_t l0 = launches_counted();
+    NSP_CUDA(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal));
+    try {
+      body(h);
+    } catch (...) {
+      cudaGraph_t unused = nullptr;
+      cudaStreamEndCapture(st, &unused);
+      throw;
+    }
+    NSP_CUDA(cudaStreamEndCapture(st, &bodyg));
+    const int64_t per_pass = launches_counted() - l0;
+    add_launches(-per_pass);   // counted when they run
+    NSP_CUDA(cudaGraphInstantiate(&sc.exec, sc.graph, 0));
+    NSP_CUDA(cudaGraphLaunch(sc.exec, st));
+    NSP_CUDA(cudaMemcpyAsync(hint + 8, passes, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NSP_CUDA(cudaStreamSynchronize(st));
+    add_launches(per_pass * (int64_t)(hint[8] - p0));
+    NSP_CUDA(cudaEventRecord(gev[1], gstream));
+    NSP_CUDA(cudaStreamWaitEvent(main_st, gev[1], 0));
+  }
 
   void pcg_batched_iteration(double rtol, int maxit) {
     const int64_t n = an.n, nI = an.nI;
@@ -2236,68 +2316,20 @@ struct Engine : EngineBase {
     }
     NSP_CUDA(cudaMemcpyAsync(vp.p, vz.p, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_seg_dot(vr.p, vz.p, chF.d, d_rz, bwork.p, st);
-    // one eager iteration, then graph replays of kGraphIters iterations
-    int done_its = 0;
-    auto any_active = [&]() {
-      NSP_CUDA(cudaMemcpyAsync(h_any, bany.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-      sync();
-      return *h_any != 0;
-    };
+    // one eager iteration (every workspace and sweep plan then exists), then the rest as a
+    // device-driven CUDA graph loop: k_seg_converge's flag ends it, with no host decision
     pcg_batched_iteration(rtol, maxit);
-    done_its = 1;
-    bool more = any_active() && done_its < maxit;
-    // graphs are captured and replayed on the engine's own non-blocking stream (the caller's
-    // stream may be the legacy default stream, which cannot be captured), ordered after the
-    // caller's stream by an event and joined back at the end
-    cudaStream_t main_st = st;
-    if (more) {
-      if (!gstream) {
-        NSP_CUDA(cudaStreamCreateWithFlags(&gstream, cudaStreamNonBlocking));
-        NSP_CUDA(cudaEventCreateWithFlags(&gev[0], cudaEventDisableTiming));
-        NSP_CUDA(cudaEventCreateWithFlags(&gev[1], cudaEventDisableTiming));
-      }
-      NSP_CUDA(cudaEventRecord(gev[0], main_st));
-      NSP_CUDA(cudaStreamWaitEvent(gstream, gev[0], 0));
-      st = gstream;
-    }
-    struct RestoreStream {
-      cudaStream_t &ref, saved;
-      ~RestoreStream() { ref = saved; }
-    } restore{st, main_st};
-    if (more) {
-      cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      const int64_t l0 = launches_counted();
-      NSP_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      try {
-        for (int q = 0; q < kGraphIters; ++q) pcg_batched_iteration(rtol, maxit);
-      } catch (...) {
-        cudaStreamEndCapture(st, &graph);
-        if (graph) cudaGraphDestroy(graph);
-        throw;
-      }
-      NSP_CUDA(cudaStreamEndCapture(st, &graph));
-      const int64_t per_replay = launches_counted() - l0;
-      add_launches(-per_replay);  // counted when they run
-      NSP_CUDA(cudaGraphInstantiate(&exec, graph, 0));
-      try {
-        while (more) {
-          NSP_CUDA(cudaGraphLaunch(exec, st));
-          add_launches(per_replay);
-          ++graph_replays;
-          done_its += kGraphIters;
-          more = any_active() && done_its < maxit;
-        }
-      } catch (...) {
-        cudaGraphExecDestroy(exec);
-        cudaGraphDestroy(graph);
-        throw;
-      }
-      cudaGraphExecDestroy(exec);
-      cudaGraphDestroy(graph);
-      NSP_CUDA(cudaEventRecord(gev[1], gstream));
-      NSP_CUDA(cudaStreamWaitEvent(main_st, gev[1], 0));
-      st = main_st;
+    NSP_CUDA(cudaMemcpyAsync(h_any, bany.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    sync();
+    if (*h_any != 0 && maxit > 1) {
+      bpass.ensure(2);
+      NSP_CUDA(cudaMemsetAsync(bpass.p + 1, 0, sizeof(int32_t), st));
+      device_while(
+          [&](cudaGraphConditionalHandle h) {
+            pcg_batched_iteration(rtol, maxit);
+            launch_loop_condition(bany.p, bpass.p + 1, h, st);
+          },
+          bpass.p + 1);
     }
     launch_axpby(n, nullptr, 1.0, x0, 1.0, vx.p, st);
     launch_scatter_rows<double, double>(i2g_I.p, nI, vx.p, x_user, 1, st);

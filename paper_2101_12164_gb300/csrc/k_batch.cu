@@ -218,6 +218,49 @@ __global__ void k_seg_converge(const double *rr, const double *fn, double rtol, 
   if (threadIdx.x == 0) *any = s_any;
 }
 
+// The per-matrix stopping rule of the inner block PCG after an iteration (one block): a
+// matrix with no search direction left stops without counting the iteration; otherwise its
+// count grows, its residual ratio and kept columns are recorded, and it stops once the ratio
+// is at most eps. *passes counts the iterations of the whole batch; *go = (a matrix is still
+// active and passes < maxit) is also written to the conditional of the CUDA graph loop that
+// runs the iterations, when set_cond is 1.
+__global__ void k_seg_inner_decide(const double *ratio, const int32_t *nkept, double eps,
+                                   int nseg, int32_t *active, int32_t *its, double *rat,
+                                   int32_t *act, int32_t *go, int32_t *passes, int maxit,
+                                   cudaGraphConditionalHandle h, int set_cond) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = 0;
+  __syncthreads();
+  for (int g = threadIdx.x; g < nseg; g += blockDim.x) {
+    if (!active[g]) continue;
+    if (nkept[g] == 0) {
+      active[g] = 0;
+      act[g] = 0;
+      continue;
+    }
+    its[g] += 1;
+    rat[g] = ratio[g];
+    act[g] = nkept[g];
+    if (!(ratio[g] > eps)) active[g] = 0;
+    else s_any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int pcount = *passes + 1;
+    *passes = pcount;
+    const int more = s_any && pcount < maxit;
+    *go = more;
+    if (set_cond) cudaGraphSetConditional(h, more ? 1u : 0u);
+  }
+}
+
+// the conditional of a CUDA graph loop from a flag the loop body computed; counts passes
+__global__ void k_loop_condition(const int32_t *flag, int32_t *passes,
+                                 cudaGraphConditionalHandle h) {
+  *passes += 1;
+  cudaGraphSetConditional(h, *flag != 0 ? 1u : 0u);
+}
+
 // Zs[i][j] = (double) Zt[i][j] * sqrt(Sigma[seg][j]) over chunks
 template <typename T>
 __global__ void k_seg_scale_sqrt(const T *Zt, int k, const double *Sigma, SegChunks ch, double *Zs) {
@@ -309,6 +352,21 @@ void launch_seg_converge(const double *rr, const double *fn, double rtol, int ma
                          int32_t *active, int32_t *its, double *rel, int32_t *any, int nseg,
                          cudaStream_t st) {
   k_seg_converge<<<1, 1024, 0, st>>>(rr, fn, rtol, maxit, active, its, rel, any, nseg);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_seg_inner_decide(const double *ratio, const int32_t *nkept, double eps, int nseg,
+                             int32_t *active, int32_t *its, double *rat, int32_t *act,
+                             int32_t *go, int32_t *passes, int maxit,
+                             cudaGraphConditionalHandle h, int set_cond, cudaStream_t st) {
+  k_seg_inner_decide<<<1, 1024, 0, st>>>(ratio, nkept, eps, nseg, active, its, rat, act, go,
+                                         passes, maxit, h, set_cond);
+  NSP_LAUNCH_CHECK();
+}
+
+void launch_loop_condition(const int32_t *flag, int32_t *passes, cudaGraphConditionalHandle h,
+                           cudaStream_t st) {
+  k_loop_condition<<<1, 1, 0, st>>>(flag, passes, h);
   NSP_LAUNCH_CHECK();
 }
 

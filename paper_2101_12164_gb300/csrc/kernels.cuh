@@ -296,5 +296,13 @@ void launch_seg_pcg_init(const double *ff, int nseg, double *fn, int32_t *active
 void launch_seg_converge(const double *rr, const double *fn, double rtol, int maxit,
                          int32_t *active, int32_t *its, double *rel, int32_t *any, int nseg,
                          cudaStream_t st);
+// inner block-PCG stopping rule of every matrix, optionally driving a CUDA graph loop
+void launch_seg_inner_decide(const double *ratio, const int32_t *nkept, double eps, int nseg,
+                             int32_t *active, int32_t *its, double *rat, int32_t *act,
+                             int32_t *go, int32_t *passes, int maxit,
+                             cudaGraphConditionalHandle h, int set_cond, cudaStream_t st);
+// sets a CUDA graph loop's conditional from *flag (and counts the pass)
+void launch_loop_condition(const int32_t *flag, int32_t *passes, cudaGraphConditionalHandle h,
+                           cudaStream_t st);
 
 }  // namespace nsp
