@@ -100,6 +100,14 @@ static int narrow_tiles() {
   return e && std::atoi(e) == 64 ? kSweepBlockRows : kSweepBlockRowsNarrow;
 }
 
+// K steps per forward K group of the single-vector shared-memory sweep (NSP_VSM_KDIV,
+// default 48; measurements)
+static int vsm_kdiv() {
+  const char *e = std::getenv("NSP_VSM_KDIV");
+  const int v = e ? std::atoi(e) : 48;
+  return v >= 8 ? v : 48;
+}
+
 static int relax_level() {
   const char *e = std::getenv("NSP_RELAX");
   return e ? std::atoi(e) : 2;
@@ -761,7 +769,10 @@ struct ForestData {
     int64_t vu = 0;
     for (int b = 0; b < nb; ++b)
       vu = std::max(vu, ((roff[b + 1] - roff[b] + 3) & ~int64_t(3)) + ((pool[b] + 3) & ~int64_t(3)));
-    auto kg_of = [&](int J) { return std::min(kVsmKG, std::max(1, (h.sn_w[J] + 47) / 48)); };
+    const int kdiv = vsm_kdiv();
+    auto kg_of = [&](int J) {
+      return std::min(kVsmKG, std::max(1, (h.sn_w[J] + kdiv - 1) / kdiv));
+    };
     int need_max = 4;
     for (int J = 0; J < nsn; ++J) {
       const int ld = (int)panel_ld(h.sn_m[J]), kg = kg_of(J);
