@@ -117,6 +117,9 @@ def test_short_sketch_refused_before_the_library_reads_it():
     with pytest.raises(ValueError):
         N.nsp_build_batched([(A, part, 2), (A, part, 2)], k=4, p=2,
                             sketch=np.zeros((n_g, 6)))
+    with pytest.raises(ValueError):      # the nested sketch of the recursive A_Gamma
+        N.nsp_build(A, part, 2, k=4, p=2, gamma_part=np.array([0, 0, 0, -1, 1, 1, 1, 1]),
+                    gamma_nblocks=2, gamma_k=1, gamma_p=1, gamma_sketch=np.zeros(1))
     N._check_sketch(dict(k=4, p=2, sketch=np.zeros((n_i, 6)), variant="m3"), n_g, n_i)
     N._check_sketch(dict(k=4, p=2, sketch=np.zeros((n_g, 6))), n_g, n_i)
 
