@@ -150,6 +150,33 @@ def test_fullsize_m1_solves_like_m2(N, torch, cfg1):
     assert its["m1"] <= its["m2"] + 5, its
 
 
+def test_fullsize_recursive_gamma_solves(N, torch, cfg1):
+    # the recursive A_G (concluding section; reading of the oracle's recursive_gamma) at the
+    # benchmark size: A_G split into 16 blocks by the interface nodes' coordinates, M2' of
+    # rank 32. Entry-wise parity is on the small cases (test_gpu_recursive.py); here the outer
+    # tolerance is reached and the weaker A_G^{-1} costs a few outer iterations over M2
+    P, D = cfg1
+    _, b = F.make_rhs(P, 1, 0)
+    G = F.make_sketch(P.n_gamma, P.s, 1, 0)
+    part2 = F.interface_partition(D.A_G, P.coords[D.gamma], 16)
+    bd = torch.tensor(b, dtype=torch.float64, device="cuda")
+    its = {}
+    for rec in (False, True):
+        kw = dict(gamma_part=part2, gamma_nblocks=16, gamma_k=32, gamma_p=16) if rec else {}
+        h = N.nsp_build(P.A, P.part, P.nsub, k=P.k, p=P.p, eps_inner=P.eps_inner,
+                        precision="fp32", sketch=G, **kw)
+        xd = torch.zeros_like(bd)
+        inf = h.solve(bd, xd, rtol=P.rtol, maxit=500)
+        its[rec] = inf["it_pcg"]
+        assert O.relative_residual(P.A, xd.cpu().numpy(), b) < 1e-8
+        if rec:
+            inf2 = h.info()
+            assert inf2["n_gamma2"] == int((part2 < 0).sum())
+            assert inf2["rank_gamma"] == 32 and inf2["it_inner_gamma"] >= 1
+        h.destroy()
+    assert its[True] <= its[False] + 10, its
+
+
 # ------------------------------------------------------------------ 128^3 (stored oracle)
 @pytest.fixture(scope="module")
 def cfg4():
